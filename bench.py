@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""rand_cholQR benchmark: effective HBM GB/s of the factorization of an m x n FP64 matrix.
+
+Workload (the large single-matrix configuration): m = 2^23 rows, n = 64 columns,
+kappa = 1e12, V = U diag(sigma) W^T (seeded, synthetic), CountSketch s1 = 2(n^2+n),
+Gaussian sketch s2 = 4n.  One step = one full rand_cholQR call (sketch, Householder R_s,
+W = V R_s^{-1}, Gram, Cholesky, Q = W R_c^{-1}, R = R_c R_s) on data resident in HBM.
+
+Metric: effective GB/s = 32 m n / t -- the method's algorithmic traffic (three reads of V
+and one write of Q, FP64) over the step time; V is 4.3 GB, far larger than the 129 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs independent replicas (one matrix per rank, no collective in the data path)
+under torchrun and reports the whole-job aggregate.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Derived FP64 ALU peak: 2 DFMA/clk/SM (GB300's FP64 units) x 152 SMs x 2.07 GHz x 2 flops.
+FP64_ALU_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=2**23)
+    p.add_argument("--n", type=int, default=64)
+    p.add_argument("--kappa", type=float, default=1e12)
+    p.add_argument("--prec", default="fp64", choices=["fp64", "f32x2"])
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip e2e, baselines, CPU baseline (quick runs)")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_name(a):
+    return f"rand_cholQR m={a.m} n={a.n} kappa={a.kappa:g} s1={2*(a.n*a.n+a.n)} s2={4*a.n}"
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for i, nm in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single-threaded, on a bounded row sample
+# ---------------------------------------------------------------------------------------
+def cpu_baseline(n, kappa, rows):
+    import oracle
+    import synthetic
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(rows, n, kappa, seed=0)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    t0 = time.perf_counter()
+    oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    dt = time.perf_counter() - t0
+    return {"value": 32.0 * rows * n / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"rand_cholQR of the first {rows} rows (m={rows}, n={n}, kappa={kappa:g}, "
+                      f"same s1/s2), single-threaded FP64 C oracle, {dt:.1f} s"}
+
+
+def run_reference(a):
+    """--impl reference: the oracle, timed on the host cores, on a bounded sample per step."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synthetic
+    rows = 1 << 16
+    s1, s2 = synthetic.default_sketch_sizes(a.n)
+    V = synthetic.make_v(rows, a.n, a.kappa, seed=0)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    for _ in range(a.warmup):
+        oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    dt = (time.perf_counter() - t0) / a.steps
+    value = 32.0 * rows * a.n / dt / 1e9
+    line = {"impl": "reference", "metric": "rand_cholQR effective HBM GB/s (m x n FP64)",
+            "value": value, "unit": "GB/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {rows} rows of the workload per step"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2309_05868_gb300 as rq
+    import synthetic
+
+    m, n = a.m, a.n
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    prec = rq.FP64 if a.prec == "fp64" else rq.F32X2
+    dev = torch.device("cuda", local_rank)
+    V = synthetic.make_v_torch(m, n, a.kappa, seed=rank, device=dev)
+    Q = torch.empty_like(V)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx = rq.Context(local_rank)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rq.randqr_factor(V, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    st, info = rq.get_status(ctx)
+    if st != 0:
+        raise rq.RandQRError(st, info)
+    ctx.kernel_times()  # clear
+    ctx.set_profiling(True)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    ctx.set_profiling(False)
+    kt = ctx.kernel_times()
+    st, info = rq.get_status(ctx)
+    if st != 0:
+        raise rq.RandQRError(st, info)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+
+    # accuracy of the timed result (whole matrix, checked on the device with torch)
+    G = Q.T @ Q
+    orth = torch.linalg.matrix_norm(G - torch.eye(n, dtype=G.dtype, device=dev), ord=2).item()
+    resid = (torch.linalg.norm(V - Q @ R) / torch.linalg.norm(V)).item()
+
+    algo_bytes = 32.0 * m * n
+    value = algo_bytes * world / (ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    kind, (tot_ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
+    avg_ms = tot_ms / launches
+    flops_per_row = {"trsm": n * n, "gram": n * (n + 1), "cs_scatter": n}.get(kind, n * n)
+    if a.prec == "fp64":
+        achieved = flops_per_row * m / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": kind, "achieved": achieved,
+                "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                "algorithmic": f"{flops_per_row} FP64 flops per row x {m} rows per launch",
+                "kernel_share": tot_ms / (ms * a.steps)}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        achieved = 16.0 * m * n / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "kernel_share": tot_ms / (ms * a.steps)}
+
+    line = {"metric": "rand_cholQR effective HBM GB/s (m x n FP64)", "value": value,
+            "unit": "GB/s", "n_gpus": world, "steps": a.steps, "warmup": max(a.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if a.prec == "fp64" else "f32x2",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "m": m, "n": n, "kappa": a.kappa,
+                       "s1": s1, "s2": s2, "precision": a.prec,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (V = %.1f GB)" % (8.0 * m * n / 1e9)},
+            "roofline": roof, "clocks": clk,
+            "gpu_launches": sum(c for _, c in kt.values()),
+            "kernels_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()},
+            "accuracy": {"orth_err_2": orth, "resid_rel_F": resid}}
+
+    if not a.no_extras:
+        # end to end through the public API: pinned host V in, Q and R back to pinned host
+        Vh = V.cpu().pin_memory()
+        Qh = torch.empty_like(Vh).pin_memory()
+        Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Vd2 = torch.empty_like(V)
+        ke = max(1, min(a.steps, 5))
+
+        def e2e_step():
+            Vd2.copy_(Vh, non_blocking=True)
+            rq.randqr_factor(Vd2, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+            Qh.copy_(Q, non_blocking=True)
+            Rh.copy_(R, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1) / ke
+        line["e2e"] = {"value": algo_bytes * world / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+                       "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n,
+                       "ms_per_step": e2e_ms}
+        del Vh, Qh, Vd2
+
+        # GPU baselines on a matrix all three can factor (kappa = 1e4), same size
+        Vb = synthetic.make_v_torch(m, n, 1e4, seed=rank + 100, device=dev)
+        times = {}
+        for name, fn in [("rand_cholqr", lambda: rq.randqr_factor(Vb, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)),
+                         ("cholqr2", lambda: rq.randqr_cholqr2(Vb, Q=Q, R=R, ctx=ctx, sync=False)),
+                         ("shifted_cholqr3", lambda: rq.randqr_shifted_cholqr3(Vb, Q=Q, R=R, ctx=ctx, sync=False))]:
+            fn()
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(3):
+                fn()
+            g1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = g0.elapsed_time(g1) / 3
+            st, _ = rq.get_status(ctx)
+            times[name + "_status"] = st
+        line["baselines_ms"] = {"kappa": 1e4, **times,
+                                "rand_cholqr_over_cholqr2": times["rand_cholqr"] / times["cholqr2"],
+                                "rand_cholqr_over_shifted_cholqr3": times["rand_cholqr"] / times["shifted_cholqr3"]}
+        del Vb
+        if rank == 0:
+            line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

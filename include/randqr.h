@@ -1,0 +1,171 @@
+/*
+ * randqr.h -- C ABI of librandqr.so: rand_cholQR on one GB300 GPU (sm_103a).
+ *
+ * Method: Higgins, Szyld, Boman & Yamazaki, "Analysis of Randomized Householder-Cholesky
+ * QR Factorization with Multisketching" (arXiv 2309.05868).
+ *   Algorithm 1 (randQR):      Ws = S2 S1 V;  R_s = R(hhqr(Ws));  W = V R_s^{-1}
+ *   Algorithm 2 (cholQR):      G = W^T W;  R_c = chol(G);  Q = W R_c^{-1}
+ *   Algorithm 3 (rand_cholQR): the two above, then R = R_c R_s
+ *   Algorithm 4 (cholQR2):     cholQR twice
+ *
+ * Letters: the paper writes V as n x m (n rows); this API uses V as m x n: m rows, n
+ * columns, m >> n.  s1 (the paper's p1) is the CountSketch size, s2 (p2) the Gaussian
+ * sketch size.  The sizes of the benchmarked configurations are s1 = 2(n^2+n), s2 = 4n.
+ *
+ * Layout: every matrix is FP64, row-major, with a leading dimension (ld) counted in
+ * elements; ld >= number of columns.  Small outputs (R, n x n) are row-major with ldr.
+ * Memory: every pointer named *_dev (or V, Q, R, Ws, S2) is device memory on the
+ * context's device, owned by the caller, and must stay valid until the call's work on
+ * the stream has finished.  The context owns its workspace (sketch buffers, Gram,
+ * triangular factors, the cached S2) and frees it in randqr_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Every compute call only enqueues work on that stream and returns RANDQR_OK once the
+ * launches succeeded -- except when `info` is non-NULL: then the call waits for the
+ * stream, copies the device status word and returns the numerical status (e.g.
+ * RANDQR_ERR_NOT_SPD) with the details in *info.  randqr_get_status() does the same
+ * wait-and-read for calls made with info == NULL.
+ *
+ * Errors: argument errors are detected on the host before any launch and return
+ * RANDQR_ERR_ARG with nothing enqueued.  Numerical failures are detected on the device:
+ * the first failing kernel writes the context's status word and every later kernel of
+ * that context returns at once, so outputs are left unspecified but nothing faults.
+ * A context is not thread-safe: use one context per host thread or serialise calls.
+ */
+#ifndef RANDQR_H_
+#define RANDQR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RANDQR_OK = 0,
+  RANDQR_PENDING = 1,           /* serving: request not finished yet */
+  RANDQR_ERR_ARG = -1,          /* bad size, ld, pointer or enum; nothing was enqueued */
+  RANDQR_ERR_NOT_SPD = -2,      /* Cholesky met a non-positive pivot; info = 1-based index */
+  RANDQR_ERR_RANK = -3,         /* zero or non-finite diagonal of R_s (V numerically rank deficient) */
+  RANDQR_ERR_NONFINITE = -4,    /* NaN or Inf reached a factor */
+  RANDQR_ERR_NOMEM = -5,        /* workspace allocation failed or exceeds the HBM budget */
+  RANDQR_ERR_ADMISSION = -6,    /* serving: request can never fit the HBM budget */
+  RANDQR_ERR_TIMEOUT = -7,      /* a bounded device-side wait gave up */
+  RANDQR_ERR_CUDA = -8,         /* a CUDA runtime call failed (see randqr_last_cuda_error) */
+  RANDQR_ERR_TICKET = -9        /* serving: unknown ticket */
+} randqr_status;
+
+typedef enum {
+  RANDQR_FP64 = 0,   /* every step in IEEE FP64 */
+  RANDQR_F32X2 = 1   /* the three row passes (triangular solves and Gram) in double-float
+                        (pairs of FP32, ~48-bit significand) on the FP32 pipes; sketch,
+                        Householder QR, Cholesky and R = R_c R_s stay in FP64 */
+} randqr_precision;
+
+typedef struct {
+  int32_t info;       /* failing Cholesky pivot (1-based) or 0 */
+  int32_t stage;      /* which Cholesky failed: 1 = first, 2 = second, 3 = third; else 0 */
+  double rs_min_diag; /* smallest diagonal entry of R_s (rand_cholQR) or of the first R */
+  double rs_max_diag; /* largest diagonal entry of that factor */
+} randqr_info;
+
+typedef struct randqr_ctx randqr_ctx;
+
+/* Create a context on `device` (made current for the call).  hbm_budget_bytes caps the
+ * context's own workspace (0 = no cap).  No workspace is allocated until first use. */
+randqr_status randqr_create(randqr_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Wait for the context's work on all streams it used, free its workspace, destroy it. */
+randqr_status randqr_destroy(randqr_ctx *ctx);
+
+/* Static description of a status code. */
+const char *randqr_status_string(randqr_status s);
+
+/* The last CUDA error string seen by this context ("" if none). */
+const char *randqr_last_cuda_error(const randqr_ctx *ctx);
+
+/* Wait for `stream`, read and clear the context's device status word. */
+randqr_status randqr_get_status(randqr_ctx *ctx, void *stream, randqr_info *info);
+
+/* Bytes of workspace the context holds now. */
+size_t randqr_workspace_bytes(const randqr_ctx *ctx);
+
+/* ---- Per-kernel timing (tracing) ------------------------------------------------------
+ * While profiling is on, every kernel the context launches is bracketed by two CUDA events
+ * recorded on the call's stream.  randqr_get_kernel_times waits for those events, writes
+ * for each kernel kind k < *n_kinds (at most max_kinds) the summed device time in ms and
+ * the launch count, and clears the record.  randqr_kernel_name(k) names kind k.  The
+ * events cost a few microseconds per launch; nothing is recorded while profiling is off. */
+randqr_status randqr_set_profiling(randqr_ctx *ctx, int enable);
+randqr_status randqr_get_kernel_times(randqr_ctx *ctx, int32_t max_kinds, double *total_ms,
+                                      int64_t *launches, int32_t *n_kinds);
+const char *randqr_kernel_name(int32_t kind);
+
+/* ---- Step 1 of Algorithm 1, split into its parts (Sec. 4.2) --------------------------
+ * CountSketch S1 (Sec. 2: one +-1 per column of S1, row and sign uniform): column i of
+ * S1 has its nonzero in row bucket[i] with value sign[i], where
+ *   x = splitmix64(seed XOR splitmix64(i)),  bucket = floor(hi32(x) * s1 / 2^32),
+ *   sign = -1 if (x & 1) else +1,
+ * splitmix64 being the output function of Steele, Lea & Flood's generator.  Writes m
+ * int32 buckets and m int8 signs to device memory.  Requires 1 <= s1 < 2^31, m >= 0. */
+randqr_status randqr_cs_hash(randqr_ctx *ctx, uint64_t seed, int64_t m, int64_t s1,
+                             int32_t *bucket_dev, int8_t *sign_dev, void *stream);
+
+/* Gaussian sketch S2 (s2 x s1, row-major, device) with N(0, 1/s2) entries (Sec. 2,
+ * S = G / sqrt(p)).  Entry (r, c) takes Philox4x64-10 (Salmon et al. 2011) at counter
+ * (r*s1 + c, 0, 0, 0) with key (seed, 0), u1 = ((x0>>11)+1) 2^-53, u2 = (x1>>11) 2^-53,
+ * and Box-Muller z = sqrt(-2 ln u1) cos(2 pi u2).  The integers are exact; the
+ * transcendental functions are CUDA's, so entries agree with a host libm to a few ulp. */
+randqr_status randqr_gauss_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
+                                  double *S2_dev, void *stream);
+
+/* Ws = S2 S1 V (Algorithm 1 step 1), s2 x n row-major (ld n) in device memory.
+ * W1 = S1 V is formed in the context's workspace by a scatter-add of V's rows (CountSketch
+ * with `seed`), then Ws = S2 W1.  S2 may be NULL: the context then uses (and caches) the
+ * sketch randqr_gauss_sketch would give for seed + 1.  Requires 1 <= n <= s2 <= s1,
+ * m >= 1, ldv >= n. */
+randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, double *Ws, void *stream);
+
+/* ---- The factorizations -------------------------------------------------------------
+ * All three return Q (m x n, ldq) with orthonormal columns and R (n x n upper, ldr,
+ * strictly-lower part zeroed, positive diagonal) with V = Q R.  Q may alias V (ldq ==
+ * ldv) for an in-place factorization; otherwise Q and V must not overlap.  Requires
+ * 1 <= n <= 128, n <= m, ld >= n. */
+
+/* rand_cholQR (Algorithm 3): randQR with the multisketch S2 S1 (sizes s1, s2, CountSketch
+ * seed `seed`, Gaussian S2 as in randqr_sketch), then cholQR of W = V R_s^{-1}, and
+ * R = R_c R_s.  R_s is normalised to a positive diagonal.  Requires n <= s2 <= s1.
+ * `prec` selects the arithmetic of the row passes (randqr_precision). */
+randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, randqr_precision prec, double *Q, int64_t ldq,
+                            double *R, int64_t ldr, randqr_info *info, void *stream);
+
+/* randQR alone (Algorithm 1): Q0 = V R_s^{-1} (S2S1-orthogonal, kappa(Q0) = O(1)) and
+ * R0 = R_s.  Same arguments as randqr_factor. */
+randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, double *Q0, int64_t ldq, double *R0,
+                            int64_t ldr, randqr_info *info, void *stream);
+
+/* CholeskyQR2 (Algorithm 4), FP64.  Fails with RANDQR_ERR_NOT_SPD once kappa(V) is near
+ * u^{-1/2} (about 1e8, Sec. 6.3). */
+randqr_status randqr_cholqr2(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                             int64_t ldv, double *Q, int64_t ldq, double *R, int64_t ldr,
+                             randqr_info *info, void *stream);
+
+/* Shifted CholeskyQR3 (cited by the paper, Sec. 1 and 6; defined by Fukaya, Kannan,
+ * Nakatsukasa, Yamamoto & Yanagisawa, SISC 2020), FP64: G = V^T V + s I with
+ * s = 11 (m n + n (n+1)) u ||V||_F^2, u = 2^-53; R0 = chol(G); Q0 = V R0^{-1}; then
+ * CholeskyQR2 of Q0 and R = R12 R0. */
+randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                                     int64_t ldv, double *Q, int64_t ldq, double *R,
+                                     int64_t ldr, randqr_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANDQR_H_ */

@@ -1,0 +1,285 @@
+"""rand_cholQR on GB300: Python binding of librandqr.so (C ABI in include/randqr.h).
+
+Argument marshalling only: every step of the factorization runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (float64, row-major, contiguous rows); torch is
+used for device memory and streams.  If the library is missing this module raises on
+first use -- there is no CPU fallback.
+
+Method: Higgins, Szyld, Boman & Yamazaki, arXiv 2309.05868 (Algorithms 1-4).  Letters: V
+is m x n (m rows), sketch sizes s1 (CountSketch) and s2 (Gaussian).
+"""
+import ctypes as _ct
+import os as _os
+
+__all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_sketch",
+           "randqr_factor", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
+           "default_sketch_sizes", "library_path", "FP64", "F32X2"]
+
+FP64, F32X2 = 0, 1
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+_LIB_PATH = _os.path.join(_HERE, "_build", "librandqr.so")
+_lib = None
+
+_STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_NOT_SPD", -3: "ERR_RANK",
+           -4: "ERR_NONFINITE", -5: "ERR_NOMEM", -6: "ERR_ADMISSION", -7: "ERR_TIMEOUT",
+           -8: "ERR_CUDA", -9: "ERR_TICKET"}
+
+
+class RandQRError(RuntimeError):
+    def __init__(self, status, info=None, detail=""):
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+        self.info = info
+        msg = f"randqr: {self.name}"
+        if info is not None and info.info:
+            msg += f" (pivot {info.info}, stage {info.stage})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class Info(_ct.Structure):
+    _fields_ = [("info", _ct.c_int32), ("stage", _ct.c_int32),
+                ("rs_min_diag", _ct.c_double), ("rs_max_diag", _ct.c_double)]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"librandqr.so not built ({_LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = _ct.CDLL(_LIB_PATH)
+    vp, i64, u64, i32 = _ct.c_void_p, _ct.c_int64, _ct.c_uint64, _ct.c_int32
+    sig = {
+        "randqr_create": [_ct.POINTER(vp), _ct.c_int, _ct.c_size_t],
+        "randqr_destroy": [vp],
+        "randqr_get_status": [vp, vp, _ct.POINTER(Info)],
+        "randqr_cs_hash": [vp, u64, i64, i64, vp, vp, vp],
+        "randqr_gauss_sketch": [vp, u64, i64, i64, vp, vp],
+        "randqr_sketch": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
+        "randqr_factor": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
+                          _ct.POINTER(Info), vp],
+        "randqr_randqr": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, i64, vp, i64,
+                          _ct.POINTER(Info), vp],
+        "randqr_cholqr2": [vp, vp, i64, i64, i64, vp, i64, vp, i64, _ct.POINTER(Info), vp],
+        "randqr_shifted_cholqr3": [vp, vp, i64, i64, i64, vp, i64, vp, i64, _ct.POINTER(Info), vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.randqr_status_string.restype = _ct.c_char_p
+    L.randqr_status_string.argtypes = [i32]
+    L.randqr_last_cuda_error.restype = _ct.c_char_p
+    L.randqr_last_cuda_error.argtypes = [vp]
+    L.randqr_workspace_bytes.restype = _ct.c_size_t
+    L.randqr_workspace_bytes.argtypes = [vp]
+    L.randqr_set_profiling.restype = i32
+    L.randqr_set_profiling.argtypes = [vp, _ct.c_int]
+    L.randqr_get_kernel_times.restype = i32
+    L.randqr_get_kernel_times.argtypes = [vp, i32, _ct.POINTER(_ct.c_double),
+                                          _ct.POINTER(_ct.c_int64), _ct.POINTER(i32)]
+    L.randqr_kernel_name.restype = _ct.c_char_p
+    L.randqr_kernel_name.argtypes = [i32]
+    _lib = L
+    return L
+
+
+def default_sketch_sizes(n):
+    """(s1, s2) = (2 (n^2 + n), 4 n)."""
+    return 2 * (n * n + n), 4 * n
+
+
+class Context:
+    """Owns a randqr_ctx (workspace, cached Gaussian sketch, device status word)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        L = _load()
+        self._h = _ct.c_void_p()
+        st = L.randqr_create(_ct.byref(self._h), int(device), int(hbm_budget_bytes))
+        if st != 0:
+            raise RandQRError(st)
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _load().randqr_destroy(self._h)
+            self._h = _ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self):
+        return int(_load().randqr_workspace_bytes(self._h))
+
+    def set_profiling(self, enable=True):
+        self._check(_load().randqr_set_profiling(self._h, int(bool(enable))))
+
+    def kernel_times(self):
+        """{kernel name: (total device ms, launches)} recorded since the last read."""
+        L = _load()
+        tot = (_ct.c_double * 32)()
+        cnt = (_ct.c_int64 * 32)()
+        nk = _ct.c_int32(0)
+        self._check(L.randqr_get_kernel_times(self._h, 32, tot, cnt, _ct.byref(nk)))
+        return {L.randqr_kernel_name(k).decode(): (tot[k], int(cnt[k]))
+                for k in range(nk.value) if cnt[k]}
+
+    def _check(self, st, info=None):
+        if st != 0:
+            detail = _load().randqr_last_cuda_error(self._h).decode() if st == -8 else ""
+            raise RandQRError(st, info, detail)
+
+
+_default_ctx = {}
+
+
+def _ctx(ctx, t):
+    if ctx is not None:
+        return ctx
+    dev = t.device.index if t.device.index is not None else 0
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _ct.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return _ct.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_mat(t, name):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2 and t.stride(1) == 1):
+        raise ValueError(f"{name}: need a CUDA float64 matrix with unit column stride")
+    return t.stride(0)
+
+
+# ---------------------------------------------------------------------------------------
+# Entry points, same names as the C ABI.
+# ---------------------------------------------------------------------------------------
+def randqr_cs_hash(seed, m, s1, device=0, ctx=None, stream=None):
+    """CountSketch buckets (int32) and signs (int8) of rows 0..m-1, on the device."""
+    import torch
+    bucket = torch.empty(m, dtype=torch.int32, device=f"cuda:{device}")
+    sign = torch.empty(m, dtype=torch.int8, device=f"cuda:{device}")
+    c = _ctx(ctx, bucket)
+    c._check(_load().randqr_cs_hash(c.handle, seed, m, s1, _ptr(bucket), _ptr(sign), _stream(stream)))
+    return bucket, sign
+
+
+def randqr_gauss_sketch(seed, s2, s1, device=0, ctx=None, stream=None):
+    """Gaussian sketch S2 (s2 x s1, N(0, 1/s2)) on the device."""
+    import torch
+    S2 = torch.empty((s2, s1), dtype=torch.float64, device=f"cuda:{device}")
+    c = _ctx(ctx, S2)
+    c._check(_load().randqr_gauss_sketch(c.handle, seed, s2, s1, _ptr(S2), _stream(stream)))
+    return S2
+
+
+def randqr_sketch(V, s1, s2, seed=0, S2=None, ctx=None, stream=None):
+    """Ws = S2 S1 V (s2 x n)."""
+    import torch
+    ldv = _check_mat(V, "V")
+    m, n = V.shape
+    Ws = torch.empty((s2, n), dtype=torch.float64, device=V.device)
+    if S2 is not None:
+        _check_mat(S2, "S2")
+    c = _ctx(ctx, V)
+    c._check(_load().randqr_sketch(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), _ptr(Ws),
+                                   _stream(stream)))
+    return Ws
+
+
+def _alloc_qr(V, Q, R):
+    import torch
+    m, n = V.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, device=V.device)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=V.device)
+    return Q, R, _check_mat(Q, "Q"), _check_mat(R, "R")
+
+
+def randqr_factor(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=None, ctx=None,
+                  stream=None, sync=True):
+    """rand_cholQR (Algorithm 3): returns (Q, R, info).  With sync=False the call only
+    enqueues work and info is None (read it later with Context.status)."""
+    ldv = _check_mat(V, "V")
+    m, n = V.shape
+    d1, d2 = default_sketch_sizes(n)
+    s1 = d1 if s1 is None else s1
+    s2 = d2 if s2 is None else s2
+    if S2 is not None:
+        _check_mat(S2, "S2")
+    Q, R, ldq, ldr = _alloc_qr(V, Q, R)
+    c = _ctx(ctx, V)
+    info = Info() if sync else None
+    st = _load().randqr_factor(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), int(prec),
+                               _ptr(Q), ldq, _ptr(R), ldr,
+                               _ct.byref(info) if sync else None, _stream(stream))
+    c._check(st, info)
+    return Q, R, info
+
+
+def randqr_randqr(V, s1=None, s2=None, seed=0, S2=None, Q=None, R=None, ctx=None, stream=None):
+    """randQR (Algorithm 1): returns (Q0, R0, info)."""
+    ldv = _check_mat(V, "V")
+    m, n = V.shape
+    d1, d2 = default_sketch_sizes(n)
+    s1 = d1 if s1 is None else s1
+    s2 = d2 if s2 is None else s2
+    Q, R, ldq, ldr = _alloc_qr(V, Q, R)
+    c = _ctx(ctx, V)
+    info = Info()
+    st = _load().randqr_randqr(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), _ptr(Q), ldq,
+                               _ptr(R), ldr, _ct.byref(info), _stream(stream))
+    c._check(st, info)
+    return Q, R, info
+
+
+def _baseline(fn, V, Q, R, ctx, stream, sync):
+    ldv = _check_mat(V, "V")
+    m, n = V.shape
+    Q, R, ldq, ldr = _alloc_qr(V, Q, R)
+    c = _ctx(ctx, V)
+    info = Info() if sync else None
+    st = fn(c.handle, _ptr(V), m, n, ldv, _ptr(Q), ldq, _ptr(R), ldr,
+            _ct.byref(info) if sync else None, _stream(stream))
+    c._check(st, info)
+    return Q, R, info
+
+
+def randqr_cholqr2(V, Q=None, R=None, ctx=None, stream=None, sync=True):
+    """CholeskyQR2 (Algorithm 4): returns (Q, R, info)."""
+    return _baseline(_load().randqr_cholqr2, V, Q, R, ctx, stream, sync)
+
+
+def randqr_shifted_cholqr3(V, Q=None, R=None, ctx=None, stream=None, sync=True):
+    """Shifted CholeskyQR3: returns (Q, R, info)."""
+    return _baseline(_load().randqr_shifted_cholqr3, V, Q, R, ctx, stream, sync)
+
+
+def get_status(ctx, stream=None):
+    """Wait for `stream` and return (status, Info) of the context's last call."""
+    info = Info()
+    st = _load().randqr_get_status(ctx.handle, _stream(stream), _ct.byref(info))
+    return st, info

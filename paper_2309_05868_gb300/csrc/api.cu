@@ -1,0 +1,467 @@
+// api.cu -- the C entry points declared in include/randqr.h.
+//
+// Each factorization is a fixed sequence of kernels on the caller's stream; the host only
+// checks arguments, carves the context's workspace and launches.  Launch sequence of
+// rand_cholQR (Algorithm 3):
+//   zero W1, Ws, G | (S2 once per (seed, s1, s2)) | CountSketch scatter V -> W1 |
+//   sketch GEMM W1 -> Ws | Householder R_s of Ws | W = V R_s^{-1} (into Q) |
+//   G = W^T W | R_c = chol(G), R = R_c R_s | Q = W R_c^{-1} (in place)
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using rq::DevStatus;
+
+namespace {
+
+constexpr int64_t kMaxN = 128;
+
+randqr_status cuda_fail(randqr_ctx *ctx, cudaError_t e, const char *where) {
+  if (ctx) snprintf(ctx->last_err, sizeof(ctx->last_err), "%s: %s", where, cudaGetErrorString(e));
+  return RANDQR_ERR_CUDA;
+}
+
+#define RQ_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+cudaEvent_t take_event(randqr_ctx *ctx) {
+  if (!ctx->prof_pool.empty()) {
+    cudaEvent_t e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch through f(); when profiling is on, bracket it with events on s.
+template <class F>
+cudaError_t timed(randqr_ctx *ctx, cudaStream_t s, int kind, F &&f) {
+  if (!ctx->prof) return f();
+  cudaEvent_t b = take_event(ctx), e = take_event(ctx);
+  if (!b || !e) return cudaErrorMemoryAllocation;
+  cudaError_t r = cudaEventRecord(b, s);
+  if (r != cudaSuccess) return r;
+  r = f();
+  if (r != cudaSuccess) return r;
+  r = cudaEventRecord(e, s);
+  ctx->prof_recs.push_back({kind, b, e});
+  return r;
+}
+
+struct Workspace {
+  double *W1, *Ws, *Rs, *G, *Rc, *Rt, *Rt2;
+};
+
+size_t packed(int64_t n) { return (size_t)(n * (n + 1) / 2); }
+
+size_t align_up(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Ensure the slab holds `bytes`; grows by reallocation (after waiting for the device).
+randqr_status ensure_ws(randqr_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return RANDQR_OK;
+  if (ctx->budget && bytes + ctx->s2_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
+  RQ_CUDA(cudaDeviceSynchronize());
+  if (ctx->ws) RQ_CUDA(cudaFree(ctx->ws));
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_NOMEM;
+  }
+  ctx->ws_bytes = bytes;
+  return RANDQR_OK;
+}
+
+randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspace *w) {
+  const size_t sz[7] = {align_up(sizeof(double) * (size_t)(s1 * n)),
+                        align_up(sizeof(double) * (size_t)(s2 * n)),
+                        align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
+                        align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
+                        align_up(sizeof(double) * packed(n))};
+  size_t total = 0;
+  for (size_t b : sz) total += b;
+  randqr_status st = ensure_ws(ctx, total);
+  if (st != RANDQR_OK) return st;
+  char *p = (char *)ctx->ws;
+  double **dst[7] = {&w->W1, &w->Ws, &w->Rs, &w->G, &w->Rc, &w->Rt, &w->Rt2};
+  for (int i = 0; i < 7; ++i) {
+    *dst[i] = (double *)p;
+    p += sz[i];
+  }
+  return RANDQR_OK;
+}
+
+// The cached S2 for (seed, s1, s2), generated on `s` if missing.
+randqr_status ensure_s2(randqr_ctx *ctx, uint64_t seed, int64_t s1, int64_t s2, cudaStream_t s,
+                        const double **out) {
+  if (!(ctx->s2_valid && ctx->s2_seed == seed && ctx->s2_s1 == s1 && ctx->s2_s2 == s2)) {
+    const size_t bytes = sizeof(double) * (size_t)(s1 * s2);
+    if (bytes > ctx->s2_bytes) {
+      if (ctx->budget && bytes + ctx->ws_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
+      RQ_CUDA(cudaDeviceSynchronize());
+      if (ctx->s2_buf) RQ_CUDA(cudaFree(ctx->s2_buf));
+      ctx->s2_buf = nullptr;
+      ctx->s2_bytes = 0;
+      if (cudaMalloc(&ctx->s2_buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RANDQR_ERR_NOMEM;
+      }
+      ctx->s2_bytes = bytes;
+    }
+    RQ_CUDA(timed(ctx, s, rq::K_GAUSS_GEN, [&] { return rq::launch_gauss_gen(seed, s2, s1, ctx->s2_buf, s); }));
+    ctx->s2_valid = true;
+    ctx->s2_seed = seed;
+    ctx->s2_s1 = s1;
+    ctx->s2_s2 = s2;
+  }
+  *out = ctx->s2_buf;
+  return RANDQR_OK;
+}
+
+bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
+  const char *pa = (const char *)a, *pb = (const char *)b;
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+size_t span_bytes(int64_t rows, int64_t cols, int64_t ld) {
+  return rows == 0 ? 0 : sizeof(double) * (size_t)((rows - 1) * ld + cols);
+}
+
+// Common checks of the factorization entry points.
+bool bad_factor_args(const double *V, int64_t m, int64_t n, int64_t ldv, const double *Q,
+                     int64_t ldq, const double *R, int64_t ldr) {
+  if (!V || !Q || !R) return true;
+  if (n < 1 || n > kMaxN || m < n || ldv < n || ldq < n || ldr < n) return true;
+  if ((const void *)Q != (const void *)V &&
+      ranges_overlap(V, span_bytes(m, n, ldv), Q, span_bytes(m, n, ldq)))
+    return true;
+  if (Q == V && ldq != ldv) return true;
+  if (ranges_overlap(R, span_bytes(n, n, ldr), Q, span_bytes(m, n, ldq))) return true;
+  return false;
+}
+
+bool bad_sketch_sizes(int64_t n, int64_t s1, int64_t s2) {
+  return s2 < n || s1 < s2 || s1 >= ((int64_t)1 << 31) || s2 > ((int64_t)1 << 20);
+}
+
+randqr_status begin_call(randqr_ctx *ctx, cudaStream_t s) {
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  RQ_CUDA(cudaMemsetAsync(ctx->status_dev, 0, sizeof(DevStatus), s));
+  return RANDQR_OK;
+}
+
+randqr_status finish_call(randqr_ctx *ctx, cudaStream_t s, randqr_info *info) {
+  if (!info) return RANDQR_OK;
+  return randqr_get_status(ctx, s, info);
+}
+
+// Algorithm 1 steps 1-2 into w.Rs (packed); V read once by the scatter.
+randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                              int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                              const double *S2, const Workspace &w, cudaStream_t s,
+                              bool do_hhqr) {
+  const double *S2p = S2;
+  if (!S2p) {
+    randqr_status st = ensure_s2(ctx, seed + 1, s1, s2, s, &S2p);
+    if (st != RANDQR_OK) return st;
+  }
+  RQ_CUDA(cudaMemsetAsync(w.W1, 0, sizeof(double) * (size_t)(s1 * n), s));
+  RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
+  RQ_CUDA(timed(ctx, s, rq::K_CS_SCATTER, [&] {
+    return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, w.W1, ctx->num_sms, ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
+    return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
+  }));
+  if (do_hhqr)
+    RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, ctx->status_dev, s); }));
+  return RANDQR_OK;
+}
+
+// One cholQR pass (Algorithm 2) on X into Y: G = X^T X (+ shift) -> R_x -> Y = X R_x^{-1}.
+// With Rprev, writes Rnext = R_x Rprev (packed); with Rdense, writes that product (or R_x)
+// dense.
+randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy,
+                          int64_t m, int64_t n, double shift_coeff, const double *Rprev,
+                          double *Rnext, double *Rdense, int64_t ldr, int stage,
+                          randqr_precision prec, const Workspace &w, cudaStream_t s) {
+  RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+  RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+    return rq::launch_gram(X, ldx, m, n, w.G, prec, ctx->num_sms, ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
+    return rq::launch_potrf(w.G, n, shift_coeff, w.Rc, Rprev, Rnext, Rdense, ldr, stage,
+                            ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
+    return rq::launch_trsm(X, ldx, Y, ldy, m, n, w.Rc, prec, ctx->num_sms, ctx->status_dev, s);
+  }));
+  return RANDQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+randqr_status randqr_create(randqr_ctx **ctx_out, int device, size_t hbm_budget_bytes) {
+  if (!ctx_out) return RANDQR_ERR_ARG;
+  *ctx_out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return RANDQR_ERR_ARG;
+  }
+  randqr_ctx *ctx = new (std::nothrow) randqr_ctx();
+  if (!ctx) return RANDQR_ERR_NOMEM;
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&ctx->status_dev, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&ctx->status_host, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMemset(ctx->status_dev, 0, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->status_dev) cudaFree(ctx->status_dev);
+    if (ctx->status_host) cudaFreeHost(ctx->status_host);
+    delete ctx;
+    return RANDQR_ERR_CUDA;
+  }
+  *ctx_out = ctx;
+  return RANDQR_OK;
+}
+
+randqr_status randqr_destroy(randqr_ctx *ctx) {
+  if (!ctx) return RANDQR_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->s2_buf) cudaFree(ctx->s2_buf);
+  if (ctx->status_dev) cudaFree(ctx->status_dev);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
+  for (auto &r : ctx->prof_recs) {
+    cudaEventDestroy(r.beg);
+    cudaEventDestroy(r.end);
+  }
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+  delete ctx;
+  return RANDQR_OK;
+}
+
+randqr_status randqr_set_profiling(randqr_ctx *ctx, int enable) {
+  if (!ctx) return RANDQR_ERR_ARG;
+  ctx->prof = enable != 0;
+  return RANDQR_OK;
+}
+
+randqr_status randqr_get_kernel_times(randqr_ctx *ctx, int32_t max_kinds, double *total_ms,
+                                      int64_t *launches, int32_t *n_kinds) {
+  if (!ctx || max_kinds < 0 || (max_kinds > 0 && (!total_ms || !launches))) return RANDQR_ERR_ARG;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  const int nk = std::min<int>(max_kinds, rq::K_NUM_KINDS);
+  for (int k = 0; k < nk; ++k) {
+    total_ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  randqr_status st = RANDQR_OK;
+  for (auto &r : ctx->prof_recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.end);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.beg, r.end);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaEventElapsedTime");
+    if (r.kind < nk) {
+      total_ms[r.kind] += ms;
+      launches[r.kind] += 1;
+    }
+    ctx->prof_pool.push_back(r.beg);
+    ctx->prof_pool.push_back(r.end);
+  }
+  ctx->prof_recs.clear();
+  if (n_kinds) *n_kinds = nk;
+  return st;
+}
+
+const char *randqr_kernel_name(int32_t kind) {
+  static const char *names[rq::K_NUM_KINDS] = {"gauss_gen", "cs_scatter", "sketch_gemm", "hhqr",
+                                               "trsm", "gram", "potrf", "unpack", "cs_hash"};
+  return (kind >= 0 && kind < rq::K_NUM_KINDS) ? names[kind] : "unknown";
+}
+
+const char *randqr_status_string(randqr_status s) {
+  switch (s) {
+    case RANDQR_OK: return "ok";
+    case RANDQR_PENDING: return "pending";
+    case RANDQR_ERR_ARG: return "invalid argument";
+    case RANDQR_ERR_NOT_SPD: return "Cholesky breakdown (Gram matrix not numerically positive definite)";
+    case RANDQR_ERR_RANK: return "zero or non-finite diagonal in the sketch's triangular factor";
+    case RANDQR_ERR_NONFINITE: return "non-finite value";
+    case RANDQR_ERR_NOMEM: return "out of device memory or over the HBM budget";
+    case RANDQR_ERR_ADMISSION: return "request can never fit the HBM budget";
+    case RANDQR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RANDQR_ERR_CUDA: return "CUDA runtime error";
+    case RANDQR_ERR_TICKET: return "unknown ticket";
+  }
+  return "unknown status";
+}
+
+const char *randqr_last_cuda_error(const randqr_ctx *ctx) { return ctx ? ctx->last_err : ""; }
+
+size_t randqr_workspace_bytes(const randqr_ctx *ctx) {
+  return ctx ? ctx->ws_bytes + ctx->s2_bytes : 0;
+}
+
+randqr_status randqr_get_status(randqr_ctx *ctx, void *stream, randqr_info *info) {
+  if (!ctx) return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  RQ_CUDA(cudaMemcpyAsync(ctx->status_host, ctx->status_dev, sizeof(DevStatus),
+                          cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  const DevStatus h = *ctx->status_host;
+  if (info) {
+    info->info = h.info;
+    info->stage = h.stage;
+    info->rs_min_diag = h.dmin;
+    info->rs_max_diag = h.dmax;
+  }
+  return (randqr_status)h.code;
+}
+
+randqr_status randqr_cs_hash(randqr_ctx *ctx, uint64_t seed, int64_t m, int64_t s1,
+                             int32_t *bucket_dev, int8_t *sign_dev, void *stream) {
+  if (!ctx || m < 0 || s1 < 1 || s1 >= ((int64_t)1 << 31) || (m > 0 && (!bucket_dev || !sign_dev)))
+    return RANDQR_ERR_ARG;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  RQ_CUDA(timed(ctx, (cudaStream_t)stream, rq::K_CS_HASH, [&] {
+    return rq::launch_cs_hash(seed, m, s1, bucket_dev, sign_dev, (cudaStream_t)stream);
+  }));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_gauss_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
+                                  double *S2_dev, void *stream) {
+  if (!ctx || !S2_dev || s2 < 1 || s1 < 1) return RANDQR_ERR_ARG;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  RQ_CUDA(timed(ctx, (cudaStream_t)stream, rq::K_GAUSS_GEN, [&] {
+    return rq::launch_gauss_gen(seed, s2, s1, S2_dev, (cudaStream_t)stream);
+  }));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, double *Ws, void *stream) {
+  if (!ctx || !V || !Ws || n < 1 || m < 1 || ldv < n || bad_sketch_sizes(n, s1, s2))
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
+  if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, false)) != RANDQR_OK)
+    return st;
+  RQ_CUDA(cudaMemcpyAsync(Ws, w.Ws, sizeof(double) * (size_t)(s2 * n), cudaMemcpyDeviceToDevice, s));
+  return RANDQR_OK;
+}
+
+static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                                 int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                                 const double *S2, randqr_precision prec, double *Q, int64_t ldq,
+                                 double *R, int64_t ldr, randqr_info *info, void *stream,
+                                 bool second_pass) {
+  if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr) || bad_sketch_sizes(n, s1, s2) ||
+      prec != RANDQR_FP64 || s2 > m)
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
+  if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, true)) != RANDQR_OK)
+    return st;
+  // W = V R_s^{-1}, written into Q.
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
+    return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, prec, ctx->num_sms, ctx->status_dev, s);
+  }));
+  if (!second_pass) {
+    RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack(w.Rs, n, R, ldr, ctx->status_dev, s); }));
+    return finish_call(ctx, s, info);
+  }
+  // cholQR of W, in place on Q; R = R_c R_s written dense.
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, prec, w, s)) !=
+      RANDQR_OK)
+    return st;
+  return finish_call(ctx, s, info);
+}
+
+randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, randqr_precision prec, double *Q, int64_t ldq,
+                            double *R, int64_t ldr, randqr_info *info, void *stream) {
+  return factor_impl(ctx, V, m, n, ldv, s1, s2, seed, S2, prec, Q, ldq, R, ldr, info, stream,
+                     true);
+}
+
+randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                            int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                            const double *S2, double *Q0, int64_t ldq, double *R0,
+                            int64_t ldr, randqr_info *info, void *stream) {
+  return factor_impl(ctx, V, m, n, ldv, s1, s2, seed, S2, RANDQR_FP64, Q0, ldq, R0, ldr, info,
+                     stream, false);
+}
+
+randqr_status randqr_cholqr2(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                             int64_t ldv, double *Q, int64_t ldq, double *R, int64_t ldr,
+                             randqr_info *info, void *stream) {
+  if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr)) return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
+  // pass 1: Q0 = V R0^{-1} into Q; keep R0 in w.Rt
+  if ((st = cholqr_pass(ctx, V, ldv, Q, ldq, m, n, 0.0, nullptr, nullptr, nullptr, 0, 1,
+                        RANDQR_FP64, w, s)) != RANDQR_OK)
+    return st;
+  RQ_CUDA(cudaMemcpyAsync(w.Rt, w.Rc, sizeof(double) * packed(n), cudaMemcpyDeviceToDevice, s));
+  // pass 2 in place; R = R1 R0
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, nullptr, R, ldr, 2, RANDQR_FP64,
+                        w, s)) != RANDQR_OK)
+    return st;
+  return finish_call(ctx, s, info);
+}
+
+randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                                     int64_t ldv, double *Q, int64_t ldq, double *R,
+                                     int64_t ldr, randqr_info *info, void *stream) {
+  if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr)) return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
+  const double u = 1.1102230246251565404e-16;  // 2^-53
+  const double coeff = 11.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * u;
+  // shifted pass: R0 -> w.Rt
+  if ((st = cholqr_pass(ctx, V, ldv, Q, ldq, m, n, coeff, nullptr, nullptr, nullptr, 0, 1,
+                        RANDQR_FP64, w, s)) != RANDQR_OK)
+    return st;
+  RQ_CUDA(cudaMemcpyAsync(w.Rt, w.Rc, sizeof(double) * packed(n), cudaMemcpyDeviceToDevice, s));
+  // cholQR2 of Q0: R1 R0 -> w.Rt2, then R2 (R1 R0) dense
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, w.Rt2, nullptr, 0, 2, RANDQR_FP64,
+                        w, s)) != RANDQR_OK)
+    return st;
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt2, nullptr, R, ldr, 3, RANDQR_FP64,
+                        w, s)) != RANDQR_OK)
+    return st;
+  return finish_call(ctx, s, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// common.cuh -- device helpers and the context shared by the librandqr translation units.
+//
+// Counter-based generators are written here from their published definitions
+// (splitmix64: Steele, Lea & Flood 2014; Philox4x64-10: Salmon et al. 2011); nothing is
+// shared with the CPU checker.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/randqr.h"
+
+namespace rq {
+
+// ---------------------------------------------------------------------------------------
+// Device status word.  The first kernel that meets a numerical failure records
+// (code, info, stage) with an atomicCAS on code; every kernel checks it on entry and
+// returns at once if it is set, so a failed factorization drains without faulting.
+// ---------------------------------------------------------------------------------------
+struct DevStatus {
+  int32_t code;   // randqr_status (0 = ok)
+  int32_t info;   // 1-based failing pivot
+  int32_t stage;  // which factorization stage failed
+  int32_t pad;
+  double dmin, dmax;  // min / max diagonal of the first triangular factor
+};
+
+__device__ __forceinline__ bool status_failed(const DevStatus *st) {
+  return *(volatile const int32_t *)&st->code != 0;
+}
+
+__device__ __forceinline__ void status_fail(DevStatus *st, int32_t code, int32_t info,
+                                            int32_t stage) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->info = info;
+    st->stage = stage;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// splitmix64 output function and the CountSketch hash built on it.
+// ---------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Row i of V goes to bucket floor(hi32(x) * s1 / 2^32) with sign bit (x & 1), where
+// x = splitmix64(seed ^ splitmix64(i)).  Returned as bucket | (signbit << 31).
+__device__ __forceinline__ uint32_t cs_bucket_sign(uint64_t seed, uint64_t i, uint32_t s1) {
+  uint64_t x = splitmix64(seed ^ splitmix64(i));
+  uint32_t b = (uint32_t)(((x >> 32) * (uint64_t)s1) >> 32);
+  return b | ((uint32_t)(x & 1ULL) << 31);
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox4x64-10.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+    uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+// Flip the sign of a double by its bit pattern (no FP64 pipe instruction).
+__device__ __forceinline__ double flip_if(double v, uint32_t signbit) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)signbit << 63));
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Packed storage of an n x n upper-triangular matrix, column by column:
+// element (k, j), k <= j, lives at j (j + 1) / 2 + k.
+__host__ __device__ __forceinline__ int tri_idx(int k, int j) { return j * (j + 1) / 2 + k; }
+
+}  // namespace rq
+
+// ---------------------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------------------
+struct randqr_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;
+  // one growable workspace slab
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  // cached Gaussian sketch S2 (seed, s1, s2)
+  double *s2_buf = nullptr;
+  size_t s2_bytes = 0;
+  bool s2_valid = false;
+  uint64_t s2_seed = 0;
+  int64_t s2_s1 = 0, s2_s2 = 0;
+  // status word on the device, and a pinned host copy
+  rq::DevStatus *status_dev = nullptr;
+  rq::DevStatus *status_host = nullptr;
+  char last_err[256] = {0};
+  // per-kernel timing (randqr_set_profiling)
+  bool prof = false;
+  struct ProfRec {
+    int kind;
+    cudaEvent_t beg, end;
+  };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace rq {
+// Kernel kinds for the per-kernel timing record.
+enum KernelKind {
+  K_GAUSS_GEN = 0, K_CS_SCATTER, K_SKETCH_GEMM, K_HHQR, K_TRSM, K_GRAM, K_POTRF, K_UNPACK,
+  K_CS_HASH, K_NUM_KINDS
+};
+}  // namespace rq
+
+namespace rq {
+// Kernel launchers (defined in the .cu files; all enqueue on `s`).
+cudaError_t launch_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign,
+                           cudaStream_t s);
+cudaError_t launch_gauss_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cudaStream_t s);
+cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
+                              uint64_t seed, double *W1, int num_sms, const DevStatus *st,
+                              cudaStream_t s);
+cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, int64_t s1,
+                               int64_t n, double *Ws, int num_sms, const DevStatus *st,
+                               cudaStream_t s);
+cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
+                        cudaStream_t s);
+cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,
+                         const double *Rprev_packed, double *Rout_packed, double *Rout,
+                         int64_t ldr, int32_t stage, DevStatus *st, cudaStream_t s);
+cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t ldr,
+                          const DevStatus *st, cudaStream_t s);
+cudaError_t launch_trsm(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m,
+                        int64_t n, const double *Rpacked, randqr_precision prec, int num_sms,
+                        const DevStatus *st, cudaStream_t s);
+cudaError_t launch_gram(const double *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
+                        randqr_precision prec, int num_sms, const DevStatus *st,
+                        cudaStream_t s);
+}  // namespace rq

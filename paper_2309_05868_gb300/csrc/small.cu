@@ -1,0 +1,231 @@
+// small.cu -- the O(poly(n)) steps that sit between the row passes:
+//   Householder QR of the s2 x n sketch (Algorithm 1 step 2), R only, positive diagonal;
+//   Cholesky of the n x n Gram (Algorithm 2 step 2), optionally shifted (sCholQR3);
+//   R = R_c R_prev (Algorithm 3 step 3 / Algorithm 4 step 3).
+// Each runs as one CTA so no host round trip separates it from the row passes; all are
+// FP64.  Triangular factors travel between kernels in packed column-major upper storage
+// (tri_idx), which is what the row-pass kernels stage in shared memory.
+#include "common.cuh"
+
+namespace rq {
+
+constexpr int SMALL_THREADS = 512;
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (int)(blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// Householder QR, R only.  Column j: sigma = ||A[j+1:, j]||^2, beta = -sign(a_jj) sqrt(a_jj^2
+// + sigma), v = A[j:, j] / (a_jj - beta) with v_j = 1, tau = (beta - a_jj) / beta, then
+// A[j:, j+1:] -= tau v (v^T A[j:, j+1:]).  The recurrence is LAPACK's dgeqr2 (Golub & Van
+// Loan Alg. 5.2.1).  A is row-major rows x n; it lives in shared memory when it fits and is
+// updated in place in global memory (L2) otherwise.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, int n,
+                                                        bool use_smem, double *Rp,
+                                                        DevStatus *st) {
+  if (status_failed(st)) return;
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double s_tau, s_v0;
+  double *w = sm;                         // n
+  double *A = use_smem ? sm + n : Ag;     // rows * n
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (use_smem) {
+    for (int e = tid; e < rows * n; e += nt) A[e] = Ag[e];
+    __syncthreads();
+  }
+  for (int j = 0; j < n; ++j) {
+    double part = 0.0;
+    for (int i = j + 1 + tid; i < rows; i += nt) part = fma(A[i * n + j], A[i * n + j], part);
+    const double sigma = block_sum(part, red);
+    if (tid == 0) {
+      const double x0 = A[j * n + j];
+      if (sigma == 0.0) {
+        s_tau = 0.0;
+      } else {
+        const double alpha = sqrt(x0 * x0 + sigma);
+        const double beta = (x0 >= 0.0) ? -alpha : alpha;
+        s_v0 = x0 - beta;
+        s_tau = (beta - x0) / beta;
+        A[j * n + j] = beta;
+      }
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    if (tau == 0.0) continue;
+    const double v0 = s_v0;
+    for (int i = j + 1 + tid; i < rows; i += nt) A[i * n + j] /= v0;
+    __syncthreads();
+    // w_k = tau (a_jk + sum_{i>j} v_i a_ik), one warp per column k
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int k = j + 1 + wid; k < n; k += nw) {
+      double acc = 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(A[i * n + j], A[i * n + k], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) w[k] = tau * (A[j * n + k] + acc);
+    }
+    __syncthreads();
+    const int ncols = n - j - 1;
+    for (int e = tid; e < (rows - j) * ncols; e += nt) {
+      const int i = j + e / ncols, k = j + 1 + e % ncols;
+      if (i == j)
+        A[j * n + k] -= w[k];
+      else
+        A[i * n + k] = fma(-A[i * n + j], w[k], A[i * n + k]);
+    }
+    __syncthreads();
+  }
+  // R with rows flipped to a positive diagonal, packed column-major upper.
+  for (int e = tid; e < n * (n + 1) / 2; e += nt) {
+    int j = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (j * (j + 1) / 2 > e) --j;
+    while ((j + 1) * (j + 2) / 2 <= e) ++j;
+    const int k = e - j * (j + 1) / 2;
+    const double d = A[k * n + k];
+    Rp[e] = (d < 0.0) ? -A[k * n + j] : A[k * n + j];
+  }
+  if (tid == 0) {
+    double dmin = INFINITY, dmax = 0.0;
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+      const double d = fabs(A[k * n + k]);
+      if (!(d > 0.0) || !isfinite(d)) bad = bad ? bad : k + 1;
+      dmin = fmin(dmin, d);
+      dmax = fmax(dmax, d);
+    }
+    st->dmin = dmin;
+    st->dmax = dmax;
+    if (bad) status_fail(st, RANDQR_ERR_RANK, bad, 0);
+  }
+}
+
+cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
+                        cudaStream_t s) {
+  size_t smem = sizeof(double) * (size_t)(n + rows * n);
+  bool use_smem = smem <= 200 * 1024;
+  size_t dyn = use_smem ? smem : sizeof(double) * (size_t)n;
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_hhqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k_hhqr<<<1, SMALL_THREADS, dyn, s>>>(A, (int)rows, (int)n, use_smem, Rpacked, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Cholesky G = R^T R (upper), right-looking on the packed upper triangle in shared memory:
+// r_jj = sqrt(g_jj); r_jl = g_jl / r_jj; g_kl -= r_jk r_jl for j < k <= l.  A pivot that is
+// not > 0 (or NaN) stops the factorization with RANDQR_ERR_NOT_SPD(j+1).  If shift_coeff
+// is nonzero, shift_coeff * trace(G) is added to the diagonal first (sCholQR3's shift,
+// since trace(V^T V) = ||V||_F^2).
+// Then, if Rprev is given, Rout = R Rprev (upper x upper, packed); if Rout_dense is given,
+// the final factor (Rout, or R itself) is written there row-major with zeros below.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, double shift_coeff,
+                                                         double *Rcp, const double *Rprev,
+                                                         double *Routp, double *Rdense,
+                                                         int64_t ldr, int stage, DevStatus *st) {
+  if (status_failed(st)) return;
+  extern __shared__ double A[];  // packed upper, n(n+1)/2
+  __shared__ double red[32];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int P = n * (n + 1) / 2;
+  for (int e = tid; e < P; e += nt) A[e] = Gp[e];
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  if (shift_coeff != 0.0) {
+    double part = 0.0;
+    for (int j = tid; j < n; j += nt) part += A[tri_idx(j, j)];
+    const double tr = block_sum(part, red);
+    for (int j = tid; j < n; j += nt) A[tri_idx(j, j)] += shift_coeff * tr;
+    __syncthreads();
+  }
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double d = A[tri_idx(j, j)];
+      if (!(d > 0.0) || !isfinite(d)) {
+        s_fail = j + 1;
+      } else {
+        A[tri_idx(j, j)] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double rjj = A[tri_idx(j, j)];
+    for (int l = j + 1 + tid; l < n; l += nt) A[tri_idx(j, l)] /= rjj;
+    __syncthreads();
+    const int m = n - j - 1;  // trailing k, l in (j, n)
+    for (int e = tid; e < m * m; e += nt) {
+      const int k = j + 1 + e / m, l = j + 1 + e % m;
+      if (k <= l) A[tri_idx(k, l)] = fma(-A[tri_idx(j, k)], A[tri_idx(j, l)], A[tri_idx(k, l)]);
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) status_fail(st, RANDQR_ERR_NOT_SPD, s_fail, stage);
+    return;
+  }
+  for (int e = tid; e < P; e += nt) Rcp[e] = A[e];
+  if (Rprev == nullptr && Rdense == nullptr) return;
+  // Rout(i, j) = sum_{k=i..j} R(i, k) Rprev(k, j)
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    double v = 0.0;
+    if (j >= i) {
+      if (Rprev) {
+        for (int k = i; k <= j; ++k) v = fma(A[tri_idx(i, k)], Rprev[tri_idx(k, j)], v);
+        if (Routp) Routp[tri_idx(i, j)] = v;
+      } else {
+        v = A[tri_idx(i, j)];
+      }
+    }
+    if (Rdense) Rdense[(int64_t)i * ldr + j] = v;
+  }
+}
+
+cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,
+                         const double *Rprev_packed, double *Rout_packed, double *Rout,
+                         int64_t ldr, int32_t stage, DevStatus *st, cudaStream_t s) {
+  size_t dyn = sizeof(double) * (size_t)(n * (n + 1) / 2);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k_potrf<<<1, SMALL_THREADS, dyn, s>>>(G, (int)n, shift_coeff, Rc_packed, Rprev_packed,
+                                        Rout_packed, Rout, ldr, stage, st);
+  return cudaGetLastError();
+}
+
+// Packed upper -> dense row-major with zeros below the diagonal.
+__global__ void k_unpack(const double *Rp, int n, double *R, int64_t ldr, const DevStatus *st) {
+  if (status_failed(st)) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e % n;
+    R[(int64_t)i * ldr + j] = (j >= i) ? Rp[tri_idx(i, j)] : 0.0;
+  }
+}
+
+cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t ldr,
+                          const DevStatus *st, cudaStream_t s) {
+  k_unpack<<<(unsigned)ceil_div(n * n, 256), 256, 0, s>>>(Rpacked, (int)n, R, ldr, st);
+  return cudaGetLastError();
+}
+
+}  // namespace rq

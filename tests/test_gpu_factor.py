@@ -1,0 +1,191 @@
+"""GPU parity of the factorizations (rand_cholQR, randQR, CholeskyQR2, shifted CholeskyQR3)
+against the CPU oracle through the C ABI, on the same seeded inputs and the same S2.
+
+Tolerances: orthogonality ||I - Q^T Q||_2 <= 1e-12 and residual ||V - QR||_F/||V||_F <=
+1e-13 for kappa(V) up to 1e14 (FP64); Q and R within max(1e-10, 10 x the oracle's own
+spread between two sketches) of the oracle -- see tests/gpu_util.py."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from gpu_util import parity_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rq():
+    import paper_2309_05868_gb300 as rq
+    return rq
+
+
+def _run(rq, V, s1, s2, seed, S2, ld_pad=0, inplace=False, prec=0):
+    m, n = V.shape
+    buf = torch.zeros((m, n + ld_pad), dtype=torch.float64, device="cuda")
+    buf[:, :n] = torch.from_numpy(V).cuda()
+    Vd = buf[:, :n]
+    S2d = torch.from_numpy(S2).cuda()
+    if inplace:
+        Q, R, info = rq.randqr_factor(Vd, s1, s2, seed=seed, S2=S2d, Q=Vd, prec=prec)
+    else:
+        Q, R, info = rq.randqr_factor(Vd, s1, s2, seed=seed, S2=S2d, prec=prec)
+    return Q.cpu().numpy(), R.cpu().numpy(), info
+
+
+CASES = [  # m, n, kappa
+    (20000, 16, 1e10),     # the small benchmarked configuration
+    (3001, 1, 1.0), (2999, 2, 1e3), (5003, 3, 1e6), (4097, 5, 1e12), (6000, 7, 1e14),
+    (10000, 32, 1e0), (10000, 32, 1e4), (12001, 33, 1e8), (20000, 64, 1e12),
+    (20000, 64, 1e14), (16385, 100, 1e8), (20000, 128, 1e4), (20000, 128, 1e14),
+]
+
+
+@pytest.mark.parametrize("m,n,kappa", CASES)
+def test_rand_cholqr_parity(rq, m, n, kappa):
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=m % 97)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, info = _run(rq, V, s1, s2, 0, S2)
+    e2, eF = oracle.orth_err(Q)
+    res = oracle.resid(V, Q, R)
+    assert e2 <= 1e-12, e2
+    assert res <= 1e-13, res
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    Qo, Ro = oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q - Qo).max() <= tq
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= tr
+
+
+@pytest.mark.parametrize("ld_pad,inplace", [(1, False), (5, True), (0, True)])
+def test_leading_dims_and_in_place(rq, ld_pad, inplace):
+    m, n = 7777, 24
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e9, seed=5)
+    S2 = oracle.gauss_sketch(3, s2, s1)
+    Q, R, _ = _run(rq, V, s1, s2, 2, S2, ld_pad=ld_pad, inplace=inplace)
+    Qo, Ro = oracle.rand_cholqr(V, s1, s2, seed=2, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q - Qo).max() <= tq and np.abs(R - Ro).max() / np.abs(Ro).max() <= tr
+
+
+def test_randqr_alone_matches_oracle(rq):
+    m, n = 15000, 20
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e6, seed=6)
+    S2 = oracle.gauss_sketch(4, s2, s1)
+    Q0, R0, info = rq.randqr_randqr(torch.from_numpy(V).cuda(), s1, s2, seed=3,
+                                    S2=torch.from_numpy(S2).cuda())
+    Q0, R0 = Q0.cpu().numpy(), R0.cpu().numpy()
+    Q0o, R0o, _, _ = oracle.randqr(V, s1, s2, seed=3, S2=S2)
+    # R_s comes from a backward-stable QR of the same sketch: rows agree to ~u kappa(Ws)
+    assert np.abs(R0 - R0o).max() / np.abs(R0o).max() < 1e-9
+    assert np.linalg.cond(Q0) < 10
+    assert np.abs(Q0 - Q0o).max() < 1e-7
+    assert info.rs_min_diag > 0 and info.rs_max_diag >= info.rs_min_diag
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e5])
+def test_cholqr2_parity(rq, kappa):
+    m, n = 20000, 32
+    V = synthetic.make_v(m, n, kappa, seed=8)
+    Q, R, _ = rq.randqr_cholqr2(torch.from_numpy(V).cuda())
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    Qo, Ro = oracle.cholqr2(V)
+    assert oracle.orth_err(Q)[0] <= 1e-13 and oracle.resid(V, Q, R) <= 1e-14
+    assert np.abs(Q - Qo).max() <= max(1e-10, 1e-14 * kappa**2)
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-12
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e9])
+def test_shifted_cholqr3_parity(rq, kappa):
+    m, n = 20000, 32
+    V = synthetic.make_v(m, n, kappa, seed=9)
+    Q, R, _ = rq.randqr_shifted_cholqr3(torch.from_numpy(V).cuda())
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    Qo, Ro = oracle.scholqr3(V)
+    assert oracle.orth_err(Q)[0] <= 1e-13 and oracle.resid(V, Q, R) <= 1e-14
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= max(1e-10, 1e-15 * kappa)
+
+
+def _fails(rq, fn, Vd):
+    try:
+        Q, R, _ = fn(Vd)
+    except rq.RandQRError as e:
+        assert e.name == "ERR_NOT_SPD" and e.info.info >= 1 and e.info.stage >= 1
+        return True
+    Qh = Q.cpu().numpy()
+    return not np.isfinite(Qh).all() or oracle.orth_err(Qh)[0] > 1e-6
+
+
+def test_failure_points_sec63(rq):
+    """cholQR2 breaks down past kappa ~ 1e8 (status NOT_SPD with stage and pivot, or a
+    useless Q), sCholQR3 past ~1e12, while rand_cholQR stays accurate (Sec. 6.3)."""
+    m, n = 20000, 32
+    Vd = torch.from_numpy(synthetic.make_v(m, n, 1e13, seed=10)).cuda()
+    assert _fails(rq, rq.randqr_cholqr2, Vd)
+    Vd = torch.from_numpy(synthetic.make_v(m, n, 1e16, seed=10)).cuda()
+    assert _fails(rq, rq.randqr_shifted_cholqr3, Vd)
+    Vd = torch.from_numpy(synthetic.make_v(m, n, 1e15, seed=10)).cuda()
+    Q, R, _ = rq.randqr_factor(Vd)
+    assert oracle.orth_err(Q.cpu().numpy())[0] <= 1e-12
+    # the context recovers: a later call on a good matrix succeeds
+    V2 = torch.from_numpy(synthetic.make_v(m, n, 10.0, seed=1)).cuda()
+    rq.randqr_cholqr2(V2)
+
+
+def test_rank_deficient_and_nonfinite_inputs(rq):
+    m, n = 5000, 8
+    V = synthetic.make_v(m, n, 10.0, seed=11)
+    V[:, 3] = 0.0
+    with pytest.raises(rq.RandQRError) as e:
+        rq.randqr_factor(torch.from_numpy(V).cuda())
+    assert e.value.name == "ERR_RANK"
+    V = synthetic.make_v(m, n, 10.0, seed=11)
+    V[17, 2] = np.nan
+    with pytest.raises(rq.RandQRError) as e:
+        rq.randqr_factor(torch.from_numpy(V).cuda())
+    assert e.value.name in ("ERR_RANK", "ERR_NOT_SPD")
+
+
+def test_argument_errors_enqueue_nothing(rq):
+    V = torch.zeros((100, 8), dtype=torch.float64, device="cuda")
+    for kw in [dict(s1=10, s2=4), dict(s1=5, s2=20), dict(s1=2**31, s2=32)]:
+        with pytest.raises(rq.RandQRError) as e:
+            rq.randqr_factor(V, **kw)
+        assert e.value.name == "ERR_ARG"
+    with pytest.raises(rq.RandQRError):
+        rq.randqr_factor(torch.zeros((100, 129), dtype=torch.float64, device="cuda"))
+    with pytest.raises(rq.RandQRError):  # Q overlapping V without being V
+        big = torch.zeros((200, 8), dtype=torch.float64, device="cuda")
+        rq.randqr_factor(big[:100], s1=144, s2=32, Q=big[50:150])
+
+
+def test_full_size_sampled(rq):
+    """m = 2^23, n = 64, kappa = 1e12 in the benchmarked launch configuration: the hash is
+    bit-exact on every row, R_s matches the oracle's (its sketch and Householder steps are
+    cheap enough to run in full), sampled rows satisfy Q_i R = V_i, and orthogonality and
+    the residual hold on the whole matrix."""
+    m, n, kappa = 2**23, 64, 1e12
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    Vd = synthetic.make_v_torch(m, n, kappa, seed=0)
+    Q, R, info = rq.randqr_factor(Vd, s1, s2, seed=0)
+    G = (Q.T @ Q).cpu().numpy()
+    e2 = oracle.sym_absmax_eig(G - np.eye(n))
+    res = (torch.linalg.norm(Vd - Q @ R) / torch.linalg.norm(Vd)).item()
+    assert e2 <= 1e-12 and res <= 1e-13, (e2, res)
+    Vh = Vd.cpu().numpy()
+    S2 = oracle.gauss_sketch(1, s2, s1)  # the context's cached S2 for seed 0 (seed + 1)
+    _, R0, _ = rq.randqr_randqr(Vd, s1, s2, seed=0)
+    W1 = oracle.countsketch(Vh, s1, 0)
+    R0o = oracle.hhqr_r(oracle.gemm(S2, W1))
+    assert np.abs(R0.cpu().numpy() - R0o).max() / np.abs(R0o).max() < 1e-9
+    rows = synthetic.rng(1).choice(m, 2000, replace=False)
+    Qs, Rh = Q[torch.from_numpy(rows).cuda()].cpu().numpy(), R.cpu().numpy()
+    assert oracle.resid(Vh[rows], Qs, Rh) <= 1e-13
+    b, sg = rq.randqr_cs_hash(0, m, s1)
+    bo, so = oracle.cs_hash(0, m, s1)
+    assert np.array_equal(b.cpu().numpy(), bo) and np.array_equal(sg.cpu().numpy(), so)
