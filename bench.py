@@ -176,48 +176,51 @@ def main():
     ctx = rq.Context(local_rank)
     stream = torch.cuda.current_stream()
 
-    def step():
-        rq.randqr_factor(V, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
-
-    for _ in range(max(a.warmup, 3)):
-        step()
-    st, info = rq.get_status(ctx)
-    if st != 0:
-        raise rq.RandQRError(st, info)
-    ctx.kernel_times()  # clear
-    ctx.set_profiling(True)
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    ctx.set_profiling(False)
-    kt = ctx.kernel_times()
-    st, info = rq.get_status(ctx)
-    if st != 0:
-        raise rq.RandQRError(st, info)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    def measure(prec_, steps, sample_clocks=False):
+        def step():
+            rq.randqr_factor(V, s1, s2, seed=0, prec=prec_, Q=Q, R=R, ctx=ctx, sync=False)
 
-    # accuracy of the timed result (whole matrix, checked on the device with torch)
-    G = Q.T @ Q
-    orth = torch.linalg.matrix_norm(G - torch.eye(n, dtype=G.dtype, device=dev), ord=2).item()
-    resid = (torch.linalg.norm(V - Q @ R) / torch.linalg.norm(V)).item()
+        for _ in range(max(a.warmup, 3)):
+            step()
+        st, info = rq.get_status(ctx)
+        if st != 0:
+            raise rq.RandQRError(st, info)
+        ctx.kernel_times()  # clear
+        ctx.set_profiling(True)
+        clocks = ClockSampler(local_rank)
+        if sample_clocks:
+            clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if sample_clocks else None
+        ms_ = e0.elapsed_time(e1) / steps
+        ctx.set_profiling(False)
+        kt_ = ctx.kernel_times()
+        st, info = rq.get_status(ctx)
+        if st != 0:
+            raise rq.RandQRError(st, info)
+        if world > 1:
+            t = torch.tensor([ms_], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_ = t.item()
+        # accuracy of the timed result (whole matrix, checked on the device with torch)
+        G = Q.T @ Q
+        orth = torch.linalg.matrix_norm(G - torch.eye(n, dtype=G.dtype, device=dev), ord=2).item()
+        resid = (torch.linalg.norm(V - Q @ R) / torch.linalg.norm(V)).item()
+        return ms_, kt_, clk, {"orth_err_2": orth, "resid_rel_F": resid}
+
+    ms, kt, clk, acc = measure(prec, a.steps, sample_clocks=True)
 
     algo_bytes = 32.0 * m * n
     value = algo_bytes * world / (ms / 1e3) / 1e9
@@ -254,9 +257,17 @@ def main():
             "roofline": roof, "clocks": clk,
             "gpu_launches": sum(c for _, c in kt.values()),
             "kernels_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()},
-            "accuracy": {"orth_err_2": orth, "resid_rel_F": resid}}
+            "accuracy": acc}
 
     if not a.no_extras:
+        # the other precision of the row passes, on the same matrix
+        other = "f32x2" if a.prec == "fp64" else "fp64"
+        oprec = rq.F32X2 if other == "f32x2" else rq.FP64
+        oms, okt, _, oacc = measure(oprec, a.steps)
+        line["modes"] = {other: {"value": algo_bytes * world / (oms / 1e3) / 1e9, "unit": "GB/s",
+                                 "ms_per_step": oms, "accuracy": oacc,
+                                 "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
+
         # end to end through the public API: pinned host V in, Q and R back to pinned host
         Vh = V.cpu().pin_memory()
         Qh = torch.empty_like(Vh).pin_memory()

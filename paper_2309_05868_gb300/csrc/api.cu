@@ -58,6 +58,7 @@ cudaError_t timed(randqr_ctx *ctx, cudaStream_t s, int kind, F &&f) {
 
 struct Workspace {
   double *W1, *Ws, *Rs, *G, *Rc, *Rt, *Rt2;
+  float2 *Rdf, *rinv;  // pair form of the current triangular factor (RANDQR_F32X2)
 };
 
 size_t packed(int64_t n) { return (size_t)(n * (n + 1) / 2); }
@@ -81,11 +82,12 @@ randqr_status ensure_ws(randqr_ctx *ctx, size_t bytes) {
 }
 
 randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspace *w) {
-  const size_t sz[7] = {align_up(sizeof(double) * (size_t)(s1 * n)),
+  const size_t sz[9] = {align_up(sizeof(double) * (size_t)(s1 * n)),
                         align_up(sizeof(double) * (size_t)(s2 * n)),
                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
-                        align_up(sizeof(double) * packed(n))};
+                        align_up(sizeof(double) * packed(n)), align_up(sizeof(float2) * packed(n)),
+                        align_up(sizeof(float2) * (size_t)n)};
   size_t total = 0;
   for (size_t b : sz) total += b;
   randqr_status st = ensure_ws(ctx, total);
@@ -96,6 +98,9 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
     *dst[i] = (double *)p;
     p += sz[i];
   }
+  w->Rdf = (float2 *)p;
+  p += sz[7];
+  w->rinv = (float2 *)p;
   return RANDQR_OK;
 }
 
@@ -290,7 +295,8 @@ randqr_status randqr_get_kernel_times(randqr_ctx *ctx, int32_t max_kinds, double
 
 const char *randqr_kernel_name(int32_t kind) {
   static const char *names[rq::K_NUM_KINDS] = {"gauss_gen", "cs_scatter", "sketch_gemm", "hhqr",
-                                               "trsm", "gram", "potrf", "unpack", "cs_hash"};
+                                               "trsm", "gram", "potrf", "unpack", "cs_hash",
+                                               "pack_df", "trsm_df", "gram_df"};
   return (kind >= 0 && kind < rq::K_NUM_KINDS) ? names[kind] : "unknown";
 }
 
@@ -371,13 +377,39 @@ randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t
   return RANDQR_OK;
 }
 
+// Algorithm 3 from R_s on, with the row passes in pair arithmetic: W = V R_s^{-1} is kept
+// in the Q buffer as (hi, lo) pairs, G = W^T W, R_c = chol(G) and R = R_c R_s in FP64, then
+// Q = W R_c^{-1} written back as FP64 in place.
+static randqr_status factor_df(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                               int64_t ldv, double *Q, int64_t ldq, double *R, int64_t ldr,
+                               const Workspace &w, cudaStream_t s, randqr_info *info) {
+  RQ_CUDA(timed(ctx, s, rq::K_PACK_DF, [&] { return rq::launch_pack_df(w.Rs, n, w.Rdf, w.rinv, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_DF, [&] {
+    return rq::launch_trsm_df(V, true, ldv, Q, false, ldq, m, n, w.Rdf, w.rinv, ctx->num_sms,
+                              ctx->status_dev, s);
+  }));
+  RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+  RQ_CUDA(timed(ctx, s, rq::K_GRAM_DF, [&] {
+    return rq::launch_gram_df((const float2 *)Q, ldq, m, n, w.G, ctx->num_sms, ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
+    return rq::launch_potrf(w.G, n, 0.0, w.Rc, w.Rs, nullptr, R, ldr, 1, ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_PACK_DF, [&] { return rq::launch_pack_df(w.Rc, n, w.Rdf, w.rinv, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_DF, [&] {
+    return rq::launch_trsm_df(Q, false, ldq, Q, true, ldq, m, n, w.Rdf, w.rinv, ctx->num_sms,
+                              ctx->status_dev, s);
+  }));
+  return finish_call(ctx, s, info);
+}
+
 static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                                  int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                                  const double *S2, randqr_precision prec, double *Q, int64_t ldq,
                                  double *R, int64_t ldr, randqr_info *info, void *stream,
                                  bool second_pass) {
   if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr) || bad_sketch_sizes(n, s1, s2) ||
-      prec != RANDQR_FP64 || s2 > m)
+      (prec != RANDQR_FP64 && prec != RANDQR_F32X2) || s2 > m)
     return RANDQR_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   randqr_status st = begin_call(ctx, s);
@@ -386,16 +418,17 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
   if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
   if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, true)) != RANDQR_OK)
     return st;
+  if (prec == RANDQR_F32X2 && second_pass) return factor_df(ctx, V, m, n, ldv, Q, ldq, R, ldr, w, s, info);
   // W = V R_s^{-1}, written into Q.
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
-    return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, prec, ctx->num_sms, ctx->status_dev, s);
+    return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
   }));
   if (!second_pass) {
     RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack(w.Rs, n, R, ldr, ctx->status_dev, s); }));
     return finish_call(ctx, s, info);
   }
   // cholQR of W, in place on Q; R = R_c R_s written dense.
-  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, prec, w, s)) !=
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s)) !=
       RANDQR_OK)
     return st;
   return finish_call(ctx, s, info);

@@ -125,7 +125,7 @@ namespace rq {
 // Kernel kinds for the per-kernel timing record.
 enum KernelKind {
   K_GAUSS_GEN = 0, K_CS_SCATTER, K_SKETCH_GEMM, K_HHQR, K_TRSM, K_GRAM, K_POTRF, K_UNPACK,
-  K_CS_HASH, K_NUM_KINDS
+  K_CS_HASH, K_PACK_DF, K_TRSM_DF, K_GRAM_DF, K_NUM_KINDS
 };
 }  // namespace rq
 
@@ -153,4 +153,13 @@ cudaError_t launch_trsm(const double *X, int64_t ldx, double *Y, int64_t ldy, in
 cudaError_t launch_gram(const double *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
                         randqr_precision prec, int num_sms, const DevStatus *st,
                         cudaStream_t s);
+// double-float (RANDQR_F32X2) row passes
+cudaError_t launch_pack_df(const double *Rp, int64_t n, float2 *Rdf, float2 *rinv,
+                           const DevStatus *st, cudaStream_t s);
+cudaError_t launch_trsm_df(const void *X, bool x_f64, int64_t ldx, void *Y, bool y_f64,
+                           int64_t ldy, int64_t m, int64_t n, const float2 *Rdf,
+                           const float2 *rinv, int num_sms, const DevStatus *st,
+                           cudaStream_t s);
+cudaError_t launch_gram_df(const float2 *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
+                           int num_sms, const DevStatus *st, cudaStream_t s);
 }  // namespace rq

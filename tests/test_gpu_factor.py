@@ -189,3 +189,37 @@ def test_full_size_sampled(rq):
     b, sg = rq.randqr_cs_hash(0, m, s1)
     bo, so = oracle.cs_hash(0, m, s1)
     assert np.array_equal(b.cpu().numpy(), bo) and np.array_equal(sg.cpu().numpy(), so)
+
+
+DF_CASES = [(20000, 16, 1e10), (3001, 1, 1.0), (5003, 3, 1e6), (6000, 7, 1e14), (10000, 32, 1e4),
+            (12001, 33, 1e8), (20000, 64, 1e12), (20000, 64, 1e14), (16385, 100, 1e8),
+            (20000, 128, 1e14)]
+
+
+@pytest.mark.parametrize("m,n,kappa", DF_CASES)
+def test_rand_cholqr_f32x2_parity(rq, m, n, kappa):
+    """Row passes in pair arithmetic (~2^-47 unit roundoff): the same orthogonality and
+    residual targets as FP64; Q and R against the FP64 oracle within the oracle's spread
+    scaled by the ratio of unit roundoffs (2^6)."""
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=m % 89)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, info = _run(rq, V, s1, s2, 0, S2, prec=rq.F32X2)
+    e2, _ = oracle.orth_err(Q)
+    res = oracle.resid(V, Q, R)
+    assert e2 <= 1e-12, e2
+    assert res <= 1e-13, res
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    Qo, Ro = oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q - Qo).max() <= 64 * tq
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 64 * tr
+
+
+def test_f32x2_in_place_and_ld(rq):
+    m, n = 9999, 40
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e11, seed=3)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, _ = _run(rq, V, s1, s2, 0, S2, ld_pad=3, inplace=True, prec=rq.F32X2)
+    assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
