@@ -129,6 +129,26 @@ randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t
                             int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                             const double *S2, double *Ws, void *stream);
 
+/* Ws = S2 S1 V exactly as randqr_sketch computes it, but without a context and without
+ * allocating any device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc where they need the sketch (a framework that owns
+ * every device allocation through its own pool, a host callback or latency-critical path
+ * where an allocation's implicit synchronisation is not allowed, a library that must not
+ * grow its host application's device footprint).
+ * Scratch: the CountSketch accumulator W1 lives in a fixed device array of 2^20 doubles
+ * (8 MiB) plus a 64-byte status word, held by every GPU that loads the library until the
+ * process exits; requires s1 * n <= 1048576 (else RANDQR_ERR_ARG, nothing enqueued).
+ * S2 (s2 x s1, device) is required (NULL -> RANDQR_ERR_ARG), since generating it would need
+ * scratch too.  Runs on the current device and `stream`; Ws (s2 x n, ld n) is overwritten.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  Every call
+ * shares the one array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong results -- serialise them.  Each call clears W1 before use.
+ * Same size rules as randqr_sketch otherwise; RANDQR_ERR_CUDA if a launch fails. */
+randqr_status randqr_sketch_static(const double *V, int64_t m, int64_t n, int64_t ldv,
+                                   int64_t s1, int64_t s2, uint64_t seed, const double *S2,
+                                   double *Ws, void *stream);
+
 /* ---- The factorizations -------------------------------------------------------------
  * All three return Q (m x n, ldq) with orthonormal columns and R (n x n upper, ldr,
  * strictly-lower part zeroed, positive diagonal) with V = Q R.  Q may alias V (ldq ==

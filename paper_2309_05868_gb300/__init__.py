@@ -63,6 +63,7 @@ def _load():
         "randqr_cs_hash": [vp, u64, i64, i64, vp, vp, vp],
         "randqr_gauss_sketch": [vp, u64, i64, i64, vp, vp],
         "randqr_sketch": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
+        "randqr_sketch_static": [vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
         "randqr_factor": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
                           _ct.POINTER(Info), vp],
         "randqr_randqr": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, i64, vp, i64,
@@ -206,6 +207,22 @@ def randqr_sketch(V, s1, s2, seed=0, S2=None, ctx=None, stream=None):
     c = _ctx(ctx, V)
     c._check(_load().randqr_sketch(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), _ptr(Ws),
                                    _stream(stream)))
+    return Ws
+
+
+def randqr_sketch_static(V, s1, s2, S2, Ws, seed=0, stream=None):
+    """Ws = S2 S1 V through the allocation-free entry point: no context, no device
+    allocation (its scratch is a fixed device array, s1 * n <= 2^20).  For callers that
+    cannot allocate device memory where they sketch; Ws (s2 x n) and S2 are caller-owned.
+    Calls that overlap on the GPU share the scratch and race."""
+    ldv = _check_mat(V, "V")
+    _check_mat(S2, "S2")
+    _check_mat(Ws, "Ws")
+    m, n = V.shape
+    st = _load().randqr_sketch_static(_ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), _ptr(Ws),
+                                      _stream(stream))
+    if st != 0:
+        raise RandQRError(st)
     return Ws
 
 

@@ -1,0 +1,88 @@
+// sketch_static.cu -- randqr_sketch_static: the multisketch Ws = S2 S1 V with its scratch
+// in a fixed device array instead of context-owned memory, for callers that must not
+// allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the point where they need a sketch: code running
+// inside a framework that owns every device allocation through its own pool, code called
+// from a host callback or a real-time path where a blocking allocation (which may
+// synchronise the device) is not allowed, or a library that must not grow the process's
+// footprint behind its host application's back.  This entry point needs no context (whose
+// creation allocates) and performs no allocation: the CountSketch accumulator W1 and the
+// device status word live in the file-scope arrays below, which every GPU that loads the
+// library holds until the process exits (8 MiB + 64 bytes per device).
+#include <mutex>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int64_t kStaticW1Max = int64_t(1) << 20;  // doubles: s1 * n <= 1,048,576 (8 MiB)
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_static_w1[kStaticW1Max];
+static __device__ __align__(256) rq::DevStatus g_static_status;
+
+struct StaticSlot {
+  bool ready = false;
+  double *w1 = nullptr;
+  rq::DevStatus *status = nullptr;
+  int num_sms = 0;
+};
+
+StaticSlot g_slots[kMaxDevices];
+std::mutex g_slots_mu;
+
+// Once per device, with that device current: the device addresses of the static arrays.
+// (In host code the array names are host-side stand-ins, not device addresses.)
+cudaError_t static_slot(int dev, StaticSlot *out) {
+  std::lock_guard<std::mutex> lock(g_slots_mu);
+  StaticSlot &s = g_slots[dev];
+  if (!s.ready) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_w1);
+    if (e != cudaSuccess) return e;
+    s.w1 = (double *)p;
+    e = cudaGetSymbolAddress(&p, g_static_status);
+    if (e != cudaSuccess) return e;
+    s.status = (rq::DevStatus *)p;
+    e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    s.ready = true;
+  }
+  *out = s;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" randqr_status randqr_sketch_static(const double *V, int64_t m, int64_t n, int64_t ldv,
+                                              int64_t s1, int64_t s2, uint64_t seed,
+                                              const double *S2, double *Ws, void *stream) {
+  if (!V || !S2 || !Ws || n < 1 || m < 1 || ldv < n || s2 < n || s1 < s2 ||
+      s1 >= (int64_t(1) << 31) || s1 * n > kStaticW1Max)
+    return RANDQR_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  StaticSlot slot;
+  if (static_slot(dev, &slot) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // W1 and Ws accumulate with atomics and the status word gates the kernels: all three
+  // must start at zero on every call (the array keeps the previous call's contents).
+  if (cudaMemsetAsync(slot.status, 0, sizeof(rq::DevStatus), s) != cudaSuccess ||
+      cudaMemsetAsync(slot.w1, 0, sizeof(double) * (size_t)(s1 * n), s) != cudaSuccess ||
+      cudaMemsetAsync(Ws, 0, sizeof(double) * (size_t)(s2 * n), s) != cudaSuccess ||
+      rq::launch_cs_scatter(V, m, n, ldv, s1, seed, slot.w1, slot.num_sms, slot.status, s) !=
+          cudaSuccess ||
+      rq::launch_sketch_gemm(S2, slot.w1, s2, s1, n, Ws, slot.num_sms, slot.status, s) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  return RANDQR_OK;
+}
