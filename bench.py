@@ -42,6 +42,11 @@ def parse():
     p.add_argument("--prec", default="fp64", choices=["fp64", "f32x2"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, baselines, CPU baseline (quick runs)")
+    p.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
+    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--gen", default="qr", choices=["qr", "gauss"],
+                   help="qr: V = U diag(sigma) W^T; gauss: plain N(0,1/m) entries (kappa ~ 1, "
+                        "no QR in the generator -- for profiler runs)")
     return p.parse_args()
 
 
@@ -150,6 +155,116 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------------------------------
+# Served stream: Poisson arrivals of requests through randqr_submit / randqr_poll
+# ---------------------------------------------------------------------------------------
+def serve_bench(rq, synthetic, torch, dev, n_req=200, load=0.8, seed=7):
+    """Requests with m log-uniform in [1e4, 4e6], n uniform in {4, 8, 16, 32, 64}, kappa
+    log-uniform in [1, 1e12] (one pre-built matrix per (n, kappa level), requests take its
+    first m rows).  Service capacity is first measured with sequential plain-FP64 solves;
+    arrivals are then Poisson at `load` x that capacity.  Reports p50/p99 latency and
+    throughput of the served path (FP64, and with max_orth_err = 1e-12, which lets rand_cholQR
+    run its row passes in pair arithmetic), next to sequential plain-FP64 solves of the same
+    stream (single FIFO server; latency from the same arrival times)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ns = [4, 8, 16, 32, 64]
+    klev = [1.0, 1e4, 1e8, 1e12]
+    pools = {(n, k): synthetic.make_v_torch(4_000_000, n, k, seed=100 + n, device=dev)
+             for n in ns for k in klev}
+    reqs = []
+    for _ in range(n_req):
+        m = int(np.exp(rng.uniform(np.log(1e4), np.log(4e6))))
+        n = int(rng.choice(ns))
+        k = klev[min(3, int(rng.uniform(0, 12) // 3))]
+        reqs.append((m, n, k))
+    outs = {}
+    for (m, n, k) in reqs:
+        if (m, n) not in outs:
+            outs[(m, n)] = (torch.empty((m, n), dtype=torch.float64, device=dev),
+                            torch.empty((n, n), dtype=torch.float64, device=dev))
+    ctx = rq.Context(dev.index or 0)
+    # sequential plain FP64: per-request service time (S2 cached first, untimed)
+    for (m, n, k) in reqs:
+        rq.randqr_factor(pools[(n, k)][:m], seed=0, ctx=ctx, Q=outs[(m, n)][0], R=outs[(m, n)][1])
+    svc = []
+    for (m, n, k) in reqs:
+        Q, R = outs[(m, n)]
+        t0 = time.perf_counter()
+        rq.randqr_factor(pools[(n, k)][:m], seed=0, ctx=ctx, Q=Q, R=R)  # waits for the status
+        svc.append(time.perf_counter() - t0)
+    mean_svc = float(np.mean(svc))
+    rate = load / mean_svc
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    # sequential FIFO server latencies for the same arrivals
+    free_at, seq_lat = 0.0, []
+    for a, s in zip(arrivals, svc):
+        start = max(a, free_at)
+        free_at = start + s
+        seq_lat.append(free_at - a)
+
+    def run_served(max_orth):
+        sctx = rq.Context(dev.index or 0)
+        rq.randqr_serve_config(sctx, slots=8, hbm_budget_bytes=64 << 30)
+        # warm the slots' workspaces and the sketch cache with the largest shapes
+        for (m, n, k) in sorted(set(reqs), key=lambda r: -r[0] * r[1])[:16]:
+            Q, R = outs[(m, n)]
+            t, _ = rq.randqr_submit(sctx, pools[(n, k)][:m], Q=Q, R=R, seed=0, max_orth_err=max_orth)
+            rq.randqr_wait(sctx, t)
+        torch.cuda.synchronize()
+        lat, pending, nxt = [], {}, 0
+        qbuf = [(torch.empty((m, n), dtype=torch.float64, device=dev),
+                 torch.empty((n, n), dtype=torch.float64, device=dev)) for (m, n, k) in reqs]
+        t0 = time.perf_counter()
+        while len(lat) < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                m, n, k = reqs[nxt]
+                Q, R = qbuf[nxt]
+                t, _ = rq.randqr_submit(sctx, pools[(n, k)][:m], Q=Q, R=R, seed=0, max_orth_err=max_orth)
+                pending[t] = nxt
+                nxt += 1
+            for t in list(pending):
+                st, _ = rq.randqr_poll(sctx, t)
+                if st != rq.PENDING:
+                    if st != 0:
+                        raise rq.RandQRError(st)
+                    lat.append(time.perf_counter() - t0 - arrivals[pending.pop(t)])
+            if not pending and nxt < n_req:
+                time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
+        makespan = time.perf_counter() - t0
+        worst = 0.0
+        for i in range(0, n_req, max(1, n_req // 16)):
+            Q, R = qbuf[i]
+            G = Q.T @ Q
+            worst = max(worst, torch.linalg.matrix_norm(G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
+        sctx.close()
+        del qbuf
+        return lat, makespan, worst
+
+    def pct(x, p):
+        return float(np.percentile(np.asarray(x) * 1e3, p))
+
+    lat64, span64, orth64 = run_served(0.0)
+    latmx, spanmx, orthmx = run_served(1e-12)
+    bytes_total = sum(32.0 * m * n for (m, n, k) in reqs)
+    res = {"requests": n_req, "offered_load": load, "rate_per_s": rate, "slots": 8,
+           "budget_bytes": 64 << 30,
+           "workload": "m log-uniform [1e4, 4e6], n in {4,8,16,32,64}, kappa in {1,1e4,1e8,1e12}",
+           "sequential_fp64": {"p50_ms": pct(seq_lat, 50), "p99_ms": pct(seq_lat, 99),
+                               "mean_service_ms": mean_svc * 1e3,
+                               "throughput_req_s": 1.0 / mean_svc},
+           "served_fp64": {"p50_ms": pct(lat64, 50), "p99_ms": pct(lat64, 99),
+                           "throughput_req_s": n_req / span64,
+                           "eff_GBs": bytes_total / span64 / 1e9, "max_orth_err_2": orth64},
+           "served_mixed": {"p50_ms": pct(latmx, 50), "p99_ms": pct(latmx, 99),
+                            "throughput_req_s": n_req / spanmx,
+                            "eff_GBs": bytes_total / spanmx / 1e9, "max_orth_err_2": orthmx}}
+    ctx.close()
+    del pools, outs
+    return res
+
+
+# ---------------------------------------------------------------------------------------
 def main():
     a = parse()
     if a.impl == "reference":
@@ -170,7 +285,12 @@ def main():
     s1, s2 = synthetic.default_sketch_sizes(n)
     prec = rq.FP64 if a.prec == "fp64" else rq.F32X2
     dev = torch.device("cuda", local_rank)
-    V = synthetic.make_v_torch(m, n, a.kappa, seed=rank, device=dev)
+    if a.gen == "qr":
+        V = synthetic.make_v_torch(m, n, a.kappa, seed=rank, device=dev)
+    else:
+        g = torch.Generator(device=dev)
+        g.manual_seed(rank)
+        V = torch.randn((m, n), generator=g, device=dev, dtype=torch.float64) / m ** 0.5
     Q = torch.empty_like(V)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     ctx = rq.Context(local_rank)
@@ -316,6 +436,10 @@ def main():
                                 "rand_cholqr_over_cholqr2": times["rand_cholqr"] / times["cholqr2"],
                                 "rand_cholqr_over_shifted_cholqr3": times["rand_cholqr"] / times["shifted_cholqr3"]}
         del Vb
+        if not a.no_serve:
+            del Q
+            torch.cuda.empty_cache()
+            line["serving"] = serve_bench(rq, synthetic, torch, dev, n_req=a.serve_requests)
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18)
 

@@ -185,6 +185,59 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
                                      int64_t ldv, double *Q, int64_t ldq, double *R,
                                      int64_t ldr, randqr_info *info, void *stream);
 
+/* ---- Serving: continuous batching of factorization requests ---------------------------
+ * The paper has no serving layer; these calls run its Algorithms 3 and 4 (and shifted
+ * CholeskyQR3) as requests.  A context's server owns `slots` CUDA streams, each with its own
+ * workspace, so admitted requests overlap on the device.  Requests are admitted in FIFO
+ * order as soon as a slot is free and their footprint (V, Q, R and workspace bytes) fits
+ * the HBM budget beside everything in flight; a request larger than the whole budget is
+ * refused at submit with RANDQR_ERR_ADMISSION.  Gaussian sketches are generated once per
+ * (seed + 1, s1, s2) and shared by all slots.  Submit and poll never block on the device
+ * (except the first use of a sketch shape, which generates it); randqr_wait blocks.  The
+ * caller keeps V, Q and R alive and untouched until poll/wait returns a status other than
+ * RANDQR_PENDING; the ticket is retired by that call.  Single host thread per context. */
+typedef enum {
+  RANDQR_ALGO_RAND_CHOLQR = 0,
+  RANDQR_ALGO_CHOLQR2 = 1,
+  RANDQR_ALGO_SHIFTED_CHOLQR3 = 2
+} randqr_algo;
+
+typedef struct {
+  int32_t algo;        /* randqr_algo */
+  int32_t prec;        /* randqr_precision of rand_cholQR's row passes */
+  const double *V;     /* m x n, row-major, ldv (device) */
+  int64_t m, n, ldv;
+  int64_t s1, s2;      /* rand_cholQR sketch sizes; 0 selects 2(n^2+n) and 4n */
+  uint64_t seed;       /* CountSketch seed; S2 uses seed + 1 */
+  double *Q;           /* m x n, ldq (device); may equal V with ldq == ldv */
+  int64_t ldq;
+  double *R;           /* n x n, ldr (device) */
+  int64_t ldr;
+  double max_orth_err; /* loss of orthogonality the caller accepts; with prec = RANDQR_FP64
+                          and a value >= 1e-12 rand_cholQR may run its row passes as
+                          RANDQR_F32X2, whose results meet ||I - Q^T Q||_2 <= 1e-12 and
+                          ||V - QR||_F/||V||_F <= 1e-13 in this library's tests; 0 = FP64 */
+} randqr_request;
+
+typedef struct {
+  uint64_t submitted, completed, queued, running;
+  size_t bytes_in_flight;
+  int32_t slots;
+  size_t budget;
+} randqr_serve_stats;
+
+/* (Re)configure the server: number of slots (1..256) and HBM budget in bytes (0 = 64 GiB).
+ * Only while nothing is queued or running.  Without this call the first submit creates a
+ * server with 8 slots and the context's budget (64 GiB if that is 0). */
+randqr_status randqr_serve_config(randqr_ctx *ctx, int32_t slots, size_t hbm_budget_bytes);
+randqr_status randqr_submit(randqr_ctx *ctx, const randqr_request *req, uint64_t *ticket);
+randqr_status randqr_submit_batch(randqr_ctx *ctx, const randqr_request *reqs, int32_t count,
+                                  uint64_t *tickets);
+/* RANDQR_PENDING while queued or running; else the request's status (and *info). */
+randqr_status randqr_poll(randqr_ctx *ctx, uint64_t ticket, randqr_info *info);
+randqr_status randqr_wait(randqr_ctx *ctx, uint64_t ticket, randqr_info *info);
+randqr_status randqr_serve_stats_get(randqr_ctx *ctx, randqr_serve_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

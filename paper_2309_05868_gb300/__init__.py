@@ -300,3 +300,113 @@ def get_status(ctx, stream=None):
     info = Info()
     st = _load().randqr_get_status(ctx.handle, _stream(stream), _ct.byref(info))
     return st, info
+
+
+# ---------------------------------------------------------------------------------------
+# Serving: randqr_submit / randqr_poll (continuous batching over the context's slots).
+# ---------------------------------------------------------------------------------------
+ALGO_RAND_CHOLQR, ALGO_CHOLQR2, ALGO_SHIFTED_CHOLQR3 = 0, 1, 2
+PENDING = 1
+
+
+class Request(_ct.Structure):
+    _fields_ = [("algo", _ct.c_int32), ("prec", _ct.c_int32), ("V", _ct.c_void_p),
+                ("m", _ct.c_int64), ("n", _ct.c_int64), ("ldv", _ct.c_int64),
+                ("s1", _ct.c_int64), ("s2", _ct.c_int64), ("seed", _ct.c_uint64),
+                ("Q", _ct.c_void_p), ("ldq", _ct.c_int64), ("R", _ct.c_void_p),
+                ("ldr", _ct.c_int64), ("max_orth_err", _ct.c_double)]
+
+
+class ServeStats(_ct.Structure):
+    _fields_ = [("submitted", _ct.c_uint64), ("completed", _ct.c_uint64),
+                ("queued", _ct.c_uint64), ("running", _ct.c_uint64),
+                ("bytes_in_flight", _ct.c_size_t), ("slots", _ct.c_int32),
+                ("budget", _ct.c_size_t)]
+
+
+def _serve_sigs(L):
+    if getattr(L, "_serve_ready", False):
+        return L
+    vp, i32 = _ct.c_void_p, _ct.c_int32
+    for name, args in {
+        "randqr_serve_config": [vp, i32, _ct.c_size_t],
+        "randqr_submit": [vp, _ct.POINTER(Request), _ct.POINTER(_ct.c_uint64)],
+        "randqr_submit_batch": [vp, _ct.POINTER(Request), i32, _ct.POINTER(_ct.c_uint64)],
+        "randqr_poll": [vp, _ct.c_uint64, _ct.POINTER(Info)],
+        "randqr_wait": [vp, _ct.c_uint64, _ct.POINTER(Info)],
+        "randqr_serve_stats_get": [vp, _ct.POINTER(ServeStats)],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L._serve_ready = True
+    return L
+
+
+_inflight = {}  # (context handle, ticket) -> tensors kept alive until the ticket retires
+
+
+def make_request(V, Q=None, R=None, algo=ALGO_RAND_CHOLQR, prec=FP64, s1=0, s2=0, seed=0,
+                 max_orth_err=0.0):
+    """A randqr_request over torch tensors (Q, R allocated if not given)."""
+    ldv = _check_mat(V, "V")
+    Q, R, ldq, ldr = _alloc_qr(V, Q, R)
+    m, n = V.shape
+    r = Request(algo, prec, V.data_ptr(), m, n, ldv, s1, s2, seed, Q.data_ptr(), ldq,
+                R.data_ptr(), ldr, max_orth_err)
+    return r, (V, Q, R)
+
+
+def randqr_serve_config(ctx, slots=8, hbm_budget_bytes=0):
+    ctx._check(_serve_sigs(_load()).randqr_serve_config(ctx.handle, slots, hbm_budget_bytes))
+
+
+def randqr_submit(ctx, V, Q=None, R=None, **kw):
+    """Submit one request; returns (ticket, (V, Q, R))."""
+    L = _serve_sigs(_load())
+    req, keep = make_request(V, Q, R, **kw)
+    t = _ct.c_uint64(0)
+    st = L.randqr_submit(ctx.handle, _ct.byref(req), _ct.byref(t))
+    if st != 0:
+        raise RandQRError(st)
+    _inflight[(ctx.handle.value, t.value)] = keep
+    return t.value, keep
+
+
+def randqr_submit_batch(ctx, requests):
+    """requests: list of (Request, keep) from make_request; returns the tickets."""
+    L = _serve_sigs(_load())
+    arr = (Request * len(requests))(*[r for r, _ in requests])
+    tickets = (_ct.c_uint64 * len(requests))()
+    st = L.randqr_submit_batch(ctx.handle, arr, len(requests), tickets)
+    if st != 0:
+        raise RandQRError(st)
+    for (r, keep), t in zip(requests, tickets):
+        _inflight[(ctx.handle.value, t)] = keep
+    return list(tickets)
+
+
+def _retire(ctx, ticket, st):
+    if st != PENDING:
+        _inflight.pop((ctx.handle.value, ticket), None)
+
+
+def randqr_poll(ctx, ticket):
+    """(status, Info): status 1 (PENDING) while queued or running."""
+    info = Info()
+    st = _serve_sigs(_load()).randqr_poll(ctx.handle, ticket, _ct.byref(info))
+    _retire(ctx, ticket, st)
+    return st, info
+
+
+def randqr_wait(ctx, ticket):
+    info = Info()
+    st = _serve_sigs(_load()).randqr_wait(ctx.handle, ticket, _ct.byref(info))
+    _retire(ctx, ticket, st)
+    return st, info
+
+
+def randqr_serve_stats_get(ctx):
+    s = ServeStats()
+    ctx._check(_serve_sigs(_load()).randqr_serve_stats_get(ctx.handle, _ct.byref(s)))
+    return {f: getattr(s, f) for f, _ in ServeStats._fields_}

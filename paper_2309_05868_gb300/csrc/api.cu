@@ -86,8 +86,9 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
                         align_up(sizeof(double) * (size_t)(s2 * n)),
                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
-                        align_up(sizeof(double) * packed(n)), align_up(sizeof(float2) * packed(n)),
-                        align_up(sizeof(float2) * (size_t)n)};
+                        align_up(sizeof(double) * packed(n)),
+                        align_up(sizeof(float2) * rq::pack_df_elems(n)),
+                        align_up(sizeof(float2) * rq::pack_df_rinv_elems(n))};
   size_t total = 0;
   for (size_t b : sz) total += b;
   randqr_status st = ensure_ws(ctx, total);
@@ -246,6 +247,7 @@ randqr_status randqr_create(randqr_ctx **ctx_out, int device, size_t hbm_budget_
 randqr_status randqr_destroy(randqr_ctx *ctx) {
   if (!ctx) return RANDQR_ERR_ARG;
   cudaSetDevice(ctx->device);
+  rq_server_destroy(ctx);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->s2_buf) cudaFree(ctx->s2_buf);

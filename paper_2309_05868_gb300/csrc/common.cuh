@@ -119,7 +119,12 @@ struct randqr_ctx {
   };
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;
+  // request server (randqr_submit / randqr_poll), created on first use
+  struct randqr_server *server = nullptr;
 };
+
+// Tear down a context's request server (waits for its streams).
+void rq_server_destroy(randqr_ctx *ctx);
 
 namespace rq {
 // Kernel kinds for the per-kernel timing record.
@@ -154,6 +159,8 @@ cudaError_t launch_gram(const double *W, int64_t ldw, int64_t m, int64_t n, doub
                         randqr_precision prec, int num_sms, const DevStatus *st,
                         cudaStream_t s);
 // double-float (RANDQR_F32X2) row passes
+size_t pack_df_elems(int64_t n);       // float2 entries of the blocked pair form of R
+size_t pack_df_rinv_elems(int64_t n);  // float2 entries of the padded 1/r_jj
 cudaError_t launch_pack_df(const double *Rp, int64_t n, float2 *Rdf, float2 *rinv,
                            const DevStatus *st, cudaStream_t s);
 cudaError_t launch_trsm_df(const void *X, bool x_f64, int64_t ldx, void *Y, bool y_f64,

@@ -98,6 +98,31 @@ __device__ __forceinline__ void df_fma(float &sh, float &sl, float2 a, float2 b)
   sh = t;
 }
 
+// s[c] -= a * b[c] for c < N, written stage by stage across the N independent updates so
+// their dependent chains interleave (same arithmetic as N calls of df_fms).
+template <int N>
+__device__ __forceinline__ void df_fms_n(float (&sh)[N], float (&sl)[N], float2 a, const float2 (&b)[N]) {
+  float p[N], e[N], t[N], z[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) p[c] = a.x * b[c].x;
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a.x, b[c].x, -p[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) t[c] = __fsub_rn(sh[c], p[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a.x, b[c].y, e[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) z[c] = __fsub_rn(t[c], sh[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a.y, b[c].x, e[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const float err = __fadd_rn(__fsub_rn(sh[c], __fsub_rn(t[c], z[c])), __fsub_rn(-p[c], z[c]));
+    sl[c] = __fadd_rn(__fsub_rn(sl[c], e[c]), err);
+    sh[c] = t[c];
+  }
+}
+
 __device__ __forceinline__ float2 df_norm(float sh, float sl) {
   const float h = __fadd_rn(sh, sl);
   return make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
@@ -113,18 +138,41 @@ __device__ __forceinline__ float2 df_mul(float sh, float sl, float2 r) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Triangular factor in pair form: packed upper R and 1/r_jj, from the FP64 packed factor.
+// Triangular factor in pair form, in column blocks of DF_JB: n is padded to n_pad (a
+// multiple of DF_JB) and block b (columns 8b .. 8b+7) stores, for every row k < 8b + 8, its
+// DF_JB entries contiguously: Rb[32 b (b+1) + 8 k + c] = R(k, 8b + c), zero where k > 8b + c
+// or the column is padding.  rinv[j] = 1/r_jj, zero on padding, so padded columns solve to
+// zero without a branch.
 // ---------------------------------------------------------------------------------------
-__global__ void k_pack_df(const double *Rp, int n, float2 *Rdf, float2 *rinv, const DevStatus *st) {
+constexpr int DF_JB = 8;
+
+__host__ __device__ __forceinline__ int df_npad(int n) { return (n + DF_JB - 1) / DF_JB * DF_JB; }
+__host__ __device__ __forceinline__ int df_block_off(int b) { return DF_JB * DF_JB / 2 * b * (b + 1); }
+__host__ __device__ __forceinline__ int df_rb_size(int n) {
+  const int nb = df_npad(n) / DF_JB;
+  return df_block_off(nb);
+}
+
+__global__ void k_pack_df(const double *Rp, int n, float2 *Rb, float2 *rinv, const DevStatus *st) {
   if (status_failed(st)) return;
-  const int P = n * (n + 1) / 2;
-  for (int e = threadIdx.x; e < P; e += blockDim.x) Rdf[e] = d2df(Rp[e]);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rinv[j] = d2df(1.0 / Rp[tri_idx(j, j)]);
+  const int np = df_npad(n), total = df_rb_size(n);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int b = 0;
+    while (df_block_off(b + 1) <= e) ++b;
+    const int local = e - df_block_off(b);
+    const int k = local / DF_JB, j = DF_JB * b + local % DF_JB;
+    Rb[e] = (j < n && k <= j) ? d2df(Rp[tri_idx(k, j)]) : make_float2(0.f, 0.f);
+  }
+  for (int j = threadIdx.x; j < np; j += blockDim.x)
+    rinv[j] = (j < n) ? d2df(1.0 / Rp[tri_idx(j, j)]) : make_float2(0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------------------
-// Y = X R^{-1} per row by forward substitution in pair arithmetic, one thread per row, two
-// independent partial sums (even / odd k) per dot product to overlap the dependent chains.
+// Y = X R^{-1} per row by forward substitution in pair arithmetic, one thread per row.
+// Columns go in blocks of DF_JB: every w_k already solved is loaded once and feeds DF_JB
+// independent accumulators (the block's R entries for that k arrive as four 16-byte
+// broadcasts); the DF_JB x DF_JB diagonal block is then finished in registers.  For each
+// column the terms are taken in ascending k, as in the row-wise solve.
 // IN_F64: X is FP64 (else pairs); OUT_F64: Y is FP64 (else pairs).  X and Y may alias.
 // ---------------------------------------------------------------------------------------
 constexpr int DF_ROWS = 128;
@@ -135,44 +183,65 @@ __global__ void __launch_bounds__(DF_ROWS) k_trsm_df(const void *X, int64_t ldx,
                                                      const float2 *__restrict__ rinvg,
                                                      const DevStatus *st) {
   if (status_failed(st)) return;
-  extern __shared__ float2 smf[];
-  const int P = n * (n + 1) / 2;
-  const int ld = (n & 1) ? n : n + 1;
-  float2 *R = smf;
-  float2 *rinv = R + P;
-  float2 *T = rinv + n;
+  extern __shared__ float4 smf4[];
+  const int np = df_npad(n), RB = df_rb_size(n);
+  const int ld = np + 1;  // odd stride in 8-byte words
+  float2 *Rb = (float2 *)smf4;
+  float2 *rinv = Rb + RB;
+  float2 *T = rinv + np;
   const int tid = threadIdx.x;
-  for (int e = tid; e < P; e += blockDim.x) R[e] = Rg[e];
-  for (int j = tid; j < n; j += blockDim.x) rinv[j] = rinvg[j];
+  for (int e = tid; e < RB; e += blockDim.x) Rb[e] = Rg[e];
+  for (int j = tid; j < np; j += blockDim.x) rinv[j] = rinvg[j];
   __syncthreads();
   for (int64_t row0 = (int64_t)blockIdx.x * DF_ROWS; row0 < m; row0 += (int64_t)gridDim.x * DF_ROWS) {
     const int rows = (int)imin64(DF_ROWS, m - row0);
-    for (int e = tid; e < rows * n; e += blockDim.x) {
-      const int r = e / n, c = e - r * n;
-      if (IN_F64)
-        T[r * ld + c] = d2df(((const double *)X)[(row0 + r) * ldx + c]);
-      else
-        T[r * ld + c] = ((const float2 *)X)[(row0 + r) * ldx + c];
+    for (int e = tid; e < rows * np; e += blockDim.x) {
+      const int r = e / np, c = e - r * np;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < n) {
+        if (IN_F64)
+          v = d2df(((const double *)X)[(row0 + r) * ldx + c]);
+        else
+          v = ((const float2 *)X)[(row0 + r) * ldx + c];
+      }
+      T[r * ld + c] = v;
     }
     __syncthreads();
     if (tid < rows) {
       float2 *w = T + tid * ld;
-      for (int j = 0; j < n; ++j) {
-        const float2 *rc = R + j * (j + 1) / 2;
-        float ah = w[j].x, al = w[j].y, bh = 0.f, bl = 0.f;
-        int k = 0;
-        for (; k + 1 < j; k += 2) {
-          df_fms(ah, al, w[k], rc[k]);
-          df_fms(bh, bl, w[k + 1], rc[k + 1]);
+      for (int b = 0; b < np / DF_JB; ++b) {
+        const int j0 = DF_JB * b;
+        const float4 *rb = (const float4 *)(Rb + df_block_off(b));  // 2 entries per float4
+        float ah[DF_JB], al[DF_JB];
+#pragma unroll
+        for (int c = 0; c < DF_JB; ++c) {
+          ah[c] = w[j0 + c].x;
+          al[c] = w[j0 + c].y;
         }
-        if (k < j) df_fms(ah, al, w[k], rc[k]);
-        // combine the two partial sums: (ah + al) + (bh + bl)
-        const float t = __fadd_rn(ah, bh);
-        const float z = __fsub_rn(t, ah);
-        const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(t, z)), __fsub_rn(bh, z));
-        const float l = __fadd_rn(__fadd_rn(al, bl), err);
-        const float2 s = df_norm(t, l);
-        w[j] = df_mul(s.x, s.y, rinv[j]);
+        for (int k = 0; k < j0; ++k) {
+          const float2 wk = w[k];
+          float2 r[DF_JB];
+#pragma unroll
+          for (int q = 0; q < DF_JB / 2; ++q) {
+            const float4 v = rb[k * (DF_JB / 2) + q];
+            r[2 * q] = make_float2(v.x, v.y);
+            r[2 * q + 1] = make_float2(v.z, v.w);
+          }
+          df_fms_n<DF_JB>(ah, al, wk, r);
+        }
+        float2 wl[DF_JB];
+#pragma unroll
+        for (int c = 0; c < DF_JB; ++c) {
+#pragma unroll
+          for (int cc = 0; cc < c; ++cc) {
+            const float2 rr = ((const float2 *)rb)[(j0 + cc) * DF_JB + c];
+            df_fms(ah[c], al[c], wl[cc], rr);
+          }
+          const float2 sn = df_norm(ah[c], al[c]);
+          wl[c] = df_mul(sn.x, sn.y, rinv[j0 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < DF_JB; ++c) w[j0 + c] = wl[c];
       }
     }
     __syncthreads();
@@ -200,7 +269,10 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
   if (status_failed(st)) return;
   __shared__ float2 T[DFG_TILE * 132];
   const int nb = (n + 3) / 4;
-  const int ld = 4 * nb + 1;  // padded row, odd stride in 8-byte words
+  // Row r keeps column c at r*ld + (c % 4)*nb + c / 4, so the 4 entries a thread reads
+  // for its block (c = 4*kb + a) sit nb apart and neighbouring threads' kb hit distinct
+  // banks; the odd row stride spreads rows.
+  const int ld = 4 * nb + 1;
   const int tid = threadIdx.x;
   const int nblk = nb * (nb + 1) / 2;
   int jb = 0, kb = 0;
@@ -221,9 +293,10 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
   for (int64_t row0 = r_begin; row0 < r_end; row0 += DFG_TILE) {
     const int rows = (int)imin64(DFG_TILE, r_end - row0);
     __syncthreads();
-    for (int e = tid; e < rows * ld; e += blockDim.x) {
-      const int r = e / ld, c = e - r * ld;
-      T[e] = (c < n) ? W[(row0 + r) * ldw + c] : make_float2(0.f, 0.f);
+    const int wpr = 4 * nb;  // padded entries per row
+    for (int e = tid; e < rows * wpr; e += blockDim.x) {
+      const int r = e / wpr, c = e - r * wpr;
+      T[r * ld + (c & 3) * nb + (c >> 2)] = (c < n) ? W[(row0 + r) * ldw + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (active) {
@@ -231,7 +304,7 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
         const float2 *t = T + r * ld;
         float2 x[4], y[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) { x[a] = t[4 * kb + a]; y[a] = t[4 * jb + a]; }
+        for (int a = 0; a < 4; ++a) { x[a] = t[a * nb + kb]; y[a] = t[a * nb + jb]; }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -249,6 +322,9 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
     }
 }
 
+size_t pack_df_elems(int64_t n) { return (size_t)df_rb_size((int)n); }
+size_t pack_df_rinv_elems(int64_t n) { return (size_t)df_npad((int)n); }
+
 cudaError_t launch_pack_df(const double *Rp, int64_t n, float2 *Rdf, float2 *rinv,
                            const DevStatus *st, cudaStream_t s) {
   k_pack_df<<<1, 256, 0, s>>>(Rp, (int)n, Rdf, rinv, st);
@@ -258,8 +334,8 @@ cudaError_t launch_pack_df(const double *Rp, int64_t n, float2 *Rdf, float2 *rin
 cudaError_t launch_trsm_df(const void *X, bool x_f64, int64_t ldx, void *Y, bool y_f64, int64_t ldy,
                            int64_t m, int64_t n, const float2 *Rdf, const float2 *rinv, int num_sms,
                            const DevStatus *st, cudaStream_t s) {
-  const int ld = (n & 1) ? (int)n : (int)n + 1;
-  const size_t smem = sizeof(float2) * ((size_t)(n * (n + 1) / 2) + n + (size_t)DF_ROWS * ld);
+  const int np = df_npad((int)n);
+  const size_t smem = sizeof(float2) * ((size_t)df_rb_size((int)n) + np + (size_t)DF_ROWS * (np + 1));
   int per_sm = std::max(1, (int)((220 * 1024) / smem));
   per_sm = std::min(per_sm, 8);
   const int64_t tiles = ceil_div(m, DF_ROWS);

@@ -1,0 +1,135 @@
+"""Serving path (randqr_submit / randqr_poll): continuous batching over the context's slots.
+
+Checked through the C ABI: every request of a mixed stream completes with the accuracy the
+direct call has; a request's result is the same alone and inside a mix; admission keeps the
+bytes in flight under the HBM budget and refuses requests that can never fit; a failing
+request does not disturb the others; tickets retire once."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from gpu_util import parity_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rq():
+    import paper_2309_05868_gb300 as rq
+    return rq
+
+
+def _V(m, n, kappa, seed):
+    return torch.from_numpy(synthetic.make_v(m, n, kappa, seed=seed)).cuda()
+
+
+def _drain(rq, ctx, tickets, timeout=120.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            st, info = rq.randqr_poll(ctx, t)
+            if st != rq.PENDING:
+                out[t] = (st, info)
+        assert time.time() - t0 < timeout, "requests did not finish"
+    return out
+
+
+MIX = [  # m, n, kappa, algo, prec, max_orth_err
+    (20000, 16, 1e10, 0, 0, 0.0), (5000, 4, 1e3, 0, 0, 0.0), (60000, 64, 1e12, 0, 0, 0.0),
+    (30000, 32, 1e6, 1, 0, 0.0), (30000, 32, 1e9, 2, 0, 0.0), (12345, 8, 1e14, 0, 0, 0.0),
+    (40000, 64, 1e8, 0, 1, 0.0), (25000, 16, 1e4, 0, 0, 1e-12), (7000, 128, 1e6, 0, 0, 0.0),
+    (50000, 8, 1e2, 1, 0, 0.0), (20000, 33, 1e11, 0, 0, 1e-12), (9000, 5, 1.0, 2, 0, 0.0),
+]
+
+
+def test_mixed_stream_completes_accurately(rq):
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=4)
+    subs = []
+    for i, (m, n, kappa, algo, prec, tol) in enumerate(MIX):
+        V = _V(m, n, kappa, seed=i)
+        t, keep = rq.randqr_submit(ctx, V, algo=algo, prec=prec, seed=i, max_orth_err=tol)
+        subs.append((t, keep))
+    res = _drain(rq, ctx, [t for t, _ in subs])
+    for (t, (V, Q, R)), (m, n, kappa, algo, prec, tol) in zip(subs, MIX):
+        st, _ = res[t]
+        assert st == 0, (m, n, kappa, algo, st)
+        Vh, Qh, Rh = V.cpu().numpy(), Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.orth_err(Qh)[0] <= 1e-12
+        assert oracle.resid(Vh, Qh, Rh) <= 1e-13
+    stats = rq.randqr_serve_stats_get(ctx)
+    assert stats["completed"] == len(MIX) and stats["queued"] == 0 and stats["running"] == 0
+    ctx.close()
+
+
+def test_result_alone_equals_result_in_mix(rq):
+    m, n, kappa = 30000, 24, 1e7
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    Vh = synthetic.make_v(m, n, kappa, seed=42)
+    V = torch.from_numpy(Vh).cuda()
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=6)
+    t, (_, Qa, Ra) = rq.randqr_submit(ctx, V, seed=5)
+    assert rq.randqr_wait(ctx, t)[0] == 0
+    others = [rq.randqr_submit(ctx, _V(40000, nn, 1e9, seed=nn), seed=nn)
+              for nn in (8, 16, 32, 64, 4, 48)]
+    t2, (_, Qb, Rb) = rq.randqr_submit(ctx, V, seed=5)
+    others += [rq.randqr_submit(ctx, _V(20000, nn, 1e3, seed=nn + 1), seed=nn)
+               for nn in (12, 20, 64)]
+    res = _drain(rq, ctx, [t2] + [o[0] for o in others])
+    assert all(st == 0 for st, _ in res.values())
+    tq, tr = parity_tolerance(Vh, s1, s2)
+    Qa, Qb, Ra, Rb = Qa.cpu().numpy(), Qb.cpu().numpy(), Ra.cpu().numpy(), Rb.cpu().numpy()
+    assert np.abs(Qa - Qb).max() <= tq
+    assert np.abs(Ra - Rb).max() / np.abs(Ra).max() <= tr
+    ctx.close()
+
+
+def test_admission_respects_budget(rq):
+    budget = 64 << 20
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=8, hbm_budget_bytes=budget)
+    subs = [rq.randqr_submit(ctx, _V(150000, 8, 1e4, seed=i), seed=i) for i in range(10)]
+    # each request holds ~19.2 MB (V, Q, R, workspace): at most 3 fit in 64 MiB
+    peak, done = 0, {}
+    t0 = time.time()
+    while len(done) < len(subs):
+        s = rq.randqr_serve_stats_get(ctx)
+        peak = max(peak, s["bytes_in_flight"])
+        assert s["running"] <= 3
+        for t, _ in subs:
+            if t not in done:
+                st, _ = rq.randqr_poll(ctx, t)
+                if st != rq.PENDING:
+                    done[t] = st
+        assert time.time() - t0 < 120
+    assert all(st == 0 for st in done.values())
+    assert 0 < peak <= budget
+    big = torch.zeros((2_000_000, 8), dtype=torch.float64, device="cuda")  # 128 MB > budget
+    with pytest.raises(rq.RandQRError) as e:
+        rq.randqr_submit(ctx, big)
+    assert e.value.name == "ERR_ADMISSION"
+    ctx.close()
+
+
+def test_failure_is_isolated_and_tickets_retire(rq):
+    ctx = rq.Context(0)
+    bad = _V(30000, 32, 1e13, seed=1)
+    good = [_V(30000, 32, 1e3, seed=s) for s in range(3)]
+    tb, _ = rq.randqr_submit(ctx, bad, algo=rq.ALGO_CHOLQR2)
+    tg = [rq.randqr_submit(ctx, g, seed=i)[0] for i, g in enumerate(good)]
+    st, info = rq.randqr_wait(ctx, tb)
+    if st != 0:
+        assert st == -2 and info.info >= 1
+    for t in tg:
+        assert rq.randqr_wait(ctx, t)[0] == 0
+    assert rq.randqr_poll(ctx, tg[0])[0] == -9  # retired
+    assert rq.randqr_poll(ctx, 123456789)[0] == -9
+    ctx.close()
