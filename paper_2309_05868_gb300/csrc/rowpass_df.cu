@@ -123,6 +123,47 @@ __device__ __forceinline__ void df_fms_n(float (&sh)[N], float (&sl)[N], float2 
   }
 }
 
+// s[c] -= a[c] * b[c] for c < N, stage by stage across the N independent updates.
+template <int N>
+__device__ __forceinline__ void df_fms_nn(float (&sh)[N], float (&sl)[N], const float2 (&a)[N],
+                                          const float2 (&b)[N]) {
+  float p[N], e[N], t[N], z[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) p[c] = a[c].x * b[c].x;
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a[c].x, b[c].x, -p[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) t[c] = __fsub_rn(sh[c], p[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a[c].x, b[c].y, e[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) z[c] = __fsub_rn(t[c], sh[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) e[c] = __fmaf_rn(a[c].y, b[c].x, e[c]);
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const float err = __fadd_rn(__fsub_rn(sh[c], __fsub_rn(t[c], z[c])), __fsub_rn(-p[c], z[c]));
+    sl[c] = __fadd_rn(__fsub_rn(sl[c], e[c]), err);
+    sh[c] = t[c];
+  }
+}
+
+// (ah + al) += (bh + bl), accurate pair addition (two TwoSums, renormalised).
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float v = __fsub_rn(s, ah);
+  float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(bh, v));
+  const float t = __fadd_rn(al, bl);
+  const float w = __fsub_rn(t, al);
+  const float f = __fadd_rn(__fsub_rn(al, __fsub_rn(t, w)), __fsub_rn(bl, w));
+  e = __fadd_rn(e, t);
+  float h = __fadd_rn(s, e);
+  float l = __fsub_rn(e, __fsub_rn(h, s));
+  l = __fadd_rn(l, f);
+  ah = __fadd_rn(h, l);
+  al = __fsub_rn(l, __fsub_rn(ah, h));
+}
+
 __device__ __forceinline__ float2 df_norm(float sh, float sl) {
   const float h = __fadd_rn(sh, sl);
   return make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
@@ -138,13 +179,13 @@ __device__ __forceinline__ float2 df_mul(float sh, float sl, float2 r) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Triangular factor in pair form, in column blocks of DF_JB: n is padded to n_pad (a
-// multiple of DF_JB) and block b (columns 8b .. 8b+7) stores, for every row k < 8b + 8, its
-// DF_JB entries contiguously: Rb[32 b (b+1) + 8 k + c] = R(k, 8b + c), zero where k > 8b + c
-// or the column is padding.  rinv[j] = 1/r_jj, zero on padding, so padded columns solve to
-// zero without a branch.
+// Triangular factor in pair form, in column blocks of DF_JB = 16: n is padded to n_pad (a
+// multiple of DF_JB) and block b (columns 16b .. 16b+15) stores, for every row k < 16b + 16,
+// its 16 entries contiguously: Rb[128 b (b+1) + 16 k + c] = R(k, 16b + c), zero where
+// k > 16b + c or the column is padding.  rinv[j] = 1/r_jj, zero on padding, so padded
+// columns solve to zero without a branch.
 // ---------------------------------------------------------------------------------------
-constexpr int DF_JB = 8;
+constexpr int DF_JB = 16;
 
 __host__ __device__ __forceinline__ int df_npad(int n) { return (n + DF_JB - 1) / DF_JB * DF_JB; }
 __host__ __device__ __forceinline__ int df_block_off(int b) { return DF_JB * DF_JB / 2 * b * (b + 1); }
@@ -168,11 +209,15 @@ __global__ void k_pack_df(const double *Rp, int n, float2 *Rb, float2 *rinv, con
 }
 
 // ---------------------------------------------------------------------------------------
-// Y = X R^{-1} per row by forward substitution in pair arithmetic, one thread per row.
-// Columns go in blocks of DF_JB: every w_k already solved is loaded once and feeds DF_JB
-// independent accumulators (the block's R entries for that k arrive as four 16-byte
-// broadcasts); the DF_JB x DF_JB diagonal block is then finished in registers.  For each
-// column the terms are taken in ascending k, as in the row-wise solve.
+// Y = X R^{-1} by blocked forward substitution in pair arithmetic (the blocked form of the
+// row-wise solve: diagonal blocks by substitution, never by an explicit inverse).  A CTA
+// holds a tile of DF_ROWS rows in shared memory.  For column block J (16 columns):
+//   (1) update  T[:, J] -= T[:, <J] R[<J, J]  -- a pair-arithmetic GEMM: warp w owns
+//       columns 16J + 4w .. +3, lane l owns rows l, l+32, l+64, l+96, so each thread keeps
+//       16 independent accumulators, reads its 4 row entries (consecutive rows: distinct
+//       banks) and the 4 R entries (one broadcast per warp) per k;
+//   (2) solve the 16 x 16 diagonal block row by row, one thread per row.
+// For every output entry the terms are taken in ascending k, as in the row-wise solve.
 // IN_F64: X is FP64 (else pairs); OUT_F64: Y is FP64 (else pairs).  X and Y may alias.
 // ---------------------------------------------------------------------------------------
 constexpr int DF_ROWS = 128;
@@ -189,16 +234,16 @@ __global__ void __launch_bounds__(DF_ROWS) k_trsm_df(const void *X, int64_t ldx,
   float2 *Rb = (float2 *)smf4;
   float2 *rinv = Rb + RB;
   float2 *T = rinv + np;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
   for (int e = tid; e < RB; e += blockDim.x) Rb[e] = Rg[e];
   for (int j = tid; j < np; j += blockDim.x) rinv[j] = rinvg[j];
   __syncthreads();
   for (int64_t row0 = (int64_t)blockIdx.x * DF_ROWS; row0 < m; row0 += (int64_t)gridDim.x * DF_ROWS) {
     const int rows = (int)imin64(DF_ROWS, m - row0);
-    for (int e = tid; e < rows * np; e += blockDim.x) {
+    for (int e = tid; e < DF_ROWS * np; e += blockDim.x) {
       const int r = e / np, c = e - r * np;
       float2 v = make_float2(0.f, 0.f);
-      if (c < n) {
+      if (c < n && r < rows) {
         if (IN_F64)
           v = d2df(((const double *)X)[(row0 + r) * ldx + c]);
         else
@@ -207,44 +252,64 @@ __global__ void __launch_bounds__(DF_ROWS) k_trsm_df(const void *X, int64_t ldx,
       T[r * ld + c] = v;
     }
     __syncthreads();
-    if (tid < rows) {
-      float2 *w = T + tid * ld;
-      for (int b = 0; b < np / DF_JB; ++b) {
-        const int j0 = DF_JB * b;
-        const float4 *rb = (const float4 *)(Rb + df_block_off(b));  // 2 entries per float4
-        float ah[DF_JB], al[DF_JB];
+    for (int b = 0; b < np / DF_JB; ++b) {
+      const int j0 = DF_JB * b;
+      const float2 *rb = Rb + df_block_off(b);
+      if (j0 > 0) {
+        // (1) off-diagonal update of the block, 4 rows x 4 columns per thread
+        const int c0 = j0 + 4 * wq;
+        float ah[16], al[16];
 #pragma unroll
-        for (int c = 0; c < DF_JB; ++c) {
-          ah[c] = w[j0 + c].x;
-          al[c] = w[j0 + c].y;
-        }
-        for (int k = 0; k < j0; ++k) {
-          const float2 wk = w[k];
-          float2 r[DF_JB];
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int q = 0; q < DF_JB / 2; ++q) {
-            const float4 v = rb[k * (DF_JB / 2) + q];
-            r[2 * q] = make_float2(v.x, v.y);
-            r[2 * q + 1] = make_float2(v.z, v.w);
+          for (int c = 0; c < 4; ++c) {
+            const float2 v = T[(lane + 32 * i) * ld + c0 + c];
+            ah[4 * i + c] = v.x;
+            al[4 * i + c] = v.y;
           }
-          df_fms_n<DF_JB>(ah, al, wk, r);
+        for (int k = 0; k < j0; ++k) {
+          float2 w4[4], r4[4], a[16], bb[16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) w4[i] = T[(lane + 32 * i) * ld + k];
+          const float4 q0 = *(const float4 *)(rb + DF_JB * k + 4 * wq);
+          const float4 q1 = *(const float4 *)(rb + DF_JB * k + 4 * wq + 2);
+          r4[0] = make_float2(q0.x, q0.y);
+          r4[1] = make_float2(q0.z, q0.w);
+          r4[2] = make_float2(q1.x, q1.y);
+          r4[3] = make_float2(q1.z, q1.w);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              a[4 * i + c] = w4[i];
+              bb[4 * i + c] = r4[c];
+            }
+          df_fms_nn<16>(ah, al, a, bb);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            T[(lane + 32 * i) * ld + c0 + c] = df_norm(ah[4 * i + c], al[4 * i + c]);
+        __syncthreads();
+      }
+      // (2) the diagonal block, one thread per row
+      {
+        float2 *t = T + tid * ld + j0;
         float2 wl[DF_JB];
 #pragma unroll
         for (int c = 0; c < DF_JB; ++c) {
+          float sh = t[c].x, sl = t[c].y;
 #pragma unroll
-          for (int cc = 0; cc < c; ++cc) {
-            const float2 rr = ((const float2 *)rb)[(j0 + cc) * DF_JB + c];
-            df_fms(ah[c], al[c], wl[cc], rr);
-          }
-          const float2 sn = df_norm(ah[c], al[c]);
+          for (int cc = 0; cc < c; ++cc) df_fms(sh, sl, wl[cc], rb[DF_JB * (j0 + cc) + c]);
+          const float2 sn = df_norm(sh, sl);
           wl[c] = df_mul(sn.x, sn.y, rinv[j0 + c]);
         }
 #pragma unroll
-        for (int c = 0; c < DF_JB; ++c) w[j0 + c] = wl[c];
+        for (int c = 0; c < DF_JB; ++c) t[c] = wl[c];
       }
+      __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < rows * n; e += blockDim.x) {
       const int r = e / n, c = e - r * n;
       const float2 v = T[r * ld + c];
@@ -283,11 +348,11 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
     while (t > jb) { t -= jb + 1; ++jb; }
     kb = t;  // kb <= jb
   }
-  float ah[4][4], al[4][4];
+  // per-tile partial sums (ph, pl) and running totals (th, tl): no pair accumulation
+  // chain is longer than one tile, the totals take one accurate pair addition per tile.
+  float th[16], tl[16];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) { ah[a][b] = 0.f; al[a][b] = 0.f; }
+  for (int q = 0; q < 16; ++q) { th[q] = 0.f; tl[q] = 0.f; }
   const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r_end = imin64(m, r_begin + rows_per_cta);
   for (int64_t row0 = r_begin; row0 < r_end; row0 += DFG_TILE) {
@@ -300,25 +365,34 @@ __global__ void k_gram_df(const float2 *__restrict__ W, int64_t ldw, int64_t m, 
     }
     __syncthreads();
     if (active) {
+      float ph[16], pl[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) { ph[q] = 0.f; pl[q] = 0.f; }
       for (int r = 0; r < rows; ++r) {
         const float2 *t = T + r * ld;
-        float2 x[4], y[4];
+        float2 x[4], y[4], a[16], bb[16];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) { x[a] = t[a * nb + kb]; y[a] = t[a * nb + jb]; }
+        for (int i = 0; i < 4; ++i) { x[i] = t[i * nb + kb]; y[i] = t[i * nb + jb]; }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) df_fma(ah[a][b], al[a][b], x[a], y[b]);
+          for (int c = 0; c < 4; ++c) {
+            a[4 * i + c] = make_float2(-x[i].x, -x[i].y);  // s -= (-x) y
+            bb[4 * i + c] = y[c];
+          }
+        df_fms_nn<16>(ph, pl, a, bb);
       }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) df_add(th[q], tl[q], ph[q], pl[q]);
     }
   }
   if (!active) return;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int k = 4 * kb + a, j = 4 * jb + b;  // G(k, j), need k <= j < n
-      if (j < n && k <= j) atomicAdd(Gp + tri_idx(k, j), (double)ah[a][b] + (double)al[a][b]);
+    for (int c = 0; c < 4; ++c) {
+      const int k = 4 * kb + i, j = 4 * jb + c;  // G(k, j), need k <= j < n
+      if (j < n && k <= j) atomicAdd(Gp + tri_idx(k, j), (double)th[4 * i + c] + (double)tl[4 * i + c]);
     }
 }
 
@@ -365,8 +439,10 @@ cudaError_t launch_gram_df(const float2 *W, int64_t ldw, int64_t m, int64_t n, d
   const int threads = std::max(32, (nblk + 31) / 32 * 32);
   const int per_sm = std::max(1, std::min(8, 1024 / threads));
   const int blocks_target = num_sms * per_sm;
-  const int64_t rows_per_cta =
-      std::max<int64_t>(DFG_TILE, ceil_div(ceil_div(m, blocks_target), DFG_TILE) * DFG_TILE);
+  // at most 64 tiles per CTA: the totals see at most 64 pair additions, then FP64 atomics
+  const int64_t rows_per_cta = std::min<int64_t>(
+      64 * DFG_TILE,
+      std::max<int64_t>(DFG_TILE, ceil_div(ceil_div(m, blocks_target), DFG_TILE) * DFG_TILE));
   const int blocks = (int)ceil_div(m, rows_per_cta);
   k_gram_df<<<blocks, threads, 0, s>>>(W, ldw, m, (int)n, rows_per_cta, Gpacked, st);
   return cudaGetLastError();
