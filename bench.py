@@ -265,6 +265,77 @@ def serve_bench(rq, synthetic, torch, dev, n_req=200, load=0.8, seed=7):
 
 
 # ---------------------------------------------------------------------------------------
+# Batched: 512 uneven matrices in one autotuned graph launch
+# ---------------------------------------------------------------------------------------
+def batch_bench(rq, synthetic, torch, dev, count=512, seed=11):
+    """m log-uniform in [4096, 262144], n uniform in {8, 16, 32, 64}, kappa log-uniform in
+    [1, 1e12] (one 262144-row matrix per (n, kappa decade pair); an item takes its first m
+    rows), default sketch sizes per item.  Times graph replays of randqr_factor_batched
+    against the same factorizations issued one call after another on one stream."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ns = [8, 16, 32, 64]
+    klev = [1.0, 1e3, 1e6, 1e9, 1e12]
+    pools = {(n, k): synthetic.make_v_torch(262144, n, k, seed=200 + n, device=dev)
+             for n in ns for k in klev}
+    shapes = []
+    for _ in range(count):
+        m = int(np.exp(rng.uniform(np.log(4096), np.log(262144))))
+        n = int(rng.choice(ns))
+        k = klev[min(4, int(rng.uniform(0, 12) // 2.4))]
+        shapes.append((m, n, k))
+    Vs = [pools[(n, k)][:m] for (m, n, k) in shapes]
+    Qs = [torch.empty((m, n), dtype=torch.float64, device=dev) for (m, n, k) in shapes]
+    Rs = [torch.empty((n, n), dtype=torch.float64, device=dev) for (m, n, k) in shapes]
+    bytes_total = sum(32.0 * m * n for (m, n, k) in shapes)
+    out = {"count": count, "V_bytes": sum(8.0 * m * n for (m, n, k) in shapes),
+           "workload": "m log-uniform [4096, 262144], n in {8,16,32,64}, kappa in {1,1e3,1e6,1e9,1e12}"}
+    stream = torch.cuda.current_stream()
+    for prec, name in ((rq.FP64, "fp64"), (rq.F32X2, "f32x2")):
+        ctx = rq.Context(dev.index or 0)
+        items = rq.batch_items(Vs, Qs, Rs, seeds=list(range(count)))
+        t0 = time.perf_counter()
+        sts = rq.randqr_factor_batched(ctx, items, prec=prec)
+        plan_s = time.perf_counter() - t0
+        if any(s != 0 for s in sts):
+            raise RuntimeError(f"batched statuses {set(sts)}")
+        lanes, tuned_ms = rq.randqr_batch_plan_info(ctx, items, prec=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            rq.randqr_factor_batched(ctx, items, prec=prec, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        # the same factorizations, one call after another on one stream
+        seq_ctx = rq.Context(dev.index or 0)
+        for i, V in enumerate(Vs):
+            rq.randqr_factor(V, seed=i, prec=prec, Q=Qs[i], R=Rs[i], ctx=seq_ctx, sync=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i, V in enumerate(Vs):
+            rq.randqr_factor(V, seed=i, prec=prec, Q=Qs[i], R=Rs[i], ctx=seq_ctx, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1)
+        rq.randqr_factor_batched(ctx, items, prec=prec)
+        worst = 0.0
+        for i in range(0, count, 32):
+            G = Qs[i].T @ Qs[i]
+            worst = max(worst, torch.linalg.matrix_norm(
+                G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
+        out[name] = {"ms_per_batch": ms, "eff_GBs": bytes_total / (ms / 1e3) / 1e9,
+                     "lanes": lanes, "autotune_ms": tuned_ms, "plan_build_s": plan_s,
+                     "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+                     "max_orth_err_2_sampled": worst}
+        seq_ctx.close()
+        ctx.close()
+    del pools, Vs, Qs, Rs
+    return out
+
+
+# ---------------------------------------------------------------------------------------
 def main():
     a = parse()
     if a.impl == "reference":
@@ -440,6 +511,8 @@ def main():
             del Q
             torch.cuda.empty_cache()
             line["serving"] = serve_bench(rq, synthetic, torch, dev, n_req=a.serve_requests)
+            torch.cuda.empty_cache()
+            line["batched"] = batch_bench(rq, synthetic, torch, dev)
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18)
 

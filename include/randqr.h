@@ -185,6 +185,39 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
                                      int64_t ldv, double *Q, int64_t ldq, double *R,
                                      int64_t ldr, randqr_info *info, void *stream);
 
+/* ---- Batched: many independent rand_cholQR factorizations in one graph launch ----------
+ * The paper factors one matrix at a time; this call factors `count` matrices of uneven
+ * sizes (Algorithm 3 on each, sketch sizes 0 -> 2(n^2+n), 4n; S2 from seed + 1) with their
+ * kernel chains captured as parallel branches of one CUDA graph over L stream lanes, each
+ * lane with its own workspace.  The first call with a given item array (the descriptors'
+ * bytes and `prec` are the key) builds a plan: uncaptured warm-up runs size the lanes'
+ * workspaces, then an autotuner captures schedules with L = 4, 8, 16, 32 lanes (items dealt
+ * to lanes largest-first) and keeps the fastest by timing replays; that first call blocks
+ * and allocates.  Later calls with the same items replay the kept graph on `stream` (one
+ * launch, no allocation).  With `statuses` non-NULL the call waits and writes each item's
+ * status (returning the first error); otherwise it returns after the launch.  The caller
+ * keeps V, Q, R alive while a launch runs and does not free them while the plan is cached
+ * (the graph holds their addresses; randqr_destroy drops the plans). */
+typedef struct {
+  const double *V;
+  int64_t m, n, ldv;
+  double *Q;
+  int64_t ldq;
+  double *R;
+  int64_t ldr;
+  int64_t s1, s2;
+  uint64_t seed;
+} randqr_batch_item;
+
+randqr_status randqr_factor_batched(randqr_ctx *ctx, const randqr_batch_item *items,
+                                    int32_t count, randqr_precision prec,
+                                    randqr_status *statuses, void *stream);
+/* The cached plan of a batch: its lane count and the autotuner's timed replay (ms).
+ * RANDQR_ERR_TICKET if no plan exists for these items. */
+randqr_status randqr_batch_plan_info(randqr_ctx *ctx, const randqr_batch_item *items,
+                                     int32_t count, randqr_precision prec, int32_t *lanes,
+                                     float *ms);
+
 /* ---- Serving: continuous batching of factorization requests ---------------------------
  * The paper has no serving layer; these calls run its Algorithms 3 and 4 (and shifted
  * CholeskyQR3) as requests.  A context's server owns `slots` CUDA streams, each with its own

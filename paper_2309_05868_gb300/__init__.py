@@ -410,3 +410,57 @@ def randqr_serve_stats_get(ctx):
     s = ServeStats()
     ctx._check(_serve_sigs(_load()).randqr_serve_stats_get(ctx.handle, _ct.byref(s)))
     return {f: getattr(s, f) for f, _ in ServeStats._fields_}
+
+
+# ---------------------------------------------------------------------------------------
+# Batched: randqr_factor_batched (one CUDA graph per batch, autotuned lane count).
+# ---------------------------------------------------------------------------------------
+class BatchItem(_ct.Structure):
+    _fields_ = [("V", _ct.c_void_p), ("m", _ct.c_int64), ("n", _ct.c_int64), ("ldv", _ct.c_int64),
+                ("Q", _ct.c_void_p), ("ldq", _ct.c_int64), ("R", _ct.c_void_p), ("ldr", _ct.c_int64),
+                ("s1", _ct.c_int64), ("s2", _ct.c_int64), ("seed", _ct.c_uint64)]
+
+
+def _batch_sigs(L):
+    if getattr(L, "_batch_ready", False):
+        return L
+    L.randqr_factor_batched.argtypes = [_ct.c_void_p, _ct.POINTER(BatchItem), _ct.c_int32, _ct.c_int,
+                                        _ct.POINTER(_ct.c_int32), _ct.c_void_p]
+    L.randqr_factor_batched.restype = _ct.c_int32
+    L.randqr_batch_plan_info.argtypes = [_ct.c_void_p, _ct.POINTER(BatchItem), _ct.c_int32, _ct.c_int,
+                                         _ct.POINTER(_ct.c_int32), _ct.POINTER(_ct.c_float)]
+    L.randqr_batch_plan_info.restype = _ct.c_int32
+    L._batch_ready = True
+    return L
+
+
+def batch_items(Vs, Qs, Rs, seeds=None):
+    """The descriptor array for lists of V, Q, R tensors (same order)."""
+    arr = (BatchItem * len(Vs))()
+    for i, (V, Q, R) in enumerate(zip(Vs, Qs, Rs)):
+        ldv, ldq, ldr = _check_mat(V, "V"), _check_mat(Q, "Q"), _check_mat(R, "R")
+        m, n = V.shape
+        arr[i] = BatchItem(V.data_ptr(), m, n, ldv, Q.data_ptr(), ldq, R.data_ptr(), ldr, 0, 0,
+                           0 if seeds is None else int(seeds[i]))
+    return arr
+
+
+def randqr_factor_batched(ctx, items, prec=FP64, stream=None, sync=True):
+    """Factor every item of `items` (from batch_items); returns the per-item statuses when
+    sync, else None.  The first call with a given array builds and autotunes its graph."""
+    L = _batch_sigs(_load())
+    n = len(items)
+    st_arr = (_ct.c_int32 * n)() if sync else None
+    st = L.randqr_factor_batched(ctx.handle, items, n, int(prec), st_arr, _stream(stream))
+    if st not in (0, -2, -3) or (st != 0 and not sync):
+        raise RandQRError(st)
+    return list(st_arr) if sync else None
+
+
+def randqr_batch_plan_info(ctx, items, prec=FP64):
+    L = _batch_sigs(_load())
+    lanes, ms = _ct.c_int32(0), _ct.c_float(0)
+    st = L.randqr_batch_plan_info(ctx.handle, items, len(items), int(prec), _ct.byref(lanes), _ct.byref(ms))
+    if st != 0:
+        raise RandQRError(st)
+    return lanes.value, ms.value

@@ -248,6 +248,7 @@ randqr_status randqr_destroy(randqr_ctx *ctx) {
   if (!ctx) return RANDQR_ERR_ARG;
   cudaSetDevice(ctx->device);
   rq_server_destroy(ctx);
+  rq_batcher_destroy(ctx);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->s2_buf) cudaFree(ctx->s2_buf);

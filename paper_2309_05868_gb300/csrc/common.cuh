@@ -121,10 +121,14 @@ struct randqr_ctx {
   std::vector<cudaEvent_t> prof_pool;
   // request server (randqr_submit / randqr_poll), created on first use
   struct randqr_server *server = nullptr;
+  // batched plans (randqr_factor_batched), created on first use
+  struct randqr_batcher *batcher = nullptr;
 };
 
 // Tear down a context's request server (waits for its streams).
 void rq_server_destroy(randqr_ctx *ctx);
+// Tear down a context's batched plans and their lanes.
+void rq_batcher_destroy(randqr_ctx *ctx);
 
 namespace rq {
 // Kernel kinds for the per-kernel timing record.
