@@ -30,6 +30,38 @@ sys.path.insert(0, ROOT)
 FP64_ALU_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
+
+# Roofline model per kernel kind: (bound, algorithmic units per row of V per launch).
+# FP64 CUDA-core passes are bound by the FP64 pipe (flops per row); the pair-arithmetic and
+# tensor-core passes, and the CountSketch scatter, by HBM (bytes per row: an 8-byte FP64
+# or (hi, lo) FP32 pair read per element, plus the write for the solves).
+def roofline_model(kind, n):
+    return {"trsm": ("alu", n * n), "gram": ("alu", n * (n + 1)),
+            "cs_scatter": ("hbm", 8 * n), "trsm_df": ("hbm", 16 * n),
+            "gram_df": ("hbm", 8 * n), "gram_tc": ("hbm", 8 * n),
+            "trsm_tc": ("hbm", 16 * n)}.get(kind)
+
+
+def kernel_roofline(kind, avg_ms, m, n):
+    model = roofline_model(kind, n)
+    if model is None:
+        return {"bound": None, "kernel": kind, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    bound, per_row = model
+    if bound == "alu":
+        achieved = per_row * m / (avg_ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": kind, "achieved": achieved,
+                "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                "algorithmic": f"{per_row} FP64 flops per row x {m} rows per launch"}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    achieved = per_row * m / (avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+            "algorithmic": f"{per_row} bytes per row x {m} rows per launch"}
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -418,23 +450,8 @@ def main():
 
     # dominant kernel and its roofline
     kind, (tot_ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
-    avg_ms = tot_ms / launches
-    flops_per_row = {"trsm": n * n, "gram": n * (n + 1), "cs_scatter": n}.get(kind, n * n)
-    if a.prec == "fp64":
-        achieved = flops_per_row * m / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": kind, "achieved": achieved,
-                "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                "algorithmic": f"{flops_per_row} FP64 flops per row x {m} rows per launch",
-                "kernel_share": tot_ms / (ms * a.steps)}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        achieved = 16.0 * m * n / (avg_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "kernel_share": tot_ms / (ms * a.steps)}
+    roof = kernel_roofline(kind, tot_ms / launches, m, n)
+    roof["kernel_share"] = tot_ms / (ms * a.steps)
 
     line = {"metric": "rand_cholQR effective HBM GB/s (m x n FP64)", "value": value,
             "unit": "GB/s", "n_gpus": world, "steps": a.steps, "warmup": max(a.warmup, 3),

@@ -129,6 +129,13 @@ class Context:
     def set_profiling(self, enable=True):
         self._check(_load().randqr_set_profiling(self._h, int(bool(enable))))
 
+    def set_tensor_cores(self, enable=True):
+        """Gram from exact split products on the tensor cores (default) or on CUDA cores."""
+        L = _load()
+        L.randqr_set_tensor_cores.argtypes = [_ct.c_void_p, _ct.c_int]
+        L.randqr_set_tensor_cores.restype = _ct.c_int32
+        self._check(L.randqr_set_tensor_cores(self._h, int(bool(enable))))
+
     def kernel_times(self):
         """{kernel name: (total device ms, launches)} recorded since the last read."""
         L = _load()

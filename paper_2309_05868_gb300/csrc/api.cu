@@ -195,18 +195,41 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
 // One cholQR pass (Algorithm 2) on X into Y: G = X^T X (+ shift) -> R_x -> Y = X R_x^{-1}.
 // With Rprev, writes Rnext = R_x Rprev (packed); with Rdense, writes that product (or R_x)
 // dense.
+// Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores: only where R_c is well
+// conditioned by construction (rand_cholQR's second pass); R_c^{-1} goes to w.Rt2.
+randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const void *X, bool x_df, int64_t ldx, double *Y,
+                                  int64_t ldy, int64_t m, int64_t n, const Workspace &w,
+                                  cudaStream_t s) {
+  RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz(X, x_df, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+  }));
+  return RANDQR_OK;
+}
+
+bool use_tc_solve(const randqr_ctx *ctx, int64_t n) { return ctx->use_tc && rq::trsm_oz_supported(n); }
+
 randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy,
                           int64_t m, int64_t n, double shift_coeff, const double *Rprev,
                           double *Rnext, double *Rdense, int64_t ldr, int stage,
-                          randqr_precision prec, const Workspace &w, cudaStream_t s) {
+                          randqr_precision prec, const Workspace &w, cudaStream_t s,
+                          bool well_conditioned = false) {
   RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
-  RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
-    return rq::launch_gram(X, ldx, m, n, w.G, prec, ctx->num_sms, ctx->status_dev, s);
-  }));
+  if (ctx->use_tc && rq::gram_oz_supported(n)) {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
+      return rq::launch_gram_oz(X, false, ldx, m, n, w.G, true, ctx->num_sms, ctx->status_dev, s);
+    }));
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+      return rq::launch_gram(X, ldx, m, n, w.G, prec, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
   RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
     return rq::launch_potrf(w.G, n, shift_coeff, w.Rc, Rprev, Rnext, Rdense, ldr, stage,
                             ctx->status_dev, s);
   }));
+  if (well_conditioned && use_tc_solve(ctx, n))
+    return solve_by_inverse_tc(ctx, X, false, ldx, Y, ldy, m, n, w, s);
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
     return rq::launch_trsm(X, ldx, Y, ldy, m, n, w.Rc, prec, ctx->num_sms, ctx->status_dev, s);
   }));
@@ -263,6 +286,12 @@ randqr_status randqr_destroy(randqr_ctx *ctx) {
   return RANDQR_OK;
 }
 
+randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable) {
+  if (!ctx) return RANDQR_ERR_ARG;
+  ctx->use_tc = enable != 0;
+  return RANDQR_OK;
+}
+
 randqr_status randqr_set_profiling(randqr_ctx *ctx, int enable) {
   if (!ctx) return RANDQR_ERR_ARG;
   ctx->prof = enable != 0;
@@ -299,7 +328,8 @@ randqr_status randqr_get_kernel_times(randqr_ctx *ctx, int32_t max_kinds, double
 const char *randqr_kernel_name(int32_t kind) {
   static const char *names[rq::K_NUM_KINDS] = {"gauss_gen", "cs_scatter", "sketch_gemm", "hhqr",
                                                "trsm", "gram", "potrf", "unpack", "cs_hash",
-                                               "pack_df", "trsm_df", "gram_df"};
+                                               "pack_df", "trsm_df", "gram_df", "gram_tc",
+                                               "tri_inv", "trsm_tc"};
   return (kind >= 0 && kind < rq::K_NUM_KINDS) ? names[kind] : "unknown";
 }
 
@@ -392,12 +422,23 @@ static randqr_status factor_df(randqr_ctx *ctx, const double *V, int64_t m, int6
                               ctx->status_dev, s);
   }));
   RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
-  RQ_CUDA(timed(ctx, s, rq::K_GRAM_DF, [&] {
-    return rq::launch_gram_df((const float2 *)Q, ldq, m, n, w.G, ctx->num_sms, ctx->status_dev, s);
-  }));
+  if (ctx->use_tc && rq::gram_oz_supported(n)) {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
+      return rq::launch_gram_oz(Q, true, ldq, m, n, w.G, false, ctx->num_sms, ctx->status_dev, s);
+    }));
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM_DF, [&] {
+      return rq::launch_gram_df((const float2 *)Q, ldq, m, n, w.G, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
   RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
     return rq::launch_potrf(w.G, n, 0.0, w.Rc, w.Rs, nullptr, R, ldr, 1, ctx->status_dev, s);
   }));
+  if (use_tc_solve(ctx, n)) {
+    randqr_status st = solve_by_inverse_tc(ctx, Q, true, ldq, Q, ldq, m, n, w, s);
+    if (st != RANDQR_OK) return st;
+    return finish_call(ctx, s, info);
+  }
   RQ_CUDA(timed(ctx, s, rq::K_PACK_DF, [&] { return rq::launch_pack_df(w.Rc, n, w.Rdf, w.rinv, ctx->status_dev, s); }));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_DF, [&] {
     return rq::launch_trsm_df(Q, false, ldq, Q, true, ldq, m, n, w.Rdf, w.rinv, ctx->num_sms,
@@ -431,8 +472,8 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
     return finish_call(ctx, s, info);
   }
   // cholQR of W, in place on Q; R = R_c R_s written dense.
-  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s)) !=
-      RANDQR_OK)
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
+                        /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
   return finish_call(ctx, s, info);
 }

@@ -111,6 +111,8 @@ struct randqr_ctx {
   rq::DevStatus *status_dev = nullptr;
   rq::DevStatus *status_host = nullptr;
   char last_err[256] = {0};
+  // Gram on the tensor cores (split products) when n <= 128
+  bool use_tc = true;
   // per-kernel timing (randqr_set_profiling)
   bool prof = false;
   struct ProfRec {
@@ -134,7 +136,7 @@ namespace rq {
 // Kernel kinds for the per-kernel timing record.
 enum KernelKind {
   K_GAUSS_GEN = 0, K_CS_SCATTER, K_SKETCH_GEMM, K_HHQR, K_TRSM, K_GRAM, K_POTRF, K_UNPACK,
-  K_CS_HASH, K_PACK_DF, K_TRSM_DF, K_GRAM_DF, K_NUM_KINDS
+  K_CS_HASH, K_PACK_DF, K_TRSM_DF, K_GRAM_DF, K_GRAM_TC, K_TRI_INV, K_TRSM_TC, K_NUM_KINDS
 };
 }  // namespace rq
 
@@ -173,4 +175,17 @@ cudaError_t launch_trsm_df(const void *X, bool x_f64, int64_t ldx, void *Y, bool
                            cudaStream_t s);
 cudaError_t launch_gram_df(const float2 *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
                            int num_sms, const DevStatus *st, cudaStream_t s);
+// X = R^{-1} for packed upper-triangular R (small.cu)
+cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, const DevStatus *st,
+                           cudaStream_t s);
+// Q = W X from exact split products on the tensor cores (trsm_tc.cu), n <= 64
+bool trsm_oz_supported(int64_t n);
+cudaError_t launch_trsm_oz(const void *W, bool in_df, int64_t ldw, double *Q, int64_t ldq, int64_t m,
+                           int64_t n, const double *Xpacked, int num_sms, DevStatus *st,
+                           cudaStream_t s);
+// Gram from exact split products on the tensor cores (gram_tc.cu)
+bool gram_oz_supported(int64_t n);
+cudaError_t launch_gram_oz(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n,
+                           double *Gpacked, bool acc_f64, int num_sms, DevStatus *st,
+                           cudaStream_t s);
 }  // namespace rq

@@ -1,0 +1,175 @@
+// tc.cuh -- fifth-generation tensor core (tcgen05) and bulk-copy primitives, and the exact
+// integer splitting of FP64 / pair values, shared by the split-product kernels.
+//
+// Splitting: a value w with scale 2^E > |w| becomes the 56-bit fixed point
+// X = trunc(|w| 2^(56 - E)), cut into eight 7-bit digits a_s = (X >> (49 - 7 s)) & 127
+// (the top digit may reach 128 for pair inputs), each carrying the sign of w:
+// w = 2^(E - 56) sum_s a_s 2^(49 - 7 s) up to 2^(E - 56).  bf16 holds every digit exactly and
+// the tensor cores accumulate digit products exactly in FP32 while the sums stay below 2^24.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rq {
+namespace tc {
+
+constexpr int SLICES = 8;
+constexpr int MAX_WAIT = 1 << 24;  // mbarrier polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: lbo = byte step between core matrices
+// (8 rows x 16 bytes) along K, sbo = byte step between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: kind::f16 with bf16 A and B (both K-major), FP32 D, M x N.
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
+}
+
+// Poll an mbarrier phase, at most MAX_WAIT times; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < MAX_WAIT && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+// Bulk asynchronous copy global -> shared (TMA engine), completion counted in bytes on mbar.
+// Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// Bulk asynchronous copy shared -> global; bulk_store_wait() returns once the shared source
+// has been read (it may then be overwritten).
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_store_wait() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+// Tensor memory, allocated by one whole warp; the address lands in *slot (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(slot)),
+               "r"(cols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(cols));
+}
+
+// 8 consecutive columns of this warp's 32 tensor-memory lanes (thread = lane).
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Exponent field of an element rebased to the FP64 bias; 0 for zero / subnormal.
+template <bool IN_DF>
+__device__ __forceinline__ int expfield(const void *p) {
+  if (IN_DF) {
+    const int ef = (__float_as_uint(((const float2 *)p)->x) >> 23) & 0xff;
+    return ef ? ef - 127 + 1023 : 0;
+  }
+  return (int)(((unsigned long long)__double_as_longlong(*(const double *)p) >> 52) & 0x7ff);
+}
+
+// Scale exponent E (|w| < 2^E) from the largest exponent field of a set; tiny sets clamp.
+__device__ __forceinline__ int scale_exp(int expfield_max) { return max(expfield_max - 1023 + 1, -100); }
+
+// Signed 56-bit fixed point of a float's value relative to 2^E (truncated).
+__device__ __forceinline__ long long fix_f32(float f, int E) {
+  const unsigned int b = __float_as_uint(f);
+  const int ef = (b >> 23) & 0xff;
+  if (ef == 0) return 0;
+  const long long mant = (long long)((b & 0x7fffff) | 0x800000);
+  const int sh = (ef - 127) + 33 - E;  // value = mant 2^(ef-127-23); times 2^(56-E)
+  long long x = sh >= 0 ? (sh < 40 ? (mant << sh) : 0) : (-sh < 63 ? (mant >> -sh) : 0);
+  return (b >> 31) ? -x : x;
+}
+
+template <bool IN_DF>
+__device__ __forceinline__ long long fixpt(const void *p, int E) {
+  if (IN_DF) {
+    const float2 v = *(const float2 *)p;
+    return fix_f32(v.x, E) + fix_f32(v.y, E);
+  }
+  const unsigned long long b = (unsigned long long)__double_as_longlong(*(const double *)p);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0) return 0;
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  const int sh = (ef - 1023) + 4 - E;  // value = mant 2^(ef-1023-52); times 2^(56-E)
+  long long x = sh >= 0 ? (sh < 8 ? (mant << sh) : 0) : (-sh < 63 ? (mant >> -sh) : 0);
+  return (b >> 63) ? -x : x;
+}
+
+// bf16 bits of a small integer (|a| < 2^22), exactly, with FP32-pipe and integer ops only.
+__device__ __forceinline__ uint32_t int_to_bf16_bits(int a) {
+  const float f = __int_as_float(0x4B400000 + a) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// Digit s of a fixed-point value, as bf16 bits.
+__device__ __forceinline__ uint32_t digit_bf16(long long x, int s) {
+  const unsigned long long ax = (unsigned long long)(x < 0 ? -x : x);
+  const int a = (int)((ax >> (49 - 7 * s)) & (s == 0 ? 255 : 127));
+  return int_to_bf16_bits(x < 0 ? -a : a);
+}
+
+__device__ __forceinline__ float pow2f(int e) {  // 2^e, e clamped to [-126, 127]
+  e = max(min(e, 127), -126);
+  return __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
+// Element offset (bf16 units) of (row, k) in a K-major, unswizzled tile with kdim columns.
+__device__ __forceinline__ int kmajor_off(int row, int k, int kdim) {
+  return ((row >> 3) * (kdim >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+}  // namespace tc
+}  // namespace rq

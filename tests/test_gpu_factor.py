@@ -223,3 +223,37 @@ def test_f32x2_in_place_and_ld(rq):
     S2 = oracle.gauss_sketch(1, s2, s1)
     Q, R, _ = _run(rq, V, s1, s2, 0, S2, ld_pad=3, inplace=True, prec=rq.F32X2)
     assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("m,n,kappa", [(20000, 16, 1e10), (30001, 64, 1e13), (9000, 100, 1e6),
+                                       (5000, 128, 1e14)])
+def test_tensor_core_gram_matches_cuda_core_gram(rq, prec, m, n, kappa):
+    """The Gram from exact split products on the tensor cores and the CUDA-core Gram give
+    factorizations that both meet the targets and agree within the parity tolerance."""
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=n)
+    Vd = torch.from_numpy(V).cuda()
+    out = []
+    for tc in (True, False):
+        ctx = rq.Context(0)
+        ctx.set_tensor_cores(tc)
+        Q, R, _ = rq.randqr_factor(Vd, s1, s2, seed=1, prec=prec, ctx=ctx)
+        Q, R = Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+        out.append((Q, R))
+        ctx.close()
+    tq, tr = parity_tolerance(V, s1, s2)
+    scale = 64 if prec else 1
+    assert np.abs(out[0][0] - out[1][0]).max() <= scale * tq
+    assert np.abs(out[0][1] - out[1][1]).max() / np.abs(out[0][1]).max() <= scale * tr
+
+
+def test_tensor_core_gram_cholqr2_exact_on_orthonormal_columns(rq):
+    # V with orthonormal columns scaled by powers of two: V^T V is diagonal and exactly known
+    m, n = 40000, 48
+    U = np.linalg.qr(synthetic.rng(3).standard_normal((m, n)))[0]
+    Q, R, _ = rq.randqr_cholqr2(torch.from_numpy(U).cuda())
+    R = R.cpu().numpy()
+    np.testing.assert_allclose(np.abs(np.diag(R)), 1.0, rtol=1e-14)
+    assert np.abs(np.triu(R, 1)).max() < 1e-14
