@@ -462,6 +462,18 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
   if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
   if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, true)) != RANDQR_OK)
     return st;
+  if (second_pass && use_tc_solve(ctx, n)) {
+    // Both solves as tensor-core products with explicit inverses (either precision): W =
+    // V (R_s^{-1}) into Q, then the Cholesky pass on W in place.
+    RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
+    RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+      return rq::launch_trsm_oz(V, false, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+    }));
+    if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
+                          /*well_conditioned=*/true)) != RANDQR_OK)
+      return st;
+    return finish_call(ctx, s, info);
+  }
   if (prec == RANDQR_F32X2 && second_pass) return factor_df(ctx, V, m, n, ldv, Q, ldq, R, ldr, w, s, info);
   // W = V R_s^{-1}, written into Q.
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {

@@ -228,36 +228,48 @@ cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t l
   return cudaGetLastError();
 }
 
-// X = R^{-1} for upper-triangular R (packed), FP64: column k of X solves R x = e_k by back
-// substitution, x_k = 1 / r_kk, x_i = -(sum_{l=i+1..k} r_il x_l) / r_ii for i = k-1 .. 0.
-// One thread per column, R staged in shared memory.  Used where R is well conditioned by
-// construction (the Cholesky factor R_c of the preconditioned W), so that applying X as a
-// product is as accurate as the triangular solve.
-__global__ void __launch_bounds__(SMALL_THREADS) k_tri_inv(const double *Rp, int n, double *Xp,
-                                                           const DevStatus *st) {
+// X = R^{-1} for upper-triangular R (packed), FP64, column by column: column k solves
+// R x = e_k by back substitution, x_k = 1 / r_kk, x_i = -(sum_{l=i+1..k} r_il x_l) / r_ii for
+// i = k-1 .. 0.  Then R X = I + F with |F| <= gamma |R| |X|: the computed inverse is
+// R^{-1} (I + F), a perturbation that stays on the right of a product V X, so V X = W (I + F)
+// keeps W's conditioning.  One warp per column, lanes split each dot product; the pivots'
+// reciprocals are formed once.
+constexpr int TRI_COLS = 8;  // columns (warps) per CTA
+
+__global__ void __launch_bounds__(TRI_COLS * 32) k_tri_inv(const double *Rp, int n, double *Xp,
+                                                         const DevStatus *st) {
   if (status_failed(st)) return;
-  extern __shared__ double Rs_[];
+  extern __shared__ double tri_sm[];
   const int P = n * (n + 1) / 2;
-  for (int e = threadIdx.x; e < P; e += blockDim.x) Rs_[e] = Rp[e];
+  double *R = tri_sm, *rdiag = tri_sm + P;
+  double *x = rdiag + n + (threadIdx.x >> 5) * n;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) R[e] = Rp[e];
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    Xp[tri_idx(k, k)] = 1.0 / Rs_[tri_idx(k, k)];
-    for (int i = k - 1; i >= 0; --i) {
-      double acc = 0.0;
-      for (int l = i + 1; l <= k; ++l) acc = fma(Rs_[tri_idx(i, l)], Xp[tri_idx(l, k)], acc);
-      Xp[tri_idx(i, k)] = -acc / Rs_[tri_idx(i, i)];
-    }
+  for (int e = threadIdx.x; e < n; e += blockDim.x) rdiag[e] = 1.0 / R[tri_idx(e, e)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, k = blockIdx.x * TRI_COLS + (threadIdx.x >> 5);
+  if (k >= n) return;
+  if (lane == 0) x[k] = rdiag[k];
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = 0.0;
+    for (int l = i + 1 + lane; l <= k; l += 32) acc = fma(R[tri_idx(i, l)], x[l], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[i] = -acc * rdiag[i];
+    __syncwarp();
   }
+  for (int i = lane; i <= k; i += 32) Xp[tri_idx(i, k)] = x[i];
 }
 
 cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, const DevStatus *st,
                            cudaStream_t s) {
-  const size_t dyn = sizeof(double) * (size_t)(n * (n + 1) / 2);
+  const size_t dyn = sizeof(double) * (size_t)(n * (n + 1) / 2 + n + TRI_COLS * n);
   if (dyn > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  k_tri_inv<<<1, SMALL_THREADS, dyn, s>>>(Rpacked, (int)n, Xpacked, st);
+  k_tri_inv<<<(unsigned)ceil_div(n, TRI_COLS), TRI_COLS * 32, dyn, s>>>(Rpacked, (int)n, Xpacked, st);
   return cudaGetLastError();
 }
 

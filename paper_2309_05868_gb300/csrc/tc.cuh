@@ -42,6 +42,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t 
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// D = A B + 2^-7 D (scale-input-d): folds the sums already in D in at a 2^-7 lower weight.
+__device__ __forceinline__ void umma_scaled7(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, 7;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc));
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar));
 }
@@ -169,6 +177,100 @@ __device__ __forceinline__ float pow2f(int e) {  // 2^e, e clamped to [-126, 127
 // Element offset (bf16 units) of (row, k) in a K-major, unswizzled tile with kdim columns.
 __device__ __forceinline__ int kmajor_off(int row, int k, int kdim) {
   return ((row >> 3) * (kdim >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+}  // namespace tc
+}  // namespace rq
+
+namespace rq {
+namespace tc {
+
+// ---------------------------------------------------------------------------------------
+// Balanced 7-bit digits (f16 operands).  An integer X with |X| < 2^54 is written as
+// X = sum_{p=0}^{7} d_p 2^(7p) with d_p in [-64, 63]: the bytes-of-seven of X + DIG_BIAS,
+// DIG_BIAS = sum_p 64 * 2^(7p), are d_p + 64.  Each d_p is an exact f16, and a product of
+// two digits is at most 2^12 in magnitude.
+// ---------------------------------------------------------------------------------------
+constexpr int NDIG = 8;
+constexpr unsigned long long DIG_BIAS = 0x81020408102040ULL;
+
+// Instruction descriptor: kind::f16 with f16 A and B (both K-major), FP32 D, M x N.
+__device__ __forceinline__ uint32_t umma_idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init_count(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+// Poll an mbarrier phase at most MAX_WAIT times, giving up early once *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int *abort) {
+  for (int it = 0; it < MAX_WAIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
+// trunc(x 2^(54 - E)) for |x| < 2^E, as a signed integer (|.| < 2^54).
+__device__ __forceinline__ long long fix54(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  const int sh = ef - 1021 - E;  // x = mant 2^(ef - 1075)
+  long long v = sh >= 0 ? (mant << (sh & 1)) : (-sh < 63 ? (mant >> -sh) : 0);
+  v = ef == 0 ? 0 : v;
+  return (b >> 63) ? -v : v;
+}
+__device__ __forceinline__ long long fix54(float f, int E) {
+  const uint32_t b = __float_as_uint(f);
+  const int ef = (int)((b >> 23) & 0xff);
+  const long long mant = (long long)((b & 0x7fffff) | 0x800000);
+  const int sh = ef - 96 - E;  // f = mant 2^(ef - 150)
+  long long v = sh >= 0 ? (sh < 31 ? (mant << sh) : 0) : (-sh < 63 ? (mant >> -sh) : 0);
+  v = ef == 0 ? 0 : v;
+  return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ uint32_t hsub2_bits(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Digit words of two fixed-point values: w[p] = f16(d_p(xa)) | f16(d_p(xb)) << 16.
+__device__ __forceinline__ void digits2(long long xa, long long xb, uint32_t (&w)[NDIG]) {
+  const unsigned long long ya = (unsigned long long)xa + DIG_BIAS;
+  const unsigned long long yb = (unsigned long long)xb + DIG_BIAS;
+  const uint32_t la = (uint32_t)ya, ha = (uint32_t)(ya >> 32);
+  const uint32_t lb = (uint32_t)yb, hb = (uint32_t)(yb >> 32);
+  uint32_t win[4];  // window q: bits 14q .. 14q + 13 of each value, one per 16-bit half
+  win[0] = __byte_perm(la, lb, 0x5410);
+  win[1] = __byte_perm(la >> 14, lb >> 14, 0x5410);
+  win[2] = __byte_perm(__funnelshift_r(la, ha, 28), __funnelshift_r(lb, hb, 28), 0x5410);
+  win[3] = __byte_perm(ha >> 10, hb >> 10, 0x5410);
+  // f16(1024 + y) = 0x6400 | y for y < 1024; subtracting f16(1088) leaves y - 64 exactly.
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    w[2 * q] = hsub2_bits((win[q] & 0x007F007Fu) | 0x64006400u, 0x64406440u);
+    w[2 * q + 1] = hsub2_bits(((win[q] >> 7) & 0x007F007Fu) | 0x64006400u, 0x64406440u);
+  }
+}
+
+// The integer value of an FP32 accumulator that holds an exact integer of magnitude < 2^22.
+__device__ __forceinline__ int acc_to_int(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
 }  // namespace tc

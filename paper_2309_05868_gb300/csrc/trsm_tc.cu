@@ -1,218 +1,351 @@
-// trsm_tc.cu -- Q = W R_c^{-1} (Algorithm 2 step 3 of rand_cholQR's second pass) as the product
-// Q = W X with X = R_c^{-1}, from exact split products on the tensor cores.
+// trsm_tc.cu -- Y = X B for an n x n upper-triangular B given by its packed FP64 entries
+// (n <= 64), from exact split products on the tensor cores.  rand_cholQR runs both of its
+// triangular solves (W = V R_s^{-1} and Q = W R_c^{-1}, Algorithm 3) this way, as products with
+// the explicit inverses.
 //
-// rand_cholQR's R_c is the Cholesky factor of the Gram of the preconditioned W, so
-// kappa(R_c) = kappa(W) = O(1) (Sec. 4.1, Theorem 5.2): applying its explicit inverse is then
-// as accurate as the row-wise solve (errors grow with kappa(R_c), not kappa(V)), and the
-// solve becomes a dense contraction with K = n.  (The first solve, W = V R_s^{-1}, keeps the
-// row-wise substitution: R_s inherits kappa(V).)
+// Number format.  Row i of X gets a scale 2^E_i > max_j |x_ij| and column k of B a scale
+// 2^F_k > max_j |b_jk|.  x_ij = 2^(E_i - 54) X_ij up to truncation, with the integer
+// X_ij = trunc(x_ij 2^(54 - E_i)) written in eight balanced 7-bit digits (tc.cuh), and the
+// same for b_jk with digits e.  With slice s = 7 - p (s = 0 the leading digit) the product keeps
+// the slice pairs s + t <= 8, gathered by g = s + t into regions of tensor memory:
+//   D_g(i, k) = sum_{s + t = g} sum_j d_s(i, j) e_t(j, k),   |D_g| <= 8 * 64 * 2^12 = 2^21,
+//   y_ik = 2^(E_i + F_k - 59) T_ik,   T_ik = sum_g 2^(7 (7 - g)) D_g(i, k).
+// Regions 0-6 hold exact FP32 integers.  Region 8 is summed first in region 7's columns and
+// folded in at weight 2^-7 by the first region-7 MMA (scale-input-d), so that region holds
+// D_7 + 2^-7 D_8 rounded to FP32, an error far below T's last unit.  The recombination turns
+// the regions into integers, forms T / 8 in 64-bit integer arithmetic and rounds once to FP64.
+// Truncation and the dropped pairs (s + t >= 9) weigh about 2^-54 of 2^(E_i + F_k) per term: a
+// relative perturbation of each row of X, so the first solve's backward error in V stays at
+// that level whatever kappa(V) is.
 //
-// Each row i of a 128-row tile gets its own scale 2^e_i and each column k of X its own scale
-// 2^f_k (tc.cuh's eight 7-bit digits): Q_ik = 2^(e_i + f_k) sum_g 2^(-14 - 7 g) D_g(i, k),
-// D_g = sum_{s + t = g} sum_j a_s(i, j) b_t(j, k), g <= 7.  Each D_g sums at most 8 x 64
-// digit products (< 2^23): exact in the FP32 accumulators.  Region g of tensor memory (64
-// columns) holds D_g; the K = 64 reduction runs in two halves of 32 so that one half of the
-// row slices (64 KB) fits in shared memory beside X's slices and the row tile.
-// n <= 64 (n padded to 64 with zeros).
+// One CTA per SM, persistent over 128-row tiles; warps specialise:
+//   warps 0-3 cut rows into digit slices (shared memory A: 8 slices x 128 rows x 64 K, f16),
+//   warps 4-7 read tensor memory back, recombine and store rows of Y,
+//   warp 8 loads 32-row sub-tiles of X into a two-slot ring with bulk copies,
+//   warp 9 owns tensor memory and issues the MMAs,
+// handing tiles over through mbarriers.  B's digit slices are built once per CTA.  B is upper
+// triangular, so the K-step j in [16c, 16c + 16) meets only columns k >= 16c and its MMAs run
+// with N = 64 - 16c.  In place (Y == X) is safe: a tile's rows are read before any are written.
 #include "common.cuh"
-#include "df.cuh"
 #include "tc.cuh"
 
 namespace rq {
 
 namespace {
-constexpr int TQ_THREADS = 256;
-constexpr int TQ_ROWS = 128;
-constexpr int TQ_NP = 64;
+using namespace tc;
+
+constexpr int TQ_ROWS = 128, TQ_NP = 64, TQ_SUB = 32, TQ_NSTAGE = 2;
+constexpr int TQ_THREADS = 320;
+constexpr int W_LOAD = 8, W_MMA = 9;
 constexpr uint32_t TQ_TMEM_COLS = 512;
-constexpr size_t TQ_B_BYTES = (size_t)tc::SLICES * TQ_NP * TQ_NP * 2;      // 64 KB
-constexpr size_t TQ_A_BYTES = (size_t)tc::SLICES * TQ_ROWS * 32 * 2;       // 64 KB
-constexpr size_t TQ_STAGE_BYTES = (size_t)TQ_ROWS * TQ_NP * 8;             // 64 KB
+// A: K-major, no swizzle; a 16-byte pad between K-adjacent core matrices spreads one row's
+// eight core-matrix rows over all 32 banks for the slicers' 4-byte stores.
+constexpr uint32_t A_LBO = 144, A_SBO = 8 * A_LBO, A_SLICE = (TQ_ROWS / 8) * A_SBO;
+// B: per K-step c a block of (64 - 16c) rows (output column k) x 16 K, 32 bytes per row.
+constexpr uint32_t B_SLICE = 160 * 32;
+constexpr uint32_t STAGE_BYTES = TQ_SUB * TQ_NP * 8;
+constexpr uint32_t OUT_PITCH = 72, OUT_BYTES = 32 * OUT_PITCH;
+constexpr size_t OFF_B = 0;
+constexpr size_t OFF_A = OFF_B + (size_t)NDIG * B_SLICE;
+constexpr size_t OFF_STAGE = OFF_A + (size_t)NDIG * A_SLICE;
+constexpr size_t OFF_OUT = OFF_STAGE + (size_t)TQ_NSTAGE * STAGE_BYTES;
+constexpr size_t OFF_ROWEXP = OFF_OUT + 4 * (size_t)OUT_BYTES;
+constexpr size_t OFF_COLEXP = OFF_ROWEXP + 2 * TQ_ROWS * sizeof(int);
+constexpr size_t OFF_BARS = OFF_COLEXP + TQ_NP * sizeof(int);
+constexpr int NBARS = 9;  // full[2], empty[2], a_full, a_empty, t_full, t_empty, drain
+constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;
+constexpr size_t TQ_SMEM = OFF_MISC + 16;
+static_assert(TQ_SMEM <= 232448, "shared memory budget");
+
+enum LoadMode { LOAD_BLOCK = 0, LOAD_ROWS = 1, LOAD_PLAIN = 2 };
+
+__device__ __forceinline__ uint32_t b_row0(int c) { return c == 0 ? 0u : c == 1 ? 64u : c == 2 ? 112u : 144u; }
+
+__device__ __forceinline__ void set_abort(volatile int *abort_flag, DevStatus *st) {
+  *abort_flag = 1;
+  status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
+}
+
+// Exponent field of one 8-byte element (FP64, or the leading float of a pair, rebased).
+template <bool IN_DF>
+__device__ __forceinline__ int elem_expfield(unsigned long long bits) {
+  if (IN_DF) {
+    const int ef = (int)(((uint32_t)bits >> 23) & 0xff);
+    return ef ? ef - 127 + 1023 : 0;
+  }
+  return (int)((bits >> 52) & 0x7ff);
+}
+
+template <bool IN_DF>
+__device__ __forceinline__ long long elem_fix(unsigned long long bits, int E) {
+  if (IN_DF)
+    return fix54(__uint_as_float((uint32_t)bits), E) + fix54(__uint_as_float((uint32_t)(bits >> 32)), E);
+  return fix54(__longlong_as_double((long long)bits), E);
+}
+
 }  // namespace
 
 template <bool IN_DF>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
-    k_trsm_oz(const void *Win, int64_t ldw, double *Q, int64_t ldq, int64_t m, int n,
-              const double *__restrict__ Xp, int64_t rows_per_cta, bool bulk, DevStatus *st) {
-  using namespace tc;
+    k_trsm_oz(const void *Xin, int64_t ldx, double *Y, int64_t ldy, int64_t m, int n,
+              const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode, bool vec_store,
+              DevStatus *st) {
   if (status_failed(st)) return;
   extern __shared__ __align__(1024) uint8_t tq_smem[];
-  uint8_t *Bt = tq_smem;
-  uint8_t *A = Bt + TQ_B_BYTES;
-  uint8_t *stage = A + TQ_A_BYTES;
-  int *rowexp = (int *)(stage + TQ_STAGE_BYTES);
-  int *colexp = rowexp + TQ_ROWS;
-  uint64_t *bars = (uint64_t *)(colexp + TQ_NP);
-  uint32_t *tmem_slot = (uint32_t *)(bars + 2);
+  uint8_t *Bs = tq_smem + OFF_B;
+  uint8_t *As = tq_smem + OFF_A;
+  uint8_t *stage = tq_smem + OFF_STAGE;
+  uint8_t *outb = tq_smem + OFF_OUT;
+  int *rowexp = (int *)(tq_smem + OFF_ROWEXP);
+  int *colexp = (int *)(tq_smem + OFF_COLEXP);
+  uint64_t *bars = (uint64_t *)(tq_smem + OFF_BARS);
+  uint32_t *tmem_slot = (uint32_t *)(tq_smem + OFF_MISC);
+  volatile int *abort_flag = (volatile int *)(tq_smem + OFF_MISC + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t copy_bar = smem_addr(&bars[0]), mma_bar = smem_addr(&bars[1]);
+  const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]);
+  const uint32_t a_full = smem_addr(&bars[4]), a_empty = smem_addr(&bars[5]);
+  const uint32_t t_full = smem_addr(&bars[6]), t_empty = smem_addr(&bars[7]);
+  const uint32_t drain = smem_addr(&bars[8]);
 
-  if (warp == 0) tmem_alloc(tmem_slot, TQ_TMEM_COLS);
   if (tid == 0) {
-    mbar_init(copy_bar);
-    mbar_init(mma_bar);
-    asm volatile("fence.mbarrier_init.release.cluster;\n");
+    mbar_init_count(full0, 1);
+    mbar_init_count(full0 + 8, 1);
+    mbar_init_count(empty0, 4);
+    mbar_init_count(empty0 + 8, 4);
+    mbar_init_count(a_full, 4);
+    mbar_init_count(a_empty, 1);
+    mbar_init_count(t_full, 1);
+    mbar_init_count(t_empty, 4);
+    mbar_init_count(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (tid < TQ_NP) colexp[tid] = 0;
+  if (warp == W_MMA) tmem_alloc(tmem_slot, TQ_TMEM_COLS);
+  __syncthreads();
+
+  // ---- B's digit slices (all threads, once)
+  for (int e = tid; e < TQ_NP * TQ_NP; e += TQ_THREADS) {
+    const int k = e >> 6, j = e & 63;
+    if (k < n && j <= k) atomicMax(&colexp[k], expfield<false>(Bp + tri_idx(j, k)));
+  }
+  __syncthreads();
+  for (int e = tid; e < TQ_NP * TQ_NP / 2; e += TQ_THREADS) {
+    const int k = e >> 5, j = 2 * (e & 31), c = j >> 4;
+    if (k < 16 * c) continue;  // block c holds rows k >= 16c only
+    const int F = scale_exp(colexp[k]);
+    const long long za = (k < n && j <= k) ? fix54(Bp[tri_idx(j, k)], F) : 0;
+    const long long zb = (k < n && j + 1 <= k) ? fix54(Bp[tri_idx(j + 1, k)], F) : 0;
+    uint32_t w[NDIG];
+    digits2(za, zb, w);
+    const int kk = k - 16 * c, jj = j & 15;
+    const uint32_t off = b_row0(c) * 32 + (kk >> 3) * 256 + (jj >> 3) * 128 + (kk & 7) * 16 + (jj & 7) * 2;
+#pragma unroll
+    for (int p = 0; p < NDIG; ++p) *(uint32_t *)(Bs + (NDIG - 1 - p) * B_SLICE + off) = w[p];
+  }
+  fence_async_smem();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  // ---- X's slices (B operand): rows k (output column), K = j; X(j, k) = 0 for j > k
-  for (int e = tid; e < TQ_NP * TQ_NP; e += TQ_THREADS) {
-    const int k = e / TQ_NP, jj = e % TQ_NP;
-    if (k < n && jj <= k) atomicMax(&colexp[k], expfield<false>(Xp + tri_idx(jj, k)));
-  }
-  __syncthreads();
-  for (int e = tid; e < TQ_NP * TQ_NP / 2; e += TQ_THREADS) {
-    const int k = e / (TQ_NP / 2), jj = 2 * (e % (TQ_NP / 2));
-    const int f = scale_exp(colexp[k]);
-    long long x[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-      x[u] = (k < n && jj + u <= k) ? fixpt<false>(Xp + tri_idx(jj + u, k), f) : 0;
-#pragma unroll
-    for (int s = 0; s < SLICES; ++s)
-      *(uint32_t *)(Bt + (size_t)s * TQ_NP * TQ_NP * 2 + (size_t)kmajor_off(k, jj, TQ_NP) * 2) =
-          digit_bf16(x[0], s) | (digit_bf16(x[1], s) << 16);
-  }
-
   const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r_end = imin64(m, r_begin + rows_per_cta);
-  const uint32_t idesc = umma_idesc(TQ_ROWS, TQ_NP);
-  const int L = 32 * (warp & 3) + lane, half = warp >> 2;  // flush: tile row L, 32 columns
-  uint32_t copy_phase = 0, mma_phase = 0;
-  bool ok = true;
-  for (int64_t row0 = r_begin; row0 < r_end && ok; row0 += TQ_ROWS) {
-    const int rows = (int)imin64(TQ_ROWS, r_end - row0);
-    if (tid < TQ_ROWS) rowexp[tid] = 0;
-    // ---- the row tile in shared memory (row-major, n entries of 8 bytes per row)
-    if (bulk) {
-      __syncthreads();
-      if (tid == 0) {
-        const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 8u;
-        mbar_expect_tx(copy_bar, bytes);
-        const uint8_t *src = (const uint8_t *)Win + (size_t)row0 * (size_t)ldw * 8;
-        for (uint32_t off = 0; off < bytes; off += 16384)
-          bulk_load(smem_addr(stage) + off, src + off, bytes - off < 16384 ? bytes - off : 16384, copy_bar);
+  const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + TQ_ROWS - 1) / TQ_ROWS) : 0;
+
+  if (warp == W_LOAD) {
+    // ------------------------------------------------------------------ loader
+    int last_u[2] = {-1, -1};
+    for (int i = 0; i < ntiles && !*abort_flag; ++i) {
+      bool ok = true;
+      for (int q = 0; q < 4; ++q) {
+        const int u = 4 * i + q, slot = u & 1;
+        if (!mbar_wait_or_abort(empty0 + 8 * slot, ((u >> 1) & 1) ^ 1, abort_flag)) {
+          if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
+          ok = false;
+          break;
+        }
+        const int64_t r0 = r_begin + (int64_t)i * TQ_ROWS + TQ_SUB * q;
+        const int cnt = r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
+        uint8_t *dst = stage + (size_t)slot * STAGE_BYTES;
+        const uint32_t fb = full0 + 8 * slot;
+        if (cnt > 0 && load_mode == LOAD_BLOCK) {
+          if (lane == 0) {
+            mbar_expect_tx(fb, (uint32_t)cnt * 512u);
+            bulk_load(smem_addr(dst), (const uint8_t *)Xin + (size_t)r0 * 512, (uint32_t)cnt * 512u, fb);
+          }
+        } else if (cnt > 0 && load_mode == LOAD_ROWS) {
+          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
+          __syncwarp();
+          for (int r = lane; r < cnt; r += 32)
+            bulk_load(smem_addr(dst + r * 512), (const uint8_t *)Xin + (size_t)(r0 + r) * (size_t)ldx * 8,
+                      (uint32_t)n * 8u, fb);
+        } else {
+          const unsigned long long *src = (const unsigned long long *)Xin;
+          for (int e = lane; e < cnt * n; e += 32) {
+            const int r = e / n, cc = e - r * n;
+            ((unsigned long long *)dst)[r * TQ_NP + cc] = src[(r0 + r) * ldx + cc];
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(fb);
+        }
+        last_u[slot] = u;
       }
-      if (!__syncthreads_and(mbar_wait(copy_bar, copy_phase))) {
-        ok = false;
-        if (tid == 0) status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        mbar_wait(copy_bar, copy_phase);
+      if (!ok) break;
+    }
+    // copies still in flight (only after an abort) land before the CTA leaves
+    if (lane == 0)
+      for (int slot = 0; slot < 2; ++slot)
+        if (last_u[slot] >= 0) mbar_wait(full0 + 8 * slot, (last_u[slot] >> 1) & 1);
+  } else if (warp == W_MMA) {
+    // ------------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+      for (int i = 0; i < ntiles; ++i) {
+        if (!mbar_wait_or_abort(a_full, i & 1, abort_flag) ||
+            !mbar_wait_or_abort(t_empty, (i & 1) ^ 1, abort_flag)) {
+          if (!*abort_flag) set_abort(abort_flag, st);
+          break;
+        }
+        fence_after_sync();
+        // region 8 first, into region 7's columns
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
+          for (int s = 1; s < NDIG; ++s) {
+            const uint64_t ad = umma_desc(a0 + (uint32_t)s * A_SLICE + (uint32_t)c * 2 * A_LBO, A_LBO, A_SBO);
+            const uint64_t bd = umma_desc(b0 + (uint32_t)(8 - s) * B_SLICE + b_row0(c) * 32, 128, 256);
+            umma_bf16(tmem + (uint32_t)(7 * 64 + 16 * c), ad, bd, idesc, (c | (s - 1)) ? 1u : 0u);
+          }
+        }
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
+#pragma unroll 1
+          for (int g = 0; g < NDIG; ++g)
+            for (int s = 0; s <= g; ++s) {
+              const int t = g - s;
+              const uint64_t ad = umma_desc(a0 + (uint32_t)s * A_SLICE + (uint32_t)c * 2 * A_LBO, A_LBO, A_SBO);
+              const uint64_t bd = umma_desc(b0 + (uint32_t)t * B_SLICE + b_row0(c) * 32, 128, 256);
+              const uint32_t d = tmem + (uint32_t)(g * 64 + 16 * c);
+              if (g == NDIG - 1 && c == 0 && s == 0)
+                umma_scaled7(d, ad, bd, idesc);  // all 64 columns: D_8 (every K-step) times 2^-7
+              else
+                umma_bf16(d, ad, bd, idesc, (c | s) ? 1u : 0u);
+            }
+        }
+        umma_commit(a_empty);
+        umma_commit(t_full);
+      }
+      // every MMA issued so far completes before tensor memory is released
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------------ slicers
+    for (int i = 0; i < ntiles; ++i) {
+      const int buf = i & 1;
+      bool ok = true;
+      for (int q = 0; q < 4; ++q) {
+        const int u = 4 * i + q, slot = u & 1;
+        if (!mbar_wait_or_abort(full0 + 8 * slot, (u >> 1) & 1, abort_flag) ||
+            (q == 0 && !mbar_wait_or_abort(a_empty, (i & 1) ^ 1, abort_flag))) {
+          ok = false;
+          break;
+        }
+        const int64_t r0 = r_begin + (int64_t)i * TQ_ROWS + TQ_SUB * q;
+        const int cnt = r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
+        const uint8_t *src = stage + (size_t)slot * STAGE_BYTES;
+        const bool ca = 2 * lane < n, cb = 2 * lane + 1 < n;
+#pragma unroll 2
+        for (int rr = 0; rr < 8; ++rr) {
+          const int r = 8 * warp + rr, row = TQ_SUB * q + r;
+          const bool vr = r < cnt;
+          const ulonglong2 raw = *(const ulonglong2 *)(src + r * 512 + 16 * lane);
+          const unsigned long long ba = (vr && ca) ? raw.x : 0ULL, bb = (vr && cb) ? raw.y : 0ULL;
+          int mx = max(elem_expfield<IN_DF>(ba), elem_expfield<IN_DF>(bb));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          const int E = scale_exp(mx);
+          if (lane == 0) rowexp[buf * TQ_ROWS + row] = E;
+          uint32_t w[NDIG];
+          digits2(elem_fix<IN_DF>(ba, E), elem_fix<IN_DF>(bb, E), w);
+          const uint32_t off = (uint32_t)(row >> 3) * A_SBO + (uint32_t)(lane >> 2) * A_LBO + (row & 7) * 16 + (lane & 3) * 4;
+#pragma unroll
+          for (int p = 0; p < NDIG; ++p) *(uint32_t *)(As + (NDIG - 1 - p) * A_SLICE + off) = w[p];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+      }
+      if (!ok) {
+        if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
         break;
       }
-      copy_phase ^= 1;
-    } else {
-      for (int e = tid; e < rows * n; e += TQ_THREADS) {
-        const int r = e / n, c = e - r * n;
-        ((unsigned long long *)stage)[e] = ((const unsigned long long *)Win)[(row0 + r) * ldw + c];
-      }
-      __syncthreads();
-    }
-    // ---- row scales
-    {
-      const int r = tid >> 1, c0 = 32 * (tid & 1);
-      int mx = 0;
-      if (r < rows)
-        for (int c = c0; c < c0 + 32 && c < n; ++c) mx = max(mx, expfield<IN_DF>(stage + ((size_t)r * n + c) * 8));
-      atomicMax(&rowexp[r], mx);
-    }
-    __syncthreads();
-    // ---- two K halves: slice W's columns 32 hk .. +31, then their products
-    for (int hk = 0; hk < 2 && ok; ++hk) {
-      for (int e = tid; e < TQ_ROWS * 16; e += TQ_THREADS) {
-        const int r = e / 16, jj = 2 * (e % 16), j = 32 * hk + jj;
-        const int er = scale_exp(rowexp[r]);
-        long long x[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          x[u] = (r < rows && j + u < n) ? fixpt<IN_DF>(stage + ((size_t)r * n + j + u) * 8, er) : 0;
-#pragma unroll
-        for (int s = 0; s < SLICES; ++s)
-          *(uint32_t *)(A + (size_t)s * TQ_ROWS * 32 * 2 + (size_t)kmajor_off(r, jj, 32) * 2) =
-              digit_bf16(x[0], s) | (digit_bf16(x[1], s) << 16);
-      }
       fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        fence_after_sync();
-        const uint32_t abase = smem_addr(A), bbase = smem_addr(Bt);
-        for (int g = 0; g < SLICES; ++g) {
-          for (int s = 0; s <= g; ++s) {
-            const int t = g - s;
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t ad = umma_desc(abase + (uint32_t)(s * TQ_ROWS * 32 * 2) + 256u * kk, 128, 512);
-              const uint64_t bd = umma_desc(bbase + (uint32_t)(t * TQ_NP * TQ_NP * 2) + 128u * (4 * hk + 2 * kk),
-                                            128, 1024);
-              umma_bf16(tmem + (uint32_t)(g * 64), ad, bd, idesc, (hk | s | kk) ? 1u : 0u);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a_full);
+    }
+  } else {
+    // ------------------------------------------------------------------ recombination
+    const int quad = warp & 3, L = 32 * quad + lane;
+    uint8_t *ob = outb + (size_t)quad * OUT_BYTES;
+    const uint32_t tq = tmem + ((uint32_t)(32 * quad) << 16);
+    for (int i = 0; i < ntiles; ++i) {
+      if (!mbar_wait_or_abort(t_full, i & 1, abort_flag)) {
+        if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
+        break;
+      }
+      fence_after_sync();
+      const int er = rowexp[(i & 1) * TQ_ROWS + L];
+      const int64_t row0 = r_begin + (int64_t)i * TQ_ROWS + 32 * quad;
+#pragma unroll 1
+      for (int cg = 0; cg < 8; ++cg) {
+        uint32_t v[NDIG][8];
+#pragma unroll
+        for (int g = 0; g < NDIG; ++g) tmem_ld8(tq + (uint32_t)(g * 64 + 8 * cg), v[g]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const long long th = ((long long)acc_to_int(v[0][c]) << 21) + ((long long)acc_to_int(v[1][c]) << 14) +
+                               ((long long)acc_to_int(v[2][c]) << 7) + (long long)acc_to_int(v[3][c]);
+          const long long tl = ((long long)acc_to_int(v[4][c]) << 21) + ((long long)acc_to_int(v[5][c]) << 14) +
+                               ((long long)acc_to_int(v[6][c]) << 7) + (long long)acc_to_int(v[7][c]);
+          const long long t = (th << 25) + (tl >> 3);  // T / 8 (|T| < 2^65)
+          double y = (double)t;
+          const int e = er + scale_exp(colexp[8 * cg + c]) - 56;
+          y = t != 0 ? __longlong_as_double(__double_as_longlong(y) + ((long long)e << 52)) : 0.0;
+          *(double *)(ob + lane * OUT_PITCH + 8 * c) = y;
+        }
+        __syncwarp();
+        // lane 4a + b stores row 8p + a of this warp's 32, columns 8 cg + 2b, 8 cg + 2b + 1
+        const int a = lane >> 2, b = lane & 3, k0 = 8 * cg + 2 * b;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int rl = 8 * p + a;
+          const double y0 = *(const double *)(ob + rl * OUT_PITCH + 16 * b);
+          const double y1 = *(const double *)(ob + rl * OUT_PITCH + 16 * b + 8);
+          const int64_t grow = row0 + rl;
+          if (grow < r_end) {
+            double *dst = Y + grow * ldy + k0;
+            if (vec_store && k0 + 1 < n) {
+              *(double2 *)dst = make_double2(y0, y1);
+            } else {
+              if (k0 < n) dst[0] = y0;
+              if (k0 + 1 < n) dst[1] = y1;
             }
           }
         }
-        umma_commit(mma_bar);
+        __syncwarp();
       }
-      if (!__syncthreads_and(mbar_wait(mma_bar, mma_phase))) {
-        ok = false;
-        if (tid == 0) status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        mbar_wait(mma_bar, mma_phase);
-        break;
-      }
-      mma_phase ^= 1;
-      fence_after_sync();
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(t_empty);
     }
-    if (!ok) break;
-    // ---- flush: row L, columns 32 half .. +31 -> FP64 Q entries into the stage
-    {
-      const int er = scale_exp(rowexp[L]);
-      double *qrow = (double *)stage + (size_t)L * n;
-#pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
-        uint32_t v[SLICES][8];
-#pragma unroll
-        for (int g = 0; g < SLICES; ++g)
-          tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(g * 64 + 32 * half + 8 * c8), v[g]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float sh = 0.f, sl = 0.f;
-#pragma unroll
-          for (int g = 0; g < SLICES; ++g) {
-            const float tv = __uint_as_float(v[g][i]) * pow2f(-14 - 7 * g);
-            const float t = __fadd_rn(sh, tv);
-            const float z = __fsub_rn(t, sh);
-            sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(tv, z)));
-            sh = t;
-          }
-          const int k = 32 * half + 8 * c8 + i;
-          if (L < rows && k < n) qrow[k] = scale_pow2(df2d(sh, sl), er + scale_exp(colexp[k]));
-        }
-      }
-    }
-    fence_before_sync();
-    fence_async_smem();
-    __syncthreads();
-    // ---- the tile back to Q (rows row0 .. row0 + rows - 1)
-    if (bulk) {
-      if (tid == 0) {
-        const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 8u;
-        uint8_t *dst = (uint8_t *)Q + (size_t)row0 * (size_t)ldq * 8;
-        for (uint32_t off = 0; off < bytes; off += 16384)
-          bulk_store(dst + off, smem_addr(stage) + off, bytes - off < 16384 ? bytes - off : 16384);
-        bulk_store_commit();
-        bulk_store_wait();
-      }
-    } else {
-      for (int e = tid; e < rows * n; e += TQ_THREADS) {
-        const int r = e / n, c = e - r * n;
-        Q[(row0 + r) * ldq + c] = ((const double *)stage)[e];
-      }
-    }
-    __syncthreads();
   }
-  if (bulk && tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");  // stores done
-  fence_before_sync();
+
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, TQ_TMEM_COLS);
+  fence_after_sync();
+  if (warp == W_MMA) tmem_free(tmem, TQ_TMEM_COLS);
 }
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
@@ -220,21 +353,25 @@ bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 cudaError_t launch_trsm_oz(const void *W, bool in_df, int64_t ldw, double *Q, int64_t ldq, int64_t m,
                            int64_t n, const double *Xpacked, int num_sms, DevStatus *st,
                            cudaStream_t s) {
-  const size_t smem = TQ_B_BYTES + TQ_A_BYTES + TQ_STAGE_BYTES + (TQ_ROWS + TQ_NP) * sizeof(int) + 32;
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
-  const bool bulk = ldw == n && ldq == n && ((n * 8) % 16 == 0) && (((uintptr_t)W & 15) == 0) &&
-                    (((uintptr_t)Q & 15) == 0);
+  const bool aligned = ((uintptr_t)W & 15) == 0;
+  const int load_mode = (aligned && n == TQ_NP && ldw == TQ_NP) ? LOAD_BLOCK
+                        : (aligned && (n * 8) % 16 == 0 && (ldw * 8) % 16 == 0) ? LOAD_ROWS
+                                                                                 : LOAD_PLAIN;
+  const bool vec_store = ((uintptr_t)Q & 15) == 0 && (ldq % 2) == 0;
   cudaError_t e;
   if (in_df) {
-    e = cudaFuncSetAttribute(k_trsm_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_trsm_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
     if (e != cudaSuccess) return e;
-    k_trsm_oz<true><<<(unsigned)ctas, TQ_THREADS, smem, s>>>(W, ldw, Q, ldq, m, (int)n, Xpacked, rows_per_cta, bulk, st);
+    k_trsm_oz<true><<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(W, ldw, Q, ldq, m, (int)n, Xpacked, rows_per_cta,
+                                                                load_mode, vec_store, st);
   } else {
-    e = cudaFuncSetAttribute(k_trsm_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_trsm_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
     if (e != cudaSuccess) return e;
-    k_trsm_oz<false><<<(unsigned)ctas, TQ_THREADS, smem, s>>>(W, ldw, Q, ldq, m, (int)n, Xpacked, rows_per_cta, bulk, st);
+    k_trsm_oz<false><<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(W, ldw, Q, ldq, m, (int)n, Xpacked, rows_per_cta,
+                                                                 load_mode, vec_store, st);
   }
   return cudaGetLastError();
 }
