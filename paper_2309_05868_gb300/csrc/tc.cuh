@@ -115,7 +115,23 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
                  "=r"(r[6]), "=r"(r[7])
                : "r"(addr));
 }
+// 4 consecutive columns of this warp's 32 tensor-memory lanes (thread = lane).
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Orders uses of tcgen05.ld destination registers after the tcgen05.wait::ld that completes
+// them: the compiler does not know the loads are asynchronous.
+template <int R, int C>
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&v)[R][C]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < C; ++c) asm volatile("" : "+r"(v[r][c]));
+}
 
 // Exponent field of an element rebased to the FP64 bias; 0 for zero / subnormal.
 template <bool IN_DF>

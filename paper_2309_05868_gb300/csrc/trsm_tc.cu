@@ -83,6 +83,87 @@ __device__ __forceinline__ long long elem_fix(unsigned long long bits, int E) {
   return fix54(__longlong_as_double((long long)bits), E);
 }
 
+// Descriptor offsets (16-byte units) of slice s / K-step c in A and slice t / K-step c in B.
+__device__ __forceinline__ constexpr uint64_t a_off(int s, int c) { return ((uint64_t)s * A_SLICE + (uint64_t)c * 2 * A_LBO) >> 4; }
+__device__ __forceinline__ constexpr uint64_t b_off(int t, int c) {
+  return ((uint64_t)t * B_SLICE + (uint64_t)(c == 0 ? 0 : c == 1 ? 64 : c == 2 ? 112 : 144) * 32) >> 4;
+}
+
+// One tile's MMAs, fully unrolled so that every descriptor is a base plus a constant (a
+// single issuing thread otherwise spends more time forming descriptors than the tensor core
+// spends on the products).  Region 8 goes first into region 7's columns; within a K-step the
+// (s, t) order walks across regions.
+__device__ __forceinline__ void issue_tile(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
+#pragma unroll
+    for (int s = 1; s < NDIG; ++s)
+      umma_bf16(tmem + (uint32_t)(7 * 64 + 16 * c), ad0 + a_off(s, c), bd0 + b_off(8 - s, c), idesc,
+                (c | (s - 1)) ? 1u : 0u);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
+#pragma unroll
+    for (int s = 0; s < NDIG; ++s)
+#pragma unroll
+      for (int t = 0; t < NDIG - s; ++t) {
+        const uint32_t d = tmem + (uint32_t)((s + t) * 64 + 16 * c);
+        if (c == 0 && s == 0 && t == NDIG - 1)
+          umma_scaled7(d, ad0 + a_off(s, c), bd0 + b_off(t, c), idesc);  // D_8 (every K-step) x 2^-7
+        else
+          umma_bf16(d, ad0 + a_off(s, c), bd0 + b_off(t, c), idesc, (c | s) ? 1u : 0u);
+      }
+  }
+}
+
+// Four columns (group h of 16) of a recombination warp's 32 rows: regions -> T -> FP64 into the
+// warp's buffer; after every second group the buffer's 8 columns go out so that four lanes
+// store 64 contiguous bytes of one row of Y.
+__device__ __forceinline__ void emit_group(const uint32_t (&v)[NDIG][4], int h, int er, const int *colexp,
+                                           uint8_t *ob, int lane, double *Y, int64_t ldy, int64_t row0,
+                                           int64_t r_end, int n, bool vec_store) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long th = ((long long)acc_to_int(v[0][c]) << 21) + ((long long)acc_to_int(v[1][c]) << 14) +
+                         ((long long)acc_to_int(v[2][c]) << 7) + (long long)acc_to_int(v[3][c]);
+    const long long tl = ((long long)acc_to_int(v[4][c]) << 21) + ((long long)acc_to_int(v[5][c]) << 14) +
+                         ((long long)acc_to_int(v[6][c]) << 7) + (long long)acc_to_int(v[7][c]);
+    const long long t = (th << 25) + (tl >> 3);  // T / 8 (|T| < 2^65)
+    double y = (double)t;
+    const int e = er + scale_exp(colexp[4 * h + c]) - 56;
+    y = t != 0 ? __longlong_as_double(__double_as_longlong(y) + ((long long)e << 52)) : 0.0;
+    *(double *)(ob + lane * OUT_PITCH + 8 * (4 * (h & 1) + c)) = y;
+  }
+  if ((h & 1) == 0) return;
+  __syncwarp();
+  // lane 4a + b stores row 8p + a of the warp's 32, columns 8 cg + 2b, 8 cg + 2b + 1
+  const int a = lane >> 2, b = lane & 3, k0 = 8 * (h >> 1) + 2 * b;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int rl = 8 * p + a;
+    const double y0 = *(const double *)(ob + rl * OUT_PITCH + 16 * b);
+    const double y1 = *(const double *)(ob + rl * OUT_PITCH + 16 * b + 8);
+    const int64_t grow = row0 + rl;
+    if (grow < r_end) {
+      double *dst = Y + grow * ldy + k0;
+      if (vec_store && k0 + 1 < n) {
+        *(double2 *)dst = make_double2(y0, y1);
+      } else {
+        if (k0 < n) dst[0] = y0;
+        if (k0 + 1 < n) dst[1] = y1;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void load_group(uint32_t tq, int h, uint32_t (&v)[NDIG][4]) {
+#pragma unroll
+  for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + 4 * h), v[g]);
+}
+
 }  // namespace
 
 template <bool IN_DF>
@@ -199,7 +280,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   } else if (warp == W_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+      const uint64_t ad0 = umma_desc(smem_addr(As), A_LBO, A_SBO), bd0 = umma_desc(smem_addr(Bs), 128, 256);
       for (int i = 0; i < ntiles; ++i) {
         if (!mbar_wait_or_abort(a_full, i & 1, abort_flag) ||
             !mbar_wait_or_abort(t_empty, (i & 1) ^ 1, abort_flag)) {
@@ -207,32 +288,10 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
           break;
         }
         fence_after_sync();
-        // region 8 first, into region 7's columns
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
-          for (int s = 1; s < NDIG; ++s) {
-            const uint64_t ad = umma_desc(a0 + (uint32_t)s * A_SLICE + (uint32_t)c * 2 * A_LBO, A_LBO, A_SBO);
-            const uint64_t bd = umma_desc(b0 + (uint32_t)(8 - s) * B_SLICE + b_row0(c) * 32, 128, 256);
-            umma_bf16(tmem + (uint32_t)(7 * 64 + 16 * c), ad, bd, idesc, (c | (s - 1)) ? 1u : 0u);
-          }
-        }
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
-#pragma unroll 1
-          for (int g = 0; g < NDIG; ++g)
-            for (int s = 0; s <= g; ++s) {
-              const int t = g - s;
-              const uint64_t ad = umma_desc(a0 + (uint32_t)s * A_SLICE + (uint32_t)c * 2 * A_LBO, A_LBO, A_SBO);
-              const uint64_t bd = umma_desc(b0 + (uint32_t)t * B_SLICE + b_row0(c) * 32, 128, 256);
-              const uint32_t d = tmem + (uint32_t)(g * 64 + 16 * c);
-              if (g == NDIG - 1 && c == 0 && s == 0)
-                umma_scaled7(d, ad, bd, idesc);  // all 64 columns: D_8 (every K-step) times 2^-7
-              else
-                umma_bf16(d, ad, bd, idesc, (c | s) ? 1u : 0u);
-            }
-        }
+        // opaque per tile: keeps the compiler from hoisting all 172 descriptor sums into registers
+        uint64_t ad = ad0, bd = bd0;
+        asm volatile("" : "+l"(ad), "+l"(bd));
+        issue_tile(tmem, ad, bd);
         umma_commit(a_empty);
         umma_commit(t_full);
       }
@@ -257,19 +316,27 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int cnt = r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
         const uint8_t *src = stage + (size_t)slot * STAGE_BYTES;
         const bool ca = 2 * lane < n, cb = 2 * lane + 1 < n;
-#pragma unroll 2
-        for (int rr = 0; rr < 8; ++rr) {
-          const int r = 8 * warp + rr, row = TQ_SUB * q + r;
-          const bool vr = r < cnt;
-          const ulonglong2 raw = *(const ulonglong2 *)(src + r * 512 + 16 * lane);
-          const unsigned long long ba = (vr && ca) ? raw.x : 0ULL, bb = (vr && cb) ? raw.y : 0ULL;
-          int mx = max(elem_expfield<IN_DF>(ba), elem_expfield<IN_DF>(bb));
+        unsigned long long ea[8], eb[8];
+        int mx[8];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const int E = scale_exp(mx);
+        for (int rr = 0; rr < 8; ++rr) {
+          const int r = 8 * warp + rr;
+          const ulonglong2 raw = *(const ulonglong2 *)(src + r * 512 + 16 * lane);
+          ea[rr] = (r < cnt && ca) ? raw.x : 0ULL;
+          eb[rr] = (r < cnt && cb) ? raw.y : 0ULL;
+          mx[rr] = max(elem_expfield<IN_DF>(ea[rr]), elem_expfield<IN_DF>(eb[rr]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) mx[rr] = max(mx[rr], __shfl_xor_sync(0xffffffffu, mx[rr], o));
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+          const int row = TQ_SUB * q + 8 * warp + rr;
+          const int E = scale_exp(mx[rr]);
           if (lane == 0) rowexp[buf * TQ_ROWS + row] = E;
           uint32_t w[NDIG];
-          digits2(elem_fix<IN_DF>(ba, E), elem_fix<IN_DF>(bb, E), w);
+          digits2(elem_fix<IN_DF>(ea[rr], E), elem_fix<IN_DF>(eb[rr], E), w);
           const uint32_t off = (uint32_t)(row >> 3) * A_SBO + (uint32_t)(lane >> 2) * A_LBO + (row & 7) * 16 + (lane & 3) * 4;
 #pragma unroll
           for (int p = 0; p < NDIG; ++p) *(uint32_t *)(As + (NDIG - 1 - p) * A_SLICE + off) = w[p];
@@ -298,48 +365,30 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       fence_after_sync();
       const int er = rowexp[(i & 1) * TQ_ROWS + L];
       const int64_t row0 = r_begin + (int64_t)i * TQ_ROWS + 32 * quad;
+      // two register sets: the loads of one 4-column group overlap the recombination of another
+      uint32_t va[NDIG][4], vb[NDIG][4];
+      load_group(tq, 0, va);
+      tmem_wait_ld();
+      tmem_regs_ready(va);
 #pragma unroll 1
-      for (int cg = 0; cg < 8; ++cg) {
-        uint32_t v[NDIG][8];
-#pragma unroll
-        for (int g = 0; g < NDIG; ++g) tmem_ld8(tq + (uint32_t)(g * 64 + 8 * cg), v[g]);
+      for (int h = 0; h < 16; h += 2) {
+        load_group(tq, h + 1, vb);
+        emit_group(va, h, er, colexp, ob, lane, Y, ldy, row0, r_end, n, vec_store);
         tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const long long th = ((long long)acc_to_int(v[0][c]) << 21) + ((long long)acc_to_int(v[1][c]) << 14) +
-                               ((long long)acc_to_int(v[2][c]) << 7) + (long long)acc_to_int(v[3][c]);
-          const long long tl = ((long long)acc_to_int(v[4][c]) << 21) + ((long long)acc_to_int(v[5][c]) << 14) +
-                               ((long long)acc_to_int(v[6][c]) << 7) + (long long)acc_to_int(v[7][c]);
-          const long long t = (th << 25) + (tl >> 3);  // T / 8 (|T| < 2^65)
-          double y = (double)t;
-          const int e = er + scale_exp(colexp[8 * cg + c]) - 56;
-          y = t != 0 ? __longlong_as_double(__double_as_longlong(y) + ((long long)e << 52)) : 0.0;
-          *(double *)(ob + lane * OUT_PITCH + 8 * c) = y;
+        tmem_regs_ready(vb);
+        if (h + 2 < 16) {
+          load_group(tq, h + 2, va);
+        } else {  // every region read: the next tile's MMAs may start
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(t_empty);
         }
-        __syncwarp();
-        // lane 4a + b stores row 8p + a of this warp's 32, columns 8 cg + 2b, 8 cg + 2b + 1
-        const int a = lane >> 2, b = lane & 3, k0 = 8 * cg + 2 * b;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int rl = 8 * p + a;
-          const double y0 = *(const double *)(ob + rl * OUT_PITCH + 16 * b);
-          const double y1 = *(const double *)(ob + rl * OUT_PITCH + 16 * b + 8);
-          const int64_t grow = row0 + rl;
-          if (grow < r_end) {
-            double *dst = Y + grow * ldy + k0;
-            if (vec_store && k0 + 1 < n) {
-              *(double2 *)dst = make_double2(y0, y1);
-            } else {
-              if (k0 < n) dst[0] = y0;
-              if (k0 + 1 < n) dst[1] = y1;
-            }
-          }
+        emit_group(vb, h + 1, er, colexp, ob, lane, Y, ldy, row0, r_end, n, vec_store);
+        if (h + 2 < 16) {
+          tmem_wait_ld();
+          tmem_regs_ready(va);
         }
-        __syncwarp();
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(t_empty);
     }
   }
 
