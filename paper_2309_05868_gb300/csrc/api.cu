@@ -209,6 +209,14 @@ randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const void *X, bool x_df, int
 
 bool use_tc_solve(const randqr_ctx *ctx, int64_t n) { return ctx->use_tc && rq::trsm_oz_supported(n); }
 
+// G += X^T X on the tensor cores: the pipelined kernel for n <= 64, the older one up to 128.
+cudaError_t launch_gram_tc(const randqr_ctx *ctx, const void *X, bool x_df, int64_t ldx, int64_t m,
+                           int64_t n, double *G, cudaStream_t s) {
+  if (rq::gram_split_supported(n))
+    return rq::launch_gram_split(X, x_df, ldx, m, n, G, ctx->num_sms, ctx->status_dev, s);
+  return rq::launch_gram_oz(X, x_df, ldx, m, n, G, !x_df, ctx->num_sms, ctx->status_dev, s);
+}
+
 randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy,
                           int64_t m, int64_t n, double shift_coeff, const double *Rprev,
                           double *Rnext, double *Rdense, int64_t ldr, int stage,
@@ -217,7 +225,7 @@ randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double 
   RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
   if (ctx->use_tc && rq::gram_oz_supported(n)) {
     RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
-      return rq::launch_gram_oz(X, false, ldx, m, n, w.G, true, ctx->num_sms, ctx->status_dev, s);
+      return launch_gram_tc(ctx, X, false, ldx, m, n, w.G, s);
     }));
   } else {
     RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
@@ -424,7 +432,7 @@ static randqr_status factor_df(randqr_ctx *ctx, const double *V, int64_t m, int6
   RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
   if (ctx->use_tc && rq::gram_oz_supported(n)) {
     RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
-      return rq::launch_gram_oz(Q, true, ldq, m, n, w.G, false, ctx->num_sms, ctx->status_dev, s);
+      return launch_gram_tc(ctx, Q, true, ldq, m, n, w.G, s);
     }));
   } else {
     RQ_CUDA(timed(ctx, s, rq::K_GRAM_DF, [&] {

@@ -183,7 +183,11 @@ bool trsm_oz_supported(int64_t n);
 cudaError_t launch_trsm_oz(const void *W, bool in_df, int64_t ldw, double *Q, int64_t ldq, int64_t m,
                            int64_t n, const double *Xpacked, int num_sms, DevStatus *st,
                            cudaStream_t s);
-// Gram from exact split products on the tensor cores (gram_tc.cu)
+// Gram from exact split products on the tensor cores, n <= 64 (gram_split.cu)
+bool gram_split_supported(int64_t n);
+cudaError_t launch_gram_split(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
+                              int num_sms, DevStatus *st, cudaStream_t s);
+// Gram from exact split products on the tensor cores, n <= 128 (gram_tc.cu)
 bool gram_oz_supported(int64_t n);
 cudaError_t launch_gram_oz(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n,
                            double *Gpacked, bool acc_f64, int num_sms, DevStatus *st,
