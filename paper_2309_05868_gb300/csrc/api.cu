@@ -296,6 +296,7 @@ randqr_status randqr_destroy(randqr_ctx *ctx) {
 
 randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable) {
   if (!ctx) return RANDQR_ERR_ARG;
+  if (ctx->use_tc != (enable != 0) && ctx->batcher) rq_batcher_destroy(ctx);  // graphs hold the old kernels
   ctx->use_tc = enable != 0;
   return RANDQR_OK;
 }

@@ -150,6 +150,7 @@ randqr_status build_plan(randqr_ctx *ctx, randqr_batcher *b, const randqr_batch_
       destroy_plan(p);
       return RANDQR_ERR_CUDA;
     }
+    c->use_tc = ctx->use_tc;
     p->streams.push_back(s);
     p->subs.push_back(c);
   }

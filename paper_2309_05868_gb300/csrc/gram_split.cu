@@ -316,13 +316,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           tmem_regs_ready(v);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const long long th = ((long long)acc_to_int(v[0][c]) << 21) + ((long long)acc_to_int(v[1][c]) << 14) +
-                                 ((long long)acc_to_int(v[2][c]) << 7) + (long long)acc_to_int(v[3][c]);
-            const long long tl = ((long long)acc_to_int(v[4][c]) << 21) + ((long long)acc_to_int(v[5][c]) << 14) +
-                                 ((long long)acc_to_int(v[6][c]) << 7) + (long long)acc_to_int(v[7][c]);
-            const long long t = (th << 23) + (tl >> 5);  // T / 32 (|T| < 2^67)
-            const int e = ebase + ce[k0 + c];
-            const double y = t != 0 ? __longlong_as_double(__double_as_longlong((double)t) + ((long long)e << 52)) : 0.0;
+            const long long t = recombine8<5>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+            const double y = int_times_pow2(t, ebase + ce[k0 + c]);  // T / 32 (|T| < 2^67)
             S[4 * h4 + c] += y;
           }
         }

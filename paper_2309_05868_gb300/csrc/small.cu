@@ -33,8 +33,9 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // Householder QR, R only.  Column j: sigma = ||A[j+1:, j]||^2, beta = -sign(a_jj) sqrt(a_jj^2
 // + sigma), v = A[j:, j] / (a_jj - beta) with v_j = 1, tau = (beta - a_jj) / beta, then
 // A[j:, j+1:] -= tau v (v^T A[j:, j+1:]).  The recurrence is LAPACK's dgeqr2 (Golub & Van
-// Loan Alg. 5.2.1).  A is row-major rows x n; it lives in shared memory when it fits and is
-// updated in place in global memory (L2) otherwise.
+// Loan Alg. 5.2.1).  A is row-major rows x n; in shared memory (row pitch n + 1, so that a
+// warp walking down a column touches different banks) when it fits, else updated in place in
+// global memory (L2, pitch n).  v is applied as A[i, j] * (1 / (a_jj - beta)) on the fly.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, int n,
                                                         bool use_smem, double *Rp,
@@ -42,52 +43,54 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, in
   if (status_failed(st)) return;
   extern __shared__ double sm[];
   __shared__ double red[32];
-  __shared__ double s_tau, s_v0;
+  __shared__ double s_tau, s_rv0;
   double *w = sm;                         // n
-  double *A = use_smem ? sm + n : Ag;     // rows * n
+  double *A = use_smem ? sm + n : Ag;     // rows x ld
+  const int ld = use_smem ? n + 1 : n;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (use_smem) {
-    for (int e = tid; e < rows * n; e += nt) A[e] = Ag[e];
+    for (int e = tid; e < rows * n; e += nt) A[(e / n) * ld + e % n] = Ag[e];
     __syncthreads();
   }
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int j = 0; j < n; ++j) {
     double part = 0.0;
-    for (int i = j + 1 + tid; i < rows; i += nt) part = fma(A[i * n + j], A[i * n + j], part);
+    for (int i = j + 1 + tid; i < rows; i += nt) part = fma(A[i * ld + j], A[i * ld + j], part);
     const double sigma = block_sum(part, red);
     if (tid == 0) {
-      const double x0 = A[j * n + j];
+      const double x0 = A[j * ld + j];
       if (sigma == 0.0) {
         s_tau = 0.0;
       } else {
         const double alpha = sqrt(x0 * x0 + sigma);
         const double beta = (x0 >= 0.0) ? -alpha : alpha;
-        s_v0 = x0 - beta;
+        s_rv0 = 1.0 / (x0 - beta);
         s_tau = (beta - x0) / beta;
-        A[j * n + j] = beta;
+        A[j * ld + j] = beta;
       }
     }
     __syncthreads();
     const double tau = s_tau;
     if (tau == 0.0) continue;
-    const double v0 = s_v0;
-    for (int i = j + 1 + tid; i < rows; i += nt) A[i * n + j] /= v0;
-    __syncthreads();
+    const double rv0 = s_rv0;
     // w_k = tau (a_jk + sum_{i>j} v_i a_ik), one warp per column k
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int k = j + 1 + wid; k < n; k += nw) {
       double acc = 0.0;
-      for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(A[i * n + j], A[i * n + k], acc);
+      for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(A[i * ld + j], A[i * ld + k], acc);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) w[k] = tau * (A[j * n + k] + acc);
+      if (lane == 0) w[k] = tau * fma(acc, rv0, A[j * ld + k]);
     }
     __syncthreads();
-    const int ncols = n - j - 1;
-    for (int e = tid; e < (rows - j) * ncols; e += nt) {
-      const int i = j + e / ncols, k = j + 1 + e % ncols;
-      if (i == j)
-        A[j * n + k] -= w[k];
-      else
-        A[i * n + k] = fma(-A[i * n + j], w[k], A[i * n + k]);
+    // A[j, k] -= w_k;  A[i, k] -= v_i w_k  (i > j, k > j); 64-column strips, no index division
+    for (int i0 = j; i0 < rows; i0 += nt / 64) {
+      const int i = i0 + tid / 64;
+      if (i >= rows) break;
+      for (int k = j + 1 + (tid & 63); k < n; k += 64) {
+        if (i == j)
+          A[j * ld + k] -= w[k];
+        else
+          A[i * ld + k] = fma(-A[i * ld + j] * rv0, w[k], A[i * ld + k]);
+      }
     }
     __syncthreads();
   }
@@ -97,14 +100,14 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, in
     while (j * (j + 1) / 2 > e) --j;
     while ((j + 1) * (j + 2) / 2 <= e) ++j;
     const int k = e - j * (j + 1) / 2;
-    const double d = A[k * n + k];
-    Rp[e] = (d < 0.0) ? -A[k * n + j] : A[k * n + j];
+    const double d = A[k * ld + k];
+    Rp[e] = (d < 0.0) ? -A[k * ld + j] : A[k * ld + j];
   }
   if (tid == 0) {
     double dmin = INFINITY, dmax = 0.0;
     int bad = 0;
     for (int k = 0; k < n; ++k) {
-      const double d = fabs(A[k * n + k]);
+      const double d = fabs(A[k * ld + k]);
       if (!(d > 0.0) || !isfinite(d)) bad = bad ? bad : k + 1;
       dmin = fmin(dmin, d);
       dmax = fmax(dmax, d);
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, in
 
 cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
                         cudaStream_t s) {
-  size_t smem = sizeof(double) * (size_t)(n + rows * n);
+  size_t smem = sizeof(double) * (size_t)(n + rows * (n + 1));
   bool use_smem = smem <= 200 * 1024;
   size_t dyn = use_smem ? smem : sizeof(double) * (size_t)n;
   if (dyn > 48 * 1024) {

@@ -289,5 +289,44 @@ __device__ __forceinline__ int acc_to_int(uint32_t bits) {
   return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
+// ---------------------------------------------------------------------------------------
+// Recombination of eight region accumulators (exact FP32 integers, |D_g| <= 2^22) into
+//   T = sum_g 2^(7 (7 - g)) D_g,
+// returned as T / 2^SH in an int64.  Each accumulator goes through one FP32 add of
+// 1.5 * 2^23, after which its bit pattern is 0x4B400000 + D_g; the patterns are summed with
+// 32 x 32 -> 64-bit multiply-adds and the offsets removed by one constant.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mad_wide(uint32_t a, uint32_t b, unsigned long long c) {
+  unsigned long long d;
+  asm("mad.wide.u32 %0, %1, %2, %3;\n" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t acc_bits(uint32_t v) {
+  return __float_as_uint(__uint_as_float(v) + 12582912.0f);
+}
+template <int SH>
+__device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
+                                                uint32_t d5, uint32_t d6, uint32_t d7) {
+  // sum of the offsets 0x4B400000 * (2^21 + 2^14 + 2^7 + 1), for each half
+  constexpr unsigned long long OFF = 0x4B400000ULL * ((1ULL << 21) + (1ULL << 14) + (1ULL << 7) + 1ULL);
+  unsigned long long h = mad_wide(acc_bits(d0), 1u << 21, 0ULL);
+  h = mad_wide(acc_bits(d1), 1u << 14, h);
+  h = mad_wide(acc_bits(d2), 1u << 7, h);
+  h += acc_bits(d3);
+  unsigned long long l = mad_wide(acc_bits(d4), 1u << 21, 0ULL);
+  l = mad_wide(acc_bits(d5), 1u << 14, l);
+  l = mad_wide(acc_bits(d6), 1u << 7, l);
+  l += acc_bits(d7);
+  const long long th = (long long)(h - OFF), tl = (long long)(l - OFF);
+  return (th << (28 - SH)) + (tl >> SH);
+}
+
+// (double) t * 2^e for an integer t != 0 with |t| < 2^63 and a result in the normal range;
+// 0 for t == 0.  The scaling adds e to the exponent field through the high word.
+__device__ __forceinline__ double int_times_pow2(long long t, int e) {
+  const double y = (double)t;
+  return t != 0 ? __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y)) : 0.0;
+}
+
 }  // namespace tc
 }  // namespace rq

@@ -19,10 +19,12 @@
 // that level whatever kappa(V) is.
 //
 // One CTA per SM, persistent over 128-row tiles; warps specialise:
-//   warps 0-3 cut rows into digit slices (shared memory A: 8 slices x 128 rows x 64 K, f16),
-//   warps 4-7 read tensor memory back, recombine and store rows of Y,
-//   warp 8 loads 32-row sub-tiles of X into a two-slot ring with bulk copies,
-//   warp 9 owns tensor memory and issues the MMAs,
+//   warps 0-7 cut rows into digit slices (shared memory A: 8 slices x 128 rows x 64 K, f16);
+//     warps 0-3 take the even 32-row sub-tiles, 4-7 the odd ones, one 8-row group each,
+//   warps 8-15 read tensor memory back (TMEM lanes 32 (w & 3) .., 32 columns each),
+//     recombine and store rows of Y,
+//   warp 16 loads 32-row sub-tiles of X into a three-slot ring with per-row bulk copies,
+//   warp 17 owns tensor memory and issues the MMAs,
 // handing tiles over through mbarriers.  B's digit slices are built once per CTA.  B is upper
 // triangular, so the K-step j in [16c, 16c + 16) meets only columns k >= 16c and its MMAs run
 // with N = 64 - 16c.  In place (Y == X) is safe: a tile's rows are read before any are written.
@@ -34,30 +36,32 @@ namespace rq {
 namespace {
 using namespace tc;
 
-constexpr int TQ_ROWS = 128, TQ_NP = 64, TQ_SUB = 32, TQ_NSTAGE = 2;
-constexpr int TQ_THREADS = 320;
-constexpr int W_LOAD = 8, W_MMA = 9;
+constexpr int TQ_ROWS = 128, TQ_NP = 64, TQ_SUB = 32, TQ_NSTAGE = 3;
+constexpr int TQ_THREADS = 576;
+constexpr int W_FLUSH0 = 8, W_LOAD = 16, W_MMA = 17;
 constexpr uint32_t TQ_TMEM_COLS = 512;
-// A: K-major, no swizzle; a 16-byte pad between K-adjacent core matrices spreads one row's
-// eight core-matrix rows over all 32 banks for the slicers' 4-byte stores.
-constexpr uint32_t A_LBO = 144, A_SBO = 8 * A_LBO, A_SLICE = (TQ_ROWS / 8) * A_SBO;
+// A: K-major, no swizzle.  A slicer lane (row r = lane & 7 of an 8-row group, pair pi =
+// lane >> 3 of every K core matrix) stores 4 bytes at r * 16 + pi * 4 of a core matrix: one
+// warp store covers one core matrix, all 32 banks.
+constexpr uint32_t A_LBO = 128, A_SBO = 8 * A_LBO, A_SLICE = (TQ_ROWS / 8) * A_SBO;
 // B: per K-step c a block of (64 - 16c) rows (output column k) x 16 K, 32 bytes per row.
 constexpr uint32_t B_SLICE = 160 * 32;
-constexpr uint32_t STAGE_BYTES = TQ_SUB * TQ_NP * 8;
-constexpr uint32_t OUT_PITCH = 72, OUT_BYTES = 32 * OUT_PITCH;
+// Staged rows are 528 bytes apart (512 + 16): the slicers' 16-byte reads of eight rows at one
+// K offset then fall into eight different bank groups.
+constexpr uint32_t STAGE_PITCH = 528;
+constexpr uint32_t STAGE_BYTES = TQ_SUB * STAGE_PITCH;
 constexpr size_t OFF_B = 0;
 constexpr size_t OFF_A = OFF_B + (size_t)NDIG * B_SLICE;
 constexpr size_t OFF_STAGE = OFF_A + (size_t)NDIG * A_SLICE;
-constexpr size_t OFF_OUT = OFF_STAGE + (size_t)TQ_NSTAGE * STAGE_BYTES;
-constexpr size_t OFF_ROWEXP = OFF_OUT + 4 * (size_t)OUT_BYTES;
+constexpr size_t OFF_ROWEXP = OFF_STAGE + (size_t)TQ_NSTAGE * STAGE_BYTES;
 constexpr size_t OFF_COLEXP = OFF_ROWEXP + 2 * TQ_ROWS * sizeof(int);
 constexpr size_t OFF_BARS = OFF_COLEXP + TQ_NP * sizeof(int);
-constexpr int NBARS = 9;  // full[2], empty[2], a_full, a_empty, t_full, t_empty, drain
+constexpr int NBARS = 2 * TQ_NSTAGE + 5;  // full[3], empty[3], a_full, a_empty, t_full, t_empty, drain
 constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;
 constexpr size_t TQ_SMEM = OFF_MISC + 16;
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
-enum LoadMode { LOAD_BLOCK = 0, LOAD_ROWS = 1, LOAD_PLAIN = 2 };
+enum LoadMode { LOAD_ROWS = 0, LOAD_PLAIN = 1 };
 
 __device__ __forceinline__ uint32_t b_row0(int c) { return c == 0 ? 0u : c == 1 ? 64u : c == 2 ? 112u : 144u; }
 
@@ -118,52 +122,6 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint64_t ad0, uint64_t
   }
 }
 
-// Four columns (group h of 16) of a recombination warp's 32 rows: regions -> T -> FP64 into the
-// warp's buffer; after every second group the buffer's 8 columns go out so that four lanes
-// store 64 contiguous bytes of one row of Y.
-__device__ __forceinline__ void emit_group(const uint32_t (&v)[NDIG][4], int h, int er, const int *colexp,
-                                           uint8_t *ob, int lane, double *Y, int64_t ldy, int64_t row0,
-                                           int64_t r_end, int n, bool vec_store) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const long long th = ((long long)acc_to_int(v[0][c]) << 21) + ((long long)acc_to_int(v[1][c]) << 14) +
-                         ((long long)acc_to_int(v[2][c]) << 7) + (long long)acc_to_int(v[3][c]);
-    const long long tl = ((long long)acc_to_int(v[4][c]) << 21) + ((long long)acc_to_int(v[5][c]) << 14) +
-                         ((long long)acc_to_int(v[6][c]) << 7) + (long long)acc_to_int(v[7][c]);
-    const long long t = (th << 25) + (tl >> 3);  // T / 8 (|T| < 2^65)
-    double y = (double)t;
-    const int e = er + scale_exp(colexp[4 * h + c]) - 56;
-    y = t != 0 ? __longlong_as_double(__double_as_longlong(y) + ((long long)e << 52)) : 0.0;
-    *(double *)(ob + lane * OUT_PITCH + 8 * (4 * (h & 1) + c)) = y;
-  }
-  if ((h & 1) == 0) return;
-  __syncwarp();
-  // lane 4a + b stores row 8p + a of the warp's 32, columns 8 cg + 2b, 8 cg + 2b + 1
-  const int a = lane >> 2, b = lane & 3, k0 = 8 * (h >> 1) + 2 * b;
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int rl = 8 * p + a;
-    const double y0 = *(const double *)(ob + rl * OUT_PITCH + 16 * b);
-    const double y1 = *(const double *)(ob + rl * OUT_PITCH + 16 * b + 8);
-    const int64_t grow = row0 + rl;
-    if (grow < r_end) {
-      double *dst = Y + grow * ldy + k0;
-      if (vec_store && k0 + 1 < n) {
-        *(double2 *)dst = make_double2(y0, y1);
-      } else {
-        if (k0 < n) dst[0] = y0;
-        if (k0 + 1 < n) dst[1] = y1;
-      }
-    }
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ void load_group(uint32_t tq, int h, uint32_t (&v)[NDIG][4]) {
-#pragma unroll
-  for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + 4 * h), v[g]);
-}
-
 }  // namespace
 
 template <bool IN_DF>
@@ -176,27 +134,26 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   uint8_t *Bs = tq_smem + OFF_B;
   uint8_t *As = tq_smem + OFF_A;
   uint8_t *stage = tq_smem + OFF_STAGE;
-  uint8_t *outb = tq_smem + OFF_OUT;
   int *rowexp = (int *)(tq_smem + OFF_ROWEXP);
   int *colexp = (int *)(tq_smem + OFF_COLEXP);
   uint64_t *bars = (uint64_t *)(tq_smem + OFF_BARS);
   uint32_t *tmem_slot = (uint32_t *)(tq_smem + OFF_MISC);
   volatile int *abort_flag = (volatile int *)(tq_smem + OFF_MISC + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]);
-  const uint32_t a_full = smem_addr(&bars[4]), a_empty = smem_addr(&bars[5]);
-  const uint32_t t_full = smem_addr(&bars[6]), t_empty = smem_addr(&bars[7]);
-  const uint32_t drain = smem_addr(&bars[8]);
+  const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[TQ_NSTAGE]);
+  const uint32_t a_full = smem_addr(&bars[2 * TQ_NSTAGE]), a_empty = smem_addr(&bars[2 * TQ_NSTAGE + 1]);
+  const uint32_t t_full = smem_addr(&bars[2 * TQ_NSTAGE + 2]), t_empty = smem_addr(&bars[2 * TQ_NSTAGE + 3]);
+  const uint32_t drain = smem_addr(&bars[2 * TQ_NSTAGE + 4]);
 
   if (tid == 0) {
-    mbar_init_count(full0, 1);
-    mbar_init_count(full0 + 8, 1);
-    mbar_init_count(empty0, 4);
-    mbar_init_count(empty0 + 8, 4);
-    mbar_init_count(a_full, 4);
+    for (int q = 0; q < TQ_NSTAGE; ++q) {
+      mbar_init_count(full0 + 8 * q, 1);
+      mbar_init_count(empty0 + 8 * q, 4);
+    }
+    mbar_init_count(a_full, 8);
     mbar_init_count(a_empty, 1);
     mbar_init_count(t_full, 1);
-    mbar_init_count(t_empty, 4);
+    mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -232,39 +189,40 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r_end = imin64(m, r_begin + rows_per_cta);
   const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + TQ_ROWS - 1) / TQ_ROWS) : 0;
+  auto sub_rows = [&](int i, int q) -> int {
+    const int64_t r0 = r_begin + (int64_t)i * TQ_ROWS + TQ_SUB * q;
+    return r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
+  };
 
   if (warp == W_LOAD) {
     // ------------------------------------------------------------------ loader
-    int last_u[2] = {-1, -1};
+    int last_u[TQ_NSTAGE];
+#pragma unroll
+    for (int q = 0; q < TQ_NSTAGE; ++q) last_u[q] = -1;
     for (int i = 0; i < ntiles && !*abort_flag; ++i) {
       bool ok = true;
       for (int q = 0; q < 4; ++q) {
-        const int u = 4 * i + q, slot = u & 1;
-        if (!mbar_wait_or_abort(empty0 + 8 * slot, ((u >> 1) & 1) ^ 1, abort_flag)) {
+        const int u = 4 * i + q, slot = u % TQ_NSTAGE;
+        if (!mbar_wait_or_abort(empty0 + 8 * slot, ((u / TQ_NSTAGE) & 1) ^ 1, abort_flag)) {
           if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
           ok = false;
           break;
         }
         const int64_t r0 = r_begin + (int64_t)i * TQ_ROWS + TQ_SUB * q;
-        const int cnt = r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
+        const int cnt = sub_rows(i, q);
         uint8_t *dst = stage + (size_t)slot * STAGE_BYTES;
         const uint32_t fb = full0 + 8 * slot;
-        if (cnt > 0 && load_mode == LOAD_BLOCK) {
-          if (lane == 0) {
-            mbar_expect_tx(fb, (uint32_t)cnt * 512u);
-            bulk_load(smem_addr(dst), (const uint8_t *)Xin + (size_t)r0 * 512, (uint32_t)cnt * 512u, fb);
-          }
-        } else if (cnt > 0 && load_mode == LOAD_ROWS) {
+        if (cnt > 0 && load_mode == LOAD_ROWS) {
           if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
           __syncwarp();
           for (int r = lane; r < cnt; r += 32)
-            bulk_load(smem_addr(dst + r * 512), (const uint8_t *)Xin + (size_t)(r0 + r) * (size_t)ldx * 8,
+            bulk_load(smem_addr(dst + r * STAGE_PITCH), (const uint8_t *)Xin + (size_t)(r0 + r) * (size_t)ldx * 8,
                       (uint32_t)n * 8u, fb);
         } else {
           const unsigned long long *src = (const unsigned long long *)Xin;
           for (int e = lane; e < cnt * n; e += 32) {
             const int r = e / n, cc = e - r * n;
-            ((unsigned long long *)dst)[r * TQ_NP + cc] = src[(r0 + r) * ldx + cc];
+            *(unsigned long long *)(dst + r * STAGE_PITCH + 8 * cc) = src[(r0 + r) * ldx + cc];
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(fb);
@@ -275,8 +233,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     }
     // copies still in flight (only after an abort) land before the CTA leaves
     if (lane == 0)
-      for (int slot = 0; slot < 2; ++slot)
-        if (last_u[slot] >= 0) mbar_wait(full0 + 8 * slot, (last_u[slot] >> 1) & 1);
+      for (int q = 0; q < TQ_NSTAGE; ++q)
+        if (last_u[q] >= 0) mbar_wait(full0 + 8 * q, (last_u[q] / TQ_NSTAGE) & 1);
   } else if (warp == W_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -300,62 +258,58 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       mbar_wait(drain, 0);
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < W_FLUSH0) {
     // ------------------------------------------------------------------ slicers
-    for (int i = 0; i < ntiles; ++i) {
+    const int grp = warp >> 2, sg = warp & 3;     // sub-tiles q = grp, grp + 2; rows 8 sg ..
+    const int r = 8 * sg + (lane & 7), pi = lane >> 3;
+    bool ok = true;
+    for (int i = 0; i < ntiles && ok; ++i) {
       const int buf = i & 1;
-      bool ok = true;
-      for (int q = 0; q < 4; ++q) {
-        const int u = 4 * i + q, slot = u & 1;
-        if (!mbar_wait_or_abort(full0 + 8 * slot, (u >> 1) & 1, abort_flag) ||
-            (q == 0 && !mbar_wait_or_abort(a_empty, (i & 1) ^ 1, abort_flag))) {
+      for (int qq = 0; qq < 2; ++qq) {
+        const int q = grp + 2 * qq, u = 4 * i + q, slot = u % TQ_NSTAGE;
+        if (!mbar_wait_or_abort(full0 + 8 * slot, (u / TQ_NSTAGE) & 1, abort_flag) ||
+            (qq == 0 && !mbar_wait_or_abort(a_empty, (i & 1) ^ 1, abort_flag))) {
           ok = false;
           break;
         }
-        const int64_t r0 = r_begin + (int64_t)i * TQ_ROWS + TQ_SUB * q;
-        const int cnt = r0 < r_end ? (int)imin64(TQ_SUB, r_end - r0) : 0;
-        const uint8_t *src = stage + (size_t)slot * STAGE_BYTES;
-        const bool ca = 2 * lane < n, cb = 2 * lane + 1 < n;
+        const int cnt = sub_rows(i, q), row = TQ_SUB * q + r;
+        const uint8_t *src = stage + (size_t)slot * STAGE_BYTES + r * STAGE_PITCH + 16 * pi;
+        // this lane: columns 8 kg + 2 pi and 8 kg + 2 pi + 1 of its row, kg = 0 .. 7
         unsigned long long ea[8], eb[8];
-        int mx[8];
+        int mx = 0;
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          const int r = 8 * warp + rr;
-          const ulonglong2 raw = *(const ulonglong2 *)(src + r * 512 + 16 * lane);
-          ea[rr] = (r < cnt && ca) ? raw.x : 0ULL;
-          eb[rr] = (r < cnt && cb) ? raw.y : 0ULL;
-          mx[rr] = max(elem_expfield<IN_DF>(ea[rr]), elem_expfield<IN_DF>(eb[rr]));
+        for (int kg = 0; kg < 8; ++kg) {
+          const ulonglong2 raw = *(const ulonglong2 *)(src + 64 * kg);
+          const int c0 = 8 * kg + 2 * pi;
+          ea[kg] = (r < cnt && c0 < n) ? raw.x : 0ULL;
+          eb[kg] = (r < cnt && c0 + 1 < n) ? raw.y : 0ULL;
+          mx = max(mx, max(elem_expfield<IN_DF>(ea[kg]), elem_expfield<IN_DF>(eb[kg])));
         }
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        const int E = scale_exp(mx);
+        if (pi == 0) rowexp[buf * TQ_ROWS + row] = E;
+        uint8_t *dst = As + (size_t)(row >> 3) * A_SBO + (row & 7) * 16 + pi * 4;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int rr = 0; rr < 8; ++rr) mx[rr] = max(mx[rr], __shfl_xor_sync(0xffffffffu, mx[rr], o));
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          const int row = TQ_SUB * q + 8 * warp + rr;
-          const int E = scale_exp(mx[rr]);
-          if (lane == 0) rowexp[buf * TQ_ROWS + row] = E;
+        for (int kg = 0; kg < 8; ++kg) {
           uint32_t w[NDIG];
-          digits2(elem_fix<IN_DF>(ea[rr], E), elem_fix<IN_DF>(eb[rr], E), w);
-          const uint32_t off = (uint32_t)(row >> 3) * A_SBO + (uint32_t)(lane >> 2) * A_LBO + (row & 7) * 16 + (lane & 3) * 4;
+          digits2(elem_fix<IN_DF>(ea[kg], E), elem_fix<IN_DF>(eb[kg], E), w);
 #pragma unroll
-          for (int p = 0; p < NDIG; ++p) *(uint32_t *)(As + (NDIG - 1 - p) * A_SLICE + off) = w[p];
+          for (int p = 0; p < NDIG; ++p) *(uint32_t *)(dst + (size_t)(NDIG - 1 - p) * A_SLICE + kg * A_LBO) = w[p];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty0 + 8 * slot);
       }
-      if (!ok) {
-        if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
-        break;
-      }
+      if (!ok) break;
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(a_full);
     }
+    if (!ok && lane == 0 && !*abort_flag) set_abort(abort_flag, st);
   } else {
     // ------------------------------------------------------------------ recombination
-    const int quad = warp & 3, L = 32 * quad + lane;
-    uint8_t *ob = outb + (size_t)quad * OUT_BYTES;
+    const int f = warp - W_FLUSH0, quad = f & 3, ch = f >> 2;  // warp % 4 == quad: TMEM lanes 32 quad ..
+    const int L = 32 * quad + lane;
     const uint32_t tq = tmem + ((uint32_t)(32 * quad) << 16);
     for (int i = 0; i < ntiles; ++i) {
       if (!mbar_wait_or_abort(t_full, i & 1, abort_flag)) {
@@ -364,29 +318,36 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       }
       fence_after_sync();
       const int er = rowexp[(i & 1) * TQ_ROWS + L];
-      const int64_t row0 = r_begin + (int64_t)i * TQ_ROWS + 32 * quad;
-      // two register sets: the loads of one 4-column group overlap the recombination of another
-      uint32_t va[NDIG][4], vb[NDIG][4];
-      load_group(tq, 0, va);
-      tmem_wait_ld();
-      tmem_regs_ready(va);
+      const int64_t grow = r_begin + (int64_t)i * TQ_ROWS + L;
+      double *yrow = Y + grow * ldy;
 #pragma unroll 1
-      for (int h = 0; h < 16; h += 2) {
-        load_group(tq, h + 1, vb);
-        emit_group(va, h, er, colexp, ob, lane, Y, ldy, row0, r_end, n, vec_store);
+      for (int h = 0; h < 8; ++h) {
+        const int k0 = 32 * ch + 4 * h;
+        uint32_t v[NDIG][4];
+#pragma unroll
+        for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + k0), v[g]);
         tmem_wait_ld();
-        tmem_regs_ready(vb);
-        if (h + 2 < 16) {
-          load_group(tq, h + 2, va);
-        } else {  // every region read: the next tile's MMAs may start
+        tmem_regs_ready(v);
+        if (h == 7) {  // every region read: the next tile's MMAs may start
           fence_before_sync();
           __syncwarp();
           if (lane == 0) mbar_arrive(t_empty);
         }
-        emit_group(vb, h + 1, er, colexp, ob, lane, Y, ldy, row0, r_end, n, vec_store);
-        if (h + 2 < 16) {
-          tmem_wait_ld();
-          tmem_regs_ready(va);
+        double y[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const long long t = recombine8<3>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+          y[c] = int_times_pow2(t, er + scale_exp(colexp[k0 + c]) - 56);  // T / 8 (|T| < 2^65)
+        }
+        if (grow < r_end) {
+          if (vec_store && k0 + 3 < n) {
+            *(double2 *)(yrow + k0) = make_double2(y[0], y[1]);
+            *(double2 *)(yrow + k0 + 2) = make_double2(y[2], y[3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (k0 + c < n) yrow[k0 + c] = y[c];
+          }
         }
       }
     }
@@ -406,9 +367,7 @@ cudaError_t launch_trsm_oz(const void *W, bool in_df, int64_t ldw, double *Q, in
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
   const bool aligned = ((uintptr_t)W & 15) == 0;
-  const int load_mode = (aligned && n == TQ_NP && ldw == TQ_NP) ? LOAD_BLOCK
-                        : (aligned && (n * 8) % 16 == 0 && (ldw * 8) % 16 == 0) ? LOAD_ROWS
-                                                                                 : LOAD_PLAIN;
+  const int load_mode = (aligned && (n * 8) % 16 == 0 && (ldw * 8) % 16 == 0) ? LOAD_ROWS : LOAD_PLAIN;
   const bool vec_store = ((uintptr_t)Q & 15) == 0 && (ldq % 2) == 0;
   cudaError_t e;
   if (in_df) {
