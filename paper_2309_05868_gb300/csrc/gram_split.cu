@@ -7,13 +7,18 @@
 // 64 columns stack into the 128 rows of A-tile a (TMEM lane 64 * (s & 1) + j); slices t of the
 // same buffer are the B operand, several stacked along N, so one MMA covers up to four
 // regions.  Region g' (64 columns of tensor memory) gathers the pairs (a, t) with 2a + t = g':
-// lanes 0-63 then hold D_g for g = g', lanes 64-127 hold g = g' + 1 (odd s), every D a sum of
-// at most 4 x 128 digit products (|D| <= 2^21, exact in FP32).  With
+// lanes 0-63 then hold D_g for g = g', lanes 64-127 hold g = g' + 1 (odd s).
+//
+// Groups go in pairs: the first takes its column maxima plus one bit of headroom as scales, the
+// second keeps those scales unless one of its columns outgrew them.  A pair with common scales
+// accumulates in the same regions (an event of 256 rows), so every D is a sum of at most
+// 4 x 256 digit products, |D| <= 2^22, exact in FP32.  With
 //   T_p(j, k) = sum_g' 2^(7 (7 - g')) D_g'(64p + j, k),
-// the group's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
-// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p is formed in 64-bit integers (T / 32:
-// an even-slice partial value is below 2^55, so |T_p| < 2^67), rounded once to FP64 and added to
-// per-thread FP64 sums; one FP64 atomic per entry (j <= k) and parity at the end.
+// the event's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
+// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p is formed in 64-bit integers (T / 64:
+// an even-slice partial value is below 2^55, so |T_p| < 2^68), converted with integer
+// instructions and added to per-thread FP64 sums; one FP64 atomic per entry (j <= k) and
+// parity at the end.
 //
 // One CTA per SM, persistent over its row range; warps specialise:
 //   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
@@ -21,7 +26,8 @@
 //   warps 4-11 read the regions back (warp w: TMEM lanes 32 (w & 3) .., columns k in
 //     [32 h, 32 h + 32) with h = (w - 4) / 4) and keep the FP64 sums,
 //   warp 12 loads 32-row sub-tiles into a four-slot ring with bulk copies,
-//   warp 13 owns tensor memory and issues the MMAs (24 per 64-row tile).
+//   warp 13 owns tensor memory and issues the MMAs (24 per 64-row tile), closing an event
+//     (commit to the recombination warps) after one group or a merged pair.
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -40,8 +46,10 @@ constexpr uint32_t GS_STAGE = GS_SUB * GS_NP * 8;   // 16 KB sub-tile
 constexpr size_t GOFF_SL = 0;
 constexpr size_t GOFF_STAGE = GOFF_SL + 2 * (size_t)GS_BUF;
 constexpr size_t GOFF_COLE = GOFF_STAGE + 4 * (size_t)GS_STAGE;
-constexpr size_t GOFF_BARS = GOFF_COLE + 3 * GS_NP * sizeof(int);
-constexpr int GS_NBARS = 15;  // full[4], empty[4], sl_full[2], sl_empty[2], t_full, t_empty, drain
+constexpr size_t GOFF_EVT = GOFF_COLE + 4 * GS_NP * sizeof(int);  // merge[3], grow[3], ev_grp[4]
+constexpr size_t GOFF_BARS = GOFF_EVT + 16 * sizeof(int);
+constexpr int GS_NBARS = 17;  // full[4], empty[4], sl_full[2], sl_empty[2], t_full, t_empty, drain,
+                              // scale_bar, ev_bar
 constexpr size_t GOFF_MISC = GOFF_BARS + GS_NBARS * 8;
 constexpr size_t GS_SMEM = GOFF_MISC + 16;
 static_assert(GS_SMEM <= 232448, "shared memory budget");
@@ -95,6 +103,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
   uint8_t *slices = gs_smem + GOFF_SL;
   uint8_t *stage = gs_smem + GOFF_STAGE;
   int *colE = (int *)(gs_smem + GOFF_COLE);
+  volatile int *evt = (volatile int *)(gs_smem + GOFF_EVT);
   uint64_t *bars = (uint64_t *)(gs_smem + GOFF_BARS);
   uint32_t *tmem_slot = (uint32_t *)(gs_smem + GOFF_MISC);
   volatile int *abort_flag = (volatile int *)(gs_smem + GOFF_MISC + 4);
@@ -102,6 +111,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
   const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[4]);
   const uint32_t slf0 = smem_addr(&bars[8]), sle0 = smem_addr(&bars[10]);
   const uint32_t t_full = smem_addr(&bars[12]), t_empty = smem_addr(&bars[13]), drain = smem_addr(&bars[14]);
+  const uint32_t scale_bar = smem_addr(&bars[15]), ev_bar = smem_addr(&bars[16]);
 
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) {
@@ -115,7 +125,10 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     mbar_init_count(t_full, 1);
     mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
+    mbar_init_count(scale_bar, 4);
+    mbar_init_count(ev_bar, 1);
     *abort_flag = 0;
+    for (int e = 0; e < 16; ++e) evt[e] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == GW_MMA) tmem_alloc(tmem_slot, GS_TMEM_COLS);
@@ -181,25 +194,38 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     if (lane == 0) {
       const uint64_t dA = umma_desc(smem_addr(slices), 128, 1024);
       const uint64_t dB = umma_desc(smem_addr(slices + GS_BUF), 128, 1024);
-      for (int g = 0; g < ngroups; ++g) {
-        if (!mbar_wait_or_abort(t_empty, (g & 1) ^ 1, abort_flag) ||
-            !mbar_wait_or_abort(slf0, g & 1, abort_flag)) {
-          if (!*abort_flag) {
-            *abort_flag = 1;
-            status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-          }
+      // Events: one tensor-memory accumulation = one group, or two when the second keeps the
+      // first's scales.  evt[8 + (ev & 3)] names the event's first group for the recombination.
+      int ev = 0, pending_g = -1;
+      bool ok = true;
+      auto close_event = [&]() {
+        evt[8 + (ev & 3)] = pending_g;
+        umma_commit(t_full);
+        mbar_arrive(ev_bar);
+        ++ev;
+        pending_g = -1;
+      };
+      for (int g = 0; g < ngroups && ok; ++g) {
+        if (!mbar_wait_or_abort(slf0, g & 1, abort_flag)) {
+          ok = false;
           break;
+        }
+        const bool merge = evt[g % 3] != 0;
+        if (!merge) {
+          if (pending_g >= 0) close_event();
+          if (!mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {  // previous event read back
+            ok = false;
+            break;
+          }
+          pending_g = g;
         }
         fence_after_sync();
         uint64_t d = dA;
         asm volatile("" : "+l"(d));
-        gram_issue_tile(tmem, d, true);
+        gram_issue_tile(tmem, d, !merge);
         umma_commit(sle0);
         if (!mbar_wait_or_abort(slf0 + 8, g & 1, abort_flag)) {
-          if (!*abort_flag) {
-            *abort_flag = 1;
-            status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-          }
+          ok = false;
           break;
         }
         fence_after_sync();
@@ -207,7 +233,15 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         asm volatile("" : "+l"(d));
         gram_issue_tile(tmem, d, false);
         umma_commit(sle0 + 8);
-        umma_commit(t_full);
+        if (merge) close_event();
+      }
+      if (ok && pending_g >= 0) close_event();
+      if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {
+        evt[8 + (ev & 3)] = -1;  // no more events
+        mbar_arrive(ev_bar);
+      } else if (!*abort_flag) {
+        *abort_flag = 1;
+        status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
       }
       umma_commit(drain);
       mbar_wait(drain, 0);
@@ -240,8 +274,29 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
       }
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-      const int E = scale_exp(mx);
-      if (h == 0) colE[(g % 3) * GS_NP + j] = E;
+      // Scales: the first group of a pair takes one bit of headroom; the second keeps the first's
+      // scales (so both accumulate in the same tensor-memory regions) unless a column outgrew them.
+      const int Eg = scale_exp(mx);
+      int E = Eg + 1;
+      if (g & 1) {
+        const int Eprev = colE[((g - 1) & 3) * GS_NP + j];
+        const bool grows = __any_sync(0xffffffffu, cj && Eg > Eprev);
+        if (lane == 0 && grows) atomicMax((int *)&evt[3 + g % 3], g + 1);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(scale_bar);  // the four slicer warps meet here
+        if (!mbar_wait_or_abort(scale_bar, (g >> 1) & 1, abort_flag)) {
+          if (lane == 0 && !*abort_flag) {
+            *abort_flag = 1;
+            status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
+          }
+          break;
+        }
+        if (evt[3 + g % 3] != g + 1) E = Eprev;
+      }
+      // four scale slots: a merged event reads its first group's slot until the slicers are two
+      // groups further on (they wait for the event's read-back before slicing the next pair)
+      if (h == 0) colE[(g & 3) * GS_NP + j] = E;
+      if (warp == 0 && lane == 0) evt[g % 3] = (g & 1) && evt[3 + g % 3] != g + 1;  // merge with g - 1
       // pass 2: the two 64-row tiles into slice buffers 0 and 1
       for (int tb = 0; tb < 2; ++tb) {
         if (!mbar_wait_or_abort(sle0 + 8 * tb, (g & 1) ^ 1, abort_flag)) {
@@ -293,8 +348,17 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
 #pragma unroll
     for (int c = 0; c < 32; ++c) S[c] = 0.0;
     const bool active = 32 * kh + 31 >= jlo;  // some k >= j in this warp's block
-    for (int g = 0; g < ngroups; ++g) {
-      if (!mbar_wait_or_abort(t_full, g & 1, abort_flag)) {
+    for (int ev = 0;; ++ev) {
+      if (!mbar_wait_or_abort(ev_bar, ev & 1, abort_flag)) {
+        if (lane == 0 && !*abort_flag) {
+          *abort_flag = 1;
+          status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
+        }
+        break;
+      }
+      const int g = evt[8 + (ev & 3)];
+      if (g < 0) break;
+      if (!mbar_wait_or_abort(t_full, ev & 1, abort_flag)) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
           status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
@@ -303,8 +367,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       }
       fence_after_sync();
       if (active) {
-        const int *ce = colE + (g % 3) * GS_NP;
-        const int ebase = ce[j] - 54 - 7 * par;
+        const int *ce = colE + (g & 3) * GS_NP;
+        const int ebase = ce[j] - 53 - 7 * par;
 #pragma unroll
         for (int h4 = 0; h4 < 8; ++h4) {
           const int k0 = 32 * kh + 4 * h4;
@@ -316,8 +380,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           tmem_regs_ready(v);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const long long t = recombine8<5>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
-            const double y = int_times_pow2(t, ebase + ce[k0 + c]);  // T / 32 (|T| < 2^67)
+            const long long t = recombine8<6>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+            const double y = int_times_pow2(t, ebase + ce[k0 + c]);  // T / 64 (|T| < 2^68)
             S[4 * h4 + c] += y;
           }
         }

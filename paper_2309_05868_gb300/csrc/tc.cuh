@@ -321,11 +321,20 @@ __device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32
   return (th << (28 - SH)) + (tl >> SH);
 }
 
-// (double) t * 2^e for an integer t != 0 with |t| < 2^63 and a result in the normal range;
-// 0 for t == 0.  The scaling adds e to the exponent field through the high word.
+// (double) t * 2^e, rounded to nearest (ties away from zero), for |t| < 2^63 and a result in
+// the normal range; 0 for t == 0.  Integer instructions only: the FP64 pipe (about 1/64 of the
+// FP32 rate on this part) is left to the callers' additions.
 __device__ __forceinline__ double int_times_pow2(long long t, int e) {
-  const double y = (double)t;
-  return t != 0 ? __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y)) : 0.0;
+  const unsigned long long sgn = (unsigned long long)(t >> 63);
+  unsigned long long a = ((unsigned long long)t ^ sgn) - sgn;  // |t|
+  const int lz = __clzll((long long)a);                        // 64 when t == 0
+  a <<= (lz & 63);                                             // leading one at bit 63
+  unsigned long long r = a + 0x400ULL;                         // round at bit 10
+  const int carry = r < a;
+  r = carry ? (1ULL << 63) : r;
+  const unsigned long long ex = (unsigned long long)(1023 + 63 - lz + carry + e);
+  const unsigned long long bits = (sgn << 63) | (ex << 52) | ((r >> 11) & 0xFFFFFFFFFFFFFULL);
+  return t == 0 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
 }  // namespace tc

@@ -57,8 +57,8 @@ constexpr size_t OFF_ROWEXP = OFF_STAGE + (size_t)TQ_NSTAGE * STAGE_BYTES;
 constexpr size_t OFF_COLEXP = OFF_ROWEXP + 2 * TQ_ROWS * sizeof(int);
 constexpr size_t OFF_BARS = OFF_COLEXP + TQ_NP * sizeof(int);
 constexpr int NBARS = 2 * TQ_NSTAGE + 5;  // full[3], empty[3], a_full, a_empty, t_full, t_empty, drain
-constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;
-constexpr size_t TQ_SMEM = OFF_MISC + 16;
+constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;  // tmem slot, abort flag, slot tags[3]
+constexpr size_t TQ_SMEM = OFF_MISC + 32;
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
 enum LoadMode { LOAD_ROWS = 0, LOAD_PLAIN = 1 };
@@ -139,6 +139,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   uint64_t *bars = (uint64_t *)(tq_smem + OFF_BARS);
   uint32_t *tmem_slot = (uint32_t *)(tq_smem + OFF_MISC);
   volatile int *abort_flag = (volatile int *)(tq_smem + OFF_MISC + 4);
+  // slot_tag[q]: the sub-tile the loader has assigned to stage slot q.  Two slicer groups take
+  // alternate sub-tiles, so a group can reach a slot's next use while the other group's load
+  // into it is still in flight; waiting for the tag first keeps the full barrier's parity
+  // unambiguous (the wait then always targets the phase in progress).
+  volatile int *slot_tag = (volatile int *)(tq_smem + OFF_MISC + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[TQ_NSTAGE]);
   const uint32_t a_full = smem_addr(&bars[2 * TQ_NSTAGE]), a_empty = smem_addr(&bars[2 * TQ_NSTAGE + 1]);
@@ -156,6 +161,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
     *abort_flag = 0;
+    for (int q = 0; q < TQ_NSTAGE; ++q) slot_tag[q] = -1;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (tid < TQ_NP) colexp[tid] = 0;
@@ -212,6 +218,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int cnt = sub_rows(i, q);
         uint8_t *dst = stage + (size_t)slot * STAGE_BYTES;
         const uint32_t fb = full0 + 8 * slot;
+        if (lane == 0) slot_tag[slot] = u;
         if (cnt > 0 && load_mode == LOAD_ROWS) {
           if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
           __syncwarp();
@@ -267,7 +274,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const int buf = i & 1;
       for (int qq = 0; qq < 2; ++qq) {
         const int q = grp + 2 * qq, u = 4 * i + q, slot = u % TQ_NSTAGE;
-        if (!mbar_wait_or_abort(full0 + 8 * slot, (u / TQ_NSTAGE) & 1, abort_flag) ||
+        bool tagged = false;
+        for (int it = 0; it < MAX_WAIT && !tagged && !*abort_flag; ++it) tagged = slot_tag[slot] == u;
+        if (!tagged || !mbar_wait_or_abort(full0 + 8 * slot, (u / TQ_NSTAGE) & 1, abort_flag) ||
             (qq == 0 && !mbar_wait_or_abort(a_empty, (i & 1) ^ 1, abort_flag))) {
           ok = false;
           break;

@@ -133,3 +133,35 @@ def test_failure_is_isolated_and_tickets_retire(rq):
     assert rq.randqr_poll(ctx, tg[0])[0] == -9  # retired
     assert rq.randqr_poll(ctx, 123456789)[0] == -9
     ctx.close()
+
+
+def test_tensor_core_kernels_under_concurrent_load(rq):
+    """Many large factorizations on eight slots at once (the row-pass kernels of different
+    requests then share the GPU's SMs and memory bandwidth, which stretches load latencies
+    inside each kernel's pipeline): every result matches the same call made alone on one
+    stream (up to the order of the Gram's final FP64 atomics: well-conditioned V, so 1e-13)."""
+    shapes = [(1 << 20, 64), (1 << 19, 4), (700001, 16), (1 << 20, 32), (300000, 64), (1 << 20, 8)]
+    Vs = [torch.randn(m, n, dtype=torch.float64, device="cuda") / 1e3 for (m, n) in shapes]
+    alone = []
+    ctx1 = rq.Context(0)
+    for i, V in enumerate(Vs):
+        Q, R, _ = rq.randqr_factor(V, seed=i, ctx=ctx1)
+        alone.append((Q.clone(), R.clone()))
+    ctx1.close()
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=8)
+    for rep in range(3):
+        outs, subs = [], []
+        for i, V in enumerate(Vs * 2):
+            Q = torch.empty_like(V)
+            R = torch.empty((V.shape[1], V.shape[1]), dtype=torch.float64, device="cuda")
+            t, keep = rq.randqr_submit(ctx, V, Q=Q, R=R, seed=i % len(Vs))
+            subs.append(t)
+            outs.append((i % len(Vs), Q, R, keep))
+        res = _drain(rq, ctx, subs)
+        assert all(st == 0 for st, _ in res.values()), res
+        for i, Q, R, _ in outs:
+            dq = (Q - alone[i][0]).abs().max().item()
+            dr = ((R - alone[i][1]).abs().max() / alone[i][1].abs().max()).item()
+            assert dq <= 1e-13 and dr <= 1e-13, (rep, i, dq, dr)
+    ctx.close()
