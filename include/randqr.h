@@ -92,14 +92,15 @@ randqr_status randqr_get_status(randqr_ctx *ctx, void *stream, randqr_info *info
 size_t randqr_workspace_bytes(const randqr_ctx *ctx);
 
 /* Gram products on the tensor cores (default on): for n <= 128 the Gram G = W^T W of the
- * Cholesky passes is formed from exact integer slices of W (eight 7-bit digits of a 56-bit
- * fixed point per column and row chunk) multiplied by tcgen05 bf16 MMAs with exact FP32
- * accumulation, then recombined in pair (double-float) running sums.  For n <= 64 the second
- * triangular solve of rand_cholQR (Q = W R_c^{-1}, Algorithm 3, where kappa(R_c) = O(1) by
- * the sketch's subspace embedding) is formed the same way as the product W (R_c^{-1}) with
- * the inverse taken in FP64; CholeskyQR2's and shifted CholeskyQR3's solves, whose R may be
- * ill-conditioned, always use substitution.  enable = 0 selects the CUDA-core kernels of the
- * chosen precision everywhere. */
+ * Cholesky passes is formed from exact integer slices of W (eight balanced 7-bit digits of a
+ * 54-bit fixed point per column and row group, each an exact f16) multiplied by tcgen05 MMAs
+ * with exact FP32 accumulation, then recombined in 64-bit integers.  For n <= 64 the triangular solves whose
+ * factor is well conditioned are formed the same way as products with the FP64 inverse: both
+ * solves of rand_cholQR (Algorithm 3; R_s^{-1} is applied to V so that its truncation error is a
+ * row-wise backward error in V, and kappa(R_c) = O(1) by the sketch's embedding property) and
+ * the last pass of CholeskyQR2 and of shifted CholeskyQR3.  Their earlier passes, whose R may be
+ * ill-conditioned, use substitution.  enable = 0 selects the CUDA-core kernels of the chosen
+ * precision everywhere. */
 randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable);
 
 /* ---- Per-kernel timing (tracing) ------------------------------------------------------

@@ -196,7 +196,8 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
 // With Rprev, writes Rnext = R_x Rprev (packed); with Rdense, writes that product (or R_x)
 // dense.
 // Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores: only where R_c is well
-// conditioned by construction (rand_cholQR's second pass); R_c^{-1} goes to w.Rt2.
+// conditioned by construction (rand_cholQR's solves, the last pass of CholeskyQR2 and of
+// shifted CholeskyQR3); R_c^{-1} goes to w.Rt2 (after the Cholesky kernel has read it).
 randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const void *X, bool x_df, int64_t ldx, double *Y,
                                   int64_t ldy, int64_t m, int64_t n, const Workspace &w,
                                   cudaStream_t s) {
@@ -529,9 +530,10 @@ randqr_status randqr_cholqr2(randqr_ctx *ctx, const double *V, int64_t m, int64_
                         RANDQR_FP64, w, s)) != RANDQR_OK)
     return st;
   RQ_CUDA(cudaMemcpyAsync(w.Rt, w.Rc, sizeof(double) * packed(n), cudaMemcpyDeviceToDevice, s));
-  // pass 2 in place; R = R1 R0
+  // pass 2 in place; R = R1 R0.  Q0 is orthonormal to O(u kappa(V)^2) when pass 1 succeeded,
+  // so R1 is well conditioned and its solve may run as a product with the inverse.
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, nullptr, R, ldr, 2, RANDQR_FP64,
-                        w, s)) != RANDQR_OK)
+                        w, s, /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
   return finish_call(ctx, s, info);
 }
@@ -556,8 +558,9 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, w.Rt2, nullptr, 0, 2, RANDQR_FP64,
                         w, s)) != RANDQR_OK)
     return st;
+  // (the last pass factors a nearly orthonormal Q1: well conditioned)
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt2, nullptr, R, ldr, 3, RANDQR_FP64,
-                        w, s)) != RANDQR_OK)
+                        w, s, /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
   return finish_call(ctx, s, info);
 }

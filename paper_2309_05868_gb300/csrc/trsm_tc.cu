@@ -54,9 +54,9 @@ constexpr size_t OFF_B = 0;
 constexpr size_t OFF_A = OFF_B + (size_t)NDIG * B_SLICE;
 constexpr size_t OFF_STAGE = OFF_A + (size_t)NDIG * A_SLICE;
 constexpr size_t OFF_ROWEXP = OFF_STAGE + (size_t)TQ_NSTAGE * STAGE_BYTES;
-constexpr size_t OFF_COLEXP = OFF_ROWEXP + 2 * TQ_ROWS * sizeof(int);
+constexpr size_t OFF_COLEXP = OFF_ROWEXP + 3 * TQ_ROWS * sizeof(int);
 constexpr size_t OFF_BARS = OFF_COLEXP + TQ_NP * sizeof(int);
-constexpr int NBARS = 2 * TQ_NSTAGE + 5;  // full[3], empty[3], a_full, a_empty, t_full, t_empty, drain
+constexpr int NBARS = 2 * TQ_NSTAGE + 7;  // full[3], empty[3], a_full, kdone[4], t_empty, drain
 constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;  // tmem slot, abort flag, slot tags[3]
 constexpr size_t TQ_SMEM = OFF_MISC + 32;
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
@@ -93,11 +93,13 @@ __device__ __forceinline__ constexpr uint64_t b_off(int t, int c) {
   return ((uint64_t)t * B_SLICE + (uint64_t)(c == 0 ? 0 : c == 1 ? 64 : c == 2 ? 112 : 144) * 32) >> 4;
 }
 
-// One tile's MMAs, fully unrolled so that every descriptor is a base plus a constant (a
-// single issuing thread otherwise spends more time forming descriptors than the tensor core
-// spends on the products).  Region 8 goes first into region 7's columns; within a K-step the
-// (s, t) order walks across regions.
-__device__ __forceinline__ void issue_tile(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
+// A tile's MMAs, fully unrolled so that every descriptor is a base plus a constant (a single
+// issuing thread otherwise spends more time forming descriptors than the tensor core spends on
+// the products).  Region 8 goes first, into region 7's columns, for every K-step; then the main
+// products K-step by K-step.  After main K-step c nothing reads A's K-block c again and no
+// later product touches columns < 16 (c + 1), so a commit there releases that block of A to
+// the next tile's slicers and columns 16c .. 16c + 15 of every region to the read-back.
+__device__ __forceinline__ void issue_region8(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
@@ -106,20 +108,21 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint64_t ad0, uint64_t
       umma_bf16(tmem + (uint32_t)(7 * 64 + 16 * c), ad0 + a_off(s, c), bd0 + b_off(8 - s, c), idesc,
                 (c | (s - 1)) ? 1u : 0u);
   }
+}
+
+template <int C>
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
+  const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * C);
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const uint32_t idesc = umma_idesc_f16(TQ_ROWS, TQ_NP - 16 * c);
+  for (int s = 0; s < NDIG; ++s)
 #pragma unroll
-    for (int s = 0; s < NDIG; ++s)
-#pragma unroll
-      for (int t = 0; t < NDIG - s; ++t) {
-        const uint32_t d = tmem + (uint32_t)((s + t) * 64 + 16 * c);
-        if (c == 0 && s == 0 && t == NDIG - 1)
-          umma_scaled7(d, ad0 + a_off(s, c), bd0 + b_off(t, c), idesc);  // D_8 (every K-step) x 2^-7
-        else
-          umma_bf16(d, ad0 + a_off(s, c), bd0 + b_off(t, c), idesc, (c | s) ? 1u : 0u);
-      }
-  }
+    for (int t = 0; t < NDIG - s; ++t) {
+      const uint32_t d = tmem + (uint32_t)((s + t) * 64 + 16 * C);
+      if (C == 0 && s == 0 && t == NDIG - 1)
+        umma_scaled7(d, ad0 + a_off(s, C), bd0 + b_off(t, C), idesc);  // D_8 (every K-step) x 2^-7
+      else
+        umma_bf16(d, ad0 + a_off(s, C), bd0 + b_off(t, C), idesc, (C | s) ? 1u : 0u);
+    }
 }
 
 }  // namespace
@@ -146,9 +149,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   volatile int *slot_tag = (volatile int *)(tq_smem + OFF_MISC + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[TQ_NSTAGE]);
-  const uint32_t a_full = smem_addr(&bars[2 * TQ_NSTAGE]), a_empty = smem_addr(&bars[2 * TQ_NSTAGE + 1]);
-  const uint32_t t_full = smem_addr(&bars[2 * TQ_NSTAGE + 2]), t_empty = smem_addr(&bars[2 * TQ_NSTAGE + 3]);
-  const uint32_t drain = smem_addr(&bars[2 * TQ_NSTAGE + 4]);
+  const uint32_t a_full = smem_addr(&bars[2 * TQ_NSTAGE]);
+  const uint32_t kdone0 = smem_addr(&bars[2 * TQ_NSTAGE + 1]);  // kdone[c] at kdone0 + 8c
+  const uint32_t t_empty = smem_addr(&bars[2 * TQ_NSTAGE + 5]), drain = smem_addr(&bars[2 * TQ_NSTAGE + 6]);
 
   if (tid == 0) {
     for (int q = 0; q < TQ_NSTAGE; ++q) {
@@ -156,8 +159,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       mbar_init_count(empty0 + 8 * q, 4);
     }
     mbar_init_count(a_full, 8);
-    mbar_init_count(a_empty, 1);
-    mbar_init_count(t_full, 1);
+    for (int c = 0; c < 4; ++c) mbar_init_count(kdone0 + 8 * c, 1);
     mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
     *abort_flag = 0;
@@ -256,9 +258,15 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         // opaque per tile: keeps the compiler from hoisting all 172 descriptor sums into registers
         uint64_t ad = ad0, bd = bd0;
         asm volatile("" : "+l"(ad), "+l"(bd));
-        issue_tile(tmem, ad, bd);
-        umma_commit(a_empty);
-        umma_commit(t_full);
+        issue_region8(tmem, ad, bd);
+        issue_kstep<0>(tmem, ad, bd);
+        umma_commit(kdone0);
+        issue_kstep<1>(tmem, ad, bd);
+        umma_commit(kdone0 + 8);
+        issue_kstep<2>(tmem, ad, bd);
+        umma_commit(kdone0 + 16);
+        issue_kstep<3>(tmem, ad, bd);
+        umma_commit(kdone0 + 24);
       }
       // every MMA issued so far completes before tensor memory is released
       umma_commit(drain);
@@ -267,47 +275,62 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     __syncwarp();
   } else if (warp < W_FLUSH0) {
     // ------------------------------------------------------------------ slicers
-    const int grp = warp >> 2, sg = warp & 3;     // sub-tiles q = grp, grp + 2; rows 8 sg ..
-    const int r = 8 * sg + (lane & 7), pi = lane >> 3;
+    // Each warp takes one 8-row group in sub-tiles grp and grp + 2, reads both into registers
+    // (freeing the stage slots at once), then writes A block by block as the previous tile's
+    // K-steps release them.
+    const int grp = warp >> 2, sg = warp & 3;
+    const int r = 8 * sg + (lane & 7), pi = lane >> 3;  // pi: column pair within each K core matrix
     bool ok = true;
     for (int i = 0; i < ntiles && ok; ++i) {
-      const int buf = i & 1;
+      unsigned long long ea[2][8], eb[2][8];
+      int E[2];
+#pragma unroll
       for (int qq = 0; qq < 2; ++qq) {
         const int q = grp + 2 * qq, u = 4 * i + q, slot = u % TQ_NSTAGE;
         bool tagged = false;
         for (int it = 0; it < MAX_WAIT && !tagged && !*abort_flag; ++it) tagged = slot_tag[slot] == u;
-        if (!tagged || !mbar_wait_or_abort(full0 + 8 * slot, (u / TQ_NSTAGE) & 1, abort_flag) ||
-            (qq == 0 && !mbar_wait_or_abort(a_empty, (i & 1) ^ 1, abort_flag))) {
+        if (!tagged || !mbar_wait_or_abort(full0 + 8 * slot, (u / TQ_NSTAGE) & 1, abort_flag)) {
           ok = false;
           break;
         }
-        const int cnt = sub_rows(i, q), row = TQ_SUB * q + r;
+        const int cnt = sub_rows(i, q);
         const uint8_t *src = stage + (size_t)slot * STAGE_BYTES + r * STAGE_PITCH + 16 * pi;
-        // this lane: columns 8 kg + 2 pi and 8 kg + 2 pi + 1 of its row, kg = 0 .. 7
-        unsigned long long ea[8], eb[8];
         int mx = 0;
 #pragma unroll
-        for (int kg = 0; kg < 8; ++kg) {
+        for (int kg = 0; kg < 8; ++kg) {  // columns 8 kg + 2 pi, 8 kg + 2 pi + 1 of row r
           const ulonglong2 raw = *(const ulonglong2 *)(src + 64 * kg);
           const int c0 = 8 * kg + 2 * pi;
-          ea[kg] = (r < cnt && c0 < n) ? raw.x : 0ULL;
-          eb[kg] = (r < cnt && c0 + 1 < n) ? raw.y : 0ULL;
-          mx = max(mx, max(elem_expfield<IN_DF>(ea[kg]), elem_expfield<IN_DF>(eb[kg])));
-        }
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-        const int E = scale_exp(mx);
-        if (pi == 0) rowexp[buf * TQ_ROWS + row] = E;
-        uint8_t *dst = As + (size_t)(row >> 3) * A_SBO + (row & 7) * 16 + pi * 4;
-#pragma unroll
-        for (int kg = 0; kg < 8; ++kg) {
-          uint32_t w[NDIG];
-          digits2(elem_fix<IN_DF>(ea[kg], E), elem_fix<IN_DF>(eb[kg], E), w);
-#pragma unroll
-          for (int p = 0; p < NDIG; ++p) *(uint32_t *)(dst + (size_t)(NDIG - 1 - p) * A_SLICE + kg * A_LBO) = w[p];
+          ea[qq][kg] = (r < cnt && c0 < n) ? raw.x : 0ULL;
+          eb[qq][kg] = (r < cnt && c0 + 1 < n) ? raw.y : 0ULL;
+          mx = max(mx, max(elem_expfield<IN_DF>(ea[qq][kg]), elem_expfield<IN_DF>(eb[qq][kg])));
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        E[qq] = scale_exp(mx);
+        if (pi == 0) rowexp[(i % 3) * TQ_ROWS + TQ_SUB * q + r] = E[qq];
+      }
+      if (!ok) break;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (i > 0 && !mbar_wait_or_abort(kdone0 + 8 * c, (i - 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+          const int row = TQ_SUB * (grp + 2 * qq) + r;
+          uint8_t *dst = As + (size_t)(row >> 3) * A_SBO + (row & 7) * 16 + pi * 4;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const int kg = 2 * c + kk;
+            uint32_t w[NDIG];
+            digits2(elem_fix<IN_DF>(ea[qq][kg], E[qq]), elem_fix<IN_DF>(eb[qq][kg], E[qq]), w);
+#pragma unroll
+            for (int p = 0; p < NDIG; ++p) *(uint32_t *)(dst + (size_t)(NDIG - 1 - p) * A_SLICE + kg * A_LBO) = w[p];
+          }
+        }
       }
       if (!ok) break;
       fence_async_smem();
@@ -317,49 +340,57 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     if (!ok && lane == 0 && !*abort_flag) set_abort(abort_flag, st);
   } else {
     // ------------------------------------------------------------------ recombination
-    const int f = warp - W_FLUSH0, quad = f & 3, ch = f >> 2;  // warp % 4 == quad: TMEM lanes 32 quad ..
+    // Column block b (16 columns) of every region is final once K-step b is done; each warp
+    // reads 8 of its columns for its 32 TMEM lanes.
+    const int f = warp - W_FLUSH0, quad = f & 3, half = f >> 2;  // warp % 4 == quad: lanes 32 quad ..
     const int L = 32 * quad + lane;
     const uint32_t tq = tmem + ((uint32_t)(32 * quad) << 16);
-    for (int i = 0; i < ntiles; ++i) {
-      if (!mbar_wait_or_abort(t_full, i & 1, abort_flag)) {
-        if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
-        break;
-      }
-      fence_after_sync();
-      const int er = rowexp[(i & 1) * TQ_ROWS + L];
+    bool ok = true;
+    for (int i = 0; i < ntiles && ok; ++i) {
       const int64_t grow = r_begin + (int64_t)i * TQ_ROWS + L;
       double *yrow = Y + grow * ldy;
+      int er = 0;
 #pragma unroll 1
-      for (int h = 0; h < 8; ++h) {
-        const int k0 = 32 * ch + 4 * h;
-        uint32_t v[NDIG][4];
-#pragma unroll
-        for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + k0), v[g]);
-        tmem_wait_ld();
-        tmem_regs_ready(v);
-        if (h == 7) {  // every region read: the next tile's MMAs may start
-          fence_before_sync();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(t_empty);
+      for (int b = 0; b < 4; ++b) {
+        if (!mbar_wait_or_abort(kdone0 + 8 * b, i & 1, abort_flag)) {
+          ok = false;
+          break;
         }
-        double y[4];
+        fence_after_sync();
+        if (b == 0) er = rowexp[(i % 3) * TQ_ROWS + L];
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh) {
+          const int k0 = 16 * b + 8 * half + 4 * hh;
+          uint32_t v[NDIG][4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const long long t = recombine8<3>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
-          y[c] = int_times_pow2(t, er + scale_exp(colexp[k0 + c]) - 56);  // T / 8 (|T| < 2^65)
-        }
-        if (grow < r_end) {
-          if (vec_store && k0 + 3 < n) {
-            *(double2 *)(yrow + k0) = make_double2(y[0], y[1]);
-            *(double2 *)(yrow + k0 + 2) = make_double2(y[2], y[3]);
-          } else {
+          for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + k0), v[g]);
+          tmem_wait_ld();
+          tmem_regs_ready(v);
+          if (b == 3 && hh == 1) {  // every region read: the next tile's MMAs may start
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty);
+          }
+          double y[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (k0 + c < n) yrow[k0 + c] = y[c];
+          for (int c = 0; c < 4; ++c) {
+            const long long t = recombine8<3>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+            y[c] = int_times_pow2(t, er + scale_exp(colexp[k0 + c]) - 56);  // T / 8 (|T| < 2^65)
+          }
+          if (grow < r_end) {
+            if (vec_store && k0 + 3 < n) {
+              *(double2 *)(yrow + k0) = make_double2(y[0], y[1]);
+              *(double2 *)(yrow + k0 + 2) = make_double2(y[2], y[3]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (k0 + c < n) yrow[k0 + c] = y[c];
+            }
           }
         }
       }
     }
+    if (!ok && lane == 0 && !*abort_flag) set_abort(abort_flag, st);
   }
 
   __syncthreads();
