@@ -321,6 +321,14 @@ __device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32
   return (th << (28 - SH)) + (tl >> SH);
 }
 
+// (double) t * 2^e for |t| < 2^63 and a result in the normal range (0 for t == 0), through the
+// FP64 pipe's int64 conversion: for kernels whose FP64 pipe is otherwise idle and whose issue
+// slots are the scarce resource.
+__device__ __forceinline__ double int_times_pow2_cvt(long long t, int e) {
+  const double y = (double)t;
+  return t != 0 ? __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y)) : 0.0;
+}
+
 // (double) t * 2^e, rounded to nearest (ties away from zero), for |t| < 2^63 and a result in
 // the normal range; 0 for t == 0.  Integer instructions only: the FP64 pipe (about 1/64 of the
 // FP32 rate on this part) is left to the callers' additions.

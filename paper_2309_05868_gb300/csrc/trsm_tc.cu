@@ -358,24 +358,29 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         }
         fence_after_sync();
         if (b == 0) er = rowexp[(i % 3) * TQ_ROWS + L];
-#pragma unroll 1
+        // both 4-column groups of this warp's 8 columns are loaded before one wait
+        uint32_t v[2][NDIG][4];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+          for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + 16 * b + 8 * half + 4 * hh), v[hh][g]);
+        tmem_wait_ld();
+        tmem_regs_ready(v[0]);
+        tmem_regs_ready(v[1]);
+        if (b == 3) {  // every region read: the next tile's MMAs may start
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(t_empty);
+        }
+#pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int k0 = 16 * b + 8 * half + 4 * hh;
-          uint32_t v[NDIG][4];
-#pragma unroll
-          for (int g = 0; g < NDIG; ++g) tmem_ld4(tq + (uint32_t)(g * 64 + k0), v[g]);
-          tmem_wait_ld();
-          tmem_regs_ready(v);
-          if (b == 3 && hh == 1) {  // every region read: the next tile's MMAs may start
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(t_empty);
-          }
           double y[4];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const long long t = recombine8<3>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
-            y[c] = int_times_pow2(t, er + scale_exp(colexp[k0 + c]) - 56);  // T / 8 (|T| < 2^65)
+            const long long t = recombine8<3>(v[hh][0][c], v[hh][1][c], v[hh][2][c], v[hh][3][c], v[hh][4][c],
+                                              v[hh][5][c], v[hh][6][c], v[hh][7][c]);
+            y[c] = int_times_pow2_cvt(t, er + scale_exp(colexp[k0 + c]) - 56);  // T / 8 (|T| < 2^65)
           }
           if (grow < r_end) {
             if (vec_store && k0 + 3 < n) {
