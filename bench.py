@@ -42,6 +42,13 @@ def roofline_model(kind, n):
             "trsm_tc": ("hbm", 16 * n)}.get(kind)
 
 
+# DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
+# m = 2^20, n = 64, divided by m; see profiles/split_product_kernels_m1048576_n64_ncu.md),
+# scaled to a launch by the rows it processes.  Valid for n = 64 and the kernels as captured.
+MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.0e6 + 483.6e6) / 1048576,
+                                   "gram_tc": (537.05e6 + 3.66e6) / 1048576}
+
+
 def kernel_roofline(kind, avg_ms, m, n):
     model = roofline_model(kind, n)
     if model is None:
@@ -57,8 +64,10 @@ def kernel_roofline(kind, avg_ms, m, n):
                 "algorithmic": f"{per_row} FP64 flops per row x {m} rows per launch"}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     achieved = per_row * m / (avg_ms / 1e3) / 1e9
+    traffic = MEASURED_DRAM_BYTES_PER_ROW_N64[kind] * m if (n == 64 and kind in MEASURED_DRAM_BYTES_PER_ROW_N64) else None
     return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_source": "ncu dram bytes per row at m=2^20, n=64, scaled by m" if traffic else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
             "algorithmic": f"{per_row} bytes per row x {m} rows per launch"}
 
