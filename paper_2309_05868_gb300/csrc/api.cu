@@ -59,6 +59,7 @@ cudaError_t timed(randqr_ctx *ctx, cudaStream_t s, int kind, F &&f) {
 struct Workspace {
   double *W1, *Ws, *Rs, *G, *Rc, *Rt, *Rt2;
   float2 *Rdf, *rinv;  // pair form of the current triangular factor (RANDQR_F32X2)
+  double *hq;          // multi-CTA Householder scratch (published reflectors, flags)
 };
 
 size_t packed(int64_t n) { return (size_t)(n * (n + 1) / 2); }
@@ -82,13 +83,14 @@ randqr_status ensure_ws(randqr_ctx *ctx, size_t bytes) {
 }
 
 randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspace *w) {
-  const size_t sz[9] = {align_up(sizeof(double) * (size_t)(s1 * n)),
-                        align_up(sizeof(double) * (size_t)(s2 * n)),
-                        align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
-                        align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
-                        align_up(sizeof(double) * packed(n)),
-                        align_up(sizeof(float2) * rq::pack_df_elems(n)),
-                        align_up(sizeof(float2) * rq::pack_df_rinv_elems(n))};
+  const size_t sz[10] = {align_up(sizeof(double) * (size_t)(s1 * n)),
+                         align_up(sizeof(double) * (size_t)(s2 * n)),
+                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
+                         align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
+                         align_up(sizeof(double) * packed(n)),
+                         align_up(sizeof(float2) * rq::pack_df_elems(n)),
+                         align_up(sizeof(float2) * rq::pack_df_rinv_elems(n)),
+                         align_up(sizeof(double) * rq::hhqr_scratch_doubles(s2, n))};
   size_t total = 0;
   for (size_t b : sz) total += b;
   randqr_status st = ensure_ws(ctx, total);
@@ -102,6 +104,8 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
   w->Rdf = (float2 *)p;
   p += sz[7];
   w->rinv = (float2 *)p;
+  p += sz[8];
+  w->hq = (double *)p;
   return RANDQR_OK;
 }
 
@@ -188,7 +192,7 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
     return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
   }));
   if (do_hhqr)
-    RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, ctx->status_dev, s); }));
+    RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));
   return RANDQR_OK;
 }
 

@@ -151,7 +151,10 @@ cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv
 cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, int64_t s1,
                                int64_t n, double *Ws, int num_sms, const DevStatus *st,
                                cudaStream_t s);
-cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
+// Householder R of the rows x n sketch; with scratch (hhqr_scratch_doubles) and n >= 32 it runs
+// on several co-resident CTAs, otherwise on one.
+size_t hhqr_scratch_doubles(int64_t rows, int64_t n);
+cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, double *scratch, DevStatus *st,
                         cudaStream_t s);
 cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,
                          const double *Rprev_packed, double *Rout_packed, double *Rout,

@@ -2,8 +2,8 @@
 //   Householder QR of the s2 x n sketch (Algorithm 1 step 2), R only, positive diagonal;
 //   Cholesky of the n x n Gram (Algorithm 2 step 2), optionally shifted (sCholQR3);
 //   R = R_c R_prev (Algorithm 3 step 3 / Algorithm 4 step 3).
-// Each runs as one CTA so no host round trip separates it from the row passes; all are
-// FP64.  Triangular factors travel between kernels in packed column-major upper storage
+// Each runs on the device (one CTA, or a few co-resident CTAs for the Householder QR) so no
+// host round trip separates it from the row passes; all are FP64.  Triangular factors travel between kernels in packed column-major upper storage
 // (tri_idx), which is what the row-pass kernels stage in shared memory.
 #include "common.cuh"
 
@@ -118,8 +118,163 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_hhqr(double *Ag, int rows, in
   }
 }
 
-cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
+// ---------------------------------------------------------------------------------------
+// The same Householder QR on HQ_CTAS co-resident CTAs (one cooperative launch).  CTA b keeps
+// the columns k with k % HQ_CTAS == b in shared memory (column-major, so a warp walks down a
+// column with unit stride).  Step j: the owner of column j forms the reflector (sigma, beta,
+// tau, v = A[j+1:, j] / (a_jj - beta)) and publishes tau, beta and v through global memory (L2)
+// with a per-step flag; every CTA then applies it to its own columns k > j, one warp per
+// column.  The owner of column j + 1 updates that column first and publishes reflector j + 1
+// before its other columns (look-ahead), so a step costs about one column update plus one
+// flag round trip.  Waits are bounded (RANDQR_ERR_TIMEOUT).  The result equals k_hhqr's up to
+// the order of the dot products.
+// ---------------------------------------------------------------------------------------
+constexpr int HQ_CTAS = 16, HQ_THREADS = 256, HQ_MAX_WAIT = 1 << 22;
+
+
+// Form reflector j from local column `col` (rows 0..rows-1) and publish it; one warp.
+__device__ __forceinline__ void hq_reflect(double *col, int rows, int j, double *pub, volatile int *flag,
+                                          int lane) {
+  double part = 0.0;
+  for (int i = j + 1 + lane; i < rows; i += 32) part = fma(col[i], col[i], part);
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  const double x0 = col[j];
+  double tau = 0.0, beta = x0, rv0 = 0.0;
+  if (part != 0.0) {
+    const double alpha = sqrt(x0 * x0 + part);
+    beta = (x0 >= 0.0) ? -alpha : alpha;
+    rv0 = 1.0 / (x0 - beta);
+    tau = (beta - x0) / beta;
+  }
+  // pub: [tau, beta, v_{j+1} .. v_{rows-1}] at offsets 0, 1, 2 + (i - j - 1)
+  for (int i = j + 1 + lane; i < rows; i += 32) {
+    const double v = col[i] * rv0;
+    col[i] = v;
+    pub[2 + (i - j - 1)] = v;
+  }
+  if (lane == 0) {
+    col[j] = beta;
+    pub[0] = tau;
+    pub[1] = beta;
+  }
+  __threadfence();  // each lane's part of the reflector is visible device-wide ...
+  __syncwarp();
+  if (lane == 0) *flag = 1;  // ... before the flag
+}
+
+__global__ void __launch_bounds__(HQ_THREADS) k_hhqr_coop(const double *Ag, int rows, int n, double *pub,
+                                                          int *flags, double *Rp, DevStatus *st) {
+  if (status_failed(st)) return;
+  extern __shared__ double hq_sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ncl = (n - b + HQ_CTAS - 1) / HQ_CTAS;  // local columns: k = b + HQ_CTAS * c
+  double *cols = hq_sm;                              // ncl x rows
+  double *vsh = hq_sm + (size_t)ncl * rows;          // rows: current reflector
+  __shared__ double s_tau;
+  __shared__ int s_fail;
+  const size_t stride = (size_t)rows + 2;
+  for (int e = tid; e < ncl * rows; e += HQ_THREADS) {
+    const int c = e / rows, i = e - c * rows;
+    cols[e] = Ag[(size_t)i * n + b + HQ_CTAS * c];
+  }
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  // reflector 0 from its owner
+  if (b == 0 && warp == 0) hq_reflect(cols, rows, 0, pub, flags, lane);
+  for (int j = 0; j < n; ++j) {
+    // wait for reflector j
+    if (tid == 0) {
+      int ok = 0;
+      for (int it = 0; it < HQ_MAX_WAIT && !ok; ++it) ok = *(volatile int *)&flags[j];
+      if (!ok) {
+        s_fail = 1;
+        status_fail(st, RANDQR_ERR_TIMEOUT, j + 1, 0);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const double *pj = pub + (size_t)j * stride;
+    for (int i = j + 1 + tid; i < rows; i += HQ_THREADS) vsh[i] = *(volatile const double *)&pj[2 + (i - j - 1)];
+    if (tid == 0) s_tau = *(volatile const double *)&pj[0];
+    __syncthreads();
+    const double tau = s_tau;
+    // local columns k > j; the owner of column j + 1 handles it first and publishes reflector j + 1
+    const int c_next = (j + 1 < n && (j + 1) % HQ_CTAS == b) ? (j + 1) / HQ_CTAS : -1;
+    if (tau != 0.0) {
+      for (int t = warp; t < ncl; t += HQ_THREADS / 32) {
+        // order: c_next first (warp 0), then the rest
+        int c = t;
+        if (c_next >= 0) c = (t == 0) ? c_next : (t <= c_next ? t - 1 : t);
+        const int k = b + HQ_CTAS * c;
+        if (k <= j) continue;
+        double *col = cols + (size_t)c * rows;
+        double acc = 0.0;
+        for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(vsh[i], col[i], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double w = tau * (col[j] + acc);
+        if (lane == 0) col[j] -= w;
+        for (int i = j + 1 + lane; i < rows; i += 32) col[i] = fma(-vsh[i], w, col[i]);
+        __syncwarp();
+        if (c == c_next) hq_reflect(col, rows, j + 1, pub + (size_t)(j + 1) * stride, flags + j + 1, lane);
+      }
+    } else if (c_next >= 0 && warp == 0) {
+      hq_reflect(cols + (size_t)c_next * rows, rows, j + 1, pub + (size_t)(j + 1) * stride, flags + j + 1, lane);
+    }
+    __syncthreads();
+  }
+  // R (rows flipped to a positive diagonal), packed column-major upper: this CTA's columns
+  for (int c = 0; c < ncl; ++c) {
+    const int k = b + HQ_CTAS * c;
+    for (int i = tid; i <= k; i += HQ_THREADS) {
+      const double bi = *(volatile const double *)&pub[(size_t)i * stride + 1];
+      const double v = cols[(size_t)c * rows + i];
+      Rp[tri_idx(i, k)] = bi < 0.0 ? -v : v;
+    }
+  }
+  if (b == 0 && tid == 0) {
+    double dmin = INFINITY, dmax = 0.0;
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+      const double d = fabs(*(volatile const double *)&pub[(size_t)k * stride + 1]);
+      if (!(d > 0.0) || !isfinite(d)) bad = bad ? bad : k + 1;
+      dmin = fmin(dmin, d);
+      dmax = fmax(dmax, d);
+    }
+    st->dmin = dmin;
+    st->dmax = dmax;
+    if (bad) status_fail(st, RANDQR_ERR_RANK, bad, 0);
+  }
+}
+
+size_t hhqr_scratch_doubles(int64_t rows, int64_t n) { return (size_t)n * (size_t)(rows + 2) + (size_t)(n + 1) / 2 + 1; }
+
+cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, double *scratch, DevStatus *st,
                         cudaStream_t s) {
+  const int ncl = (int)ceil_div(n, HQ_CTAS);
+  const size_t coop_smem = sizeof(double) * (size_t)(ncl + 1) * (size_t)rows;
+  if (scratch && n >= 2 * HQ_CTAS && coop_smem <= 200 * 1024) {
+    // scratch: n published reflectors (rows + 2 doubles each), then n flags
+    double *pub = scratch;
+    int *flags = (int *)(scratch + (size_t)n * (size_t)(rows + 2));
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    if (coop_smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_hhqr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coop_smem);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(HQ_CTAS);
+    cfg.blockDim = dim3(HQ_THREADS);
+    cfg.dynamicSmemBytes = coop_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_hhqr_coop, (const double *)A, (int)rows, (int)n, pub, flags, Rpacked, st);
+  }
   size_t smem = sizeof(double) * (size_t)(n + rows * (n + 1));
   bool use_smem = smem <= 200 * 1024;
   size_t dyn = use_smem ? smem : sizeof(double) * (size_t)n;
