@@ -11,8 +11,10 @@ and one write of Q, FP64) over the step time; V is 4.3 GB, far larger than the 1
 so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-N > 1 runs independent replicas (one matrix per rank, no collective in the data path)
-under torchrun and reports the whole-job aggregate.
+N > 1 (under torchrun) factors ONE matrix of N m rows, row-sharded over the ranks (Sec. 4.1):
+each rank holds m rows, and the step's two cross-shard sums (the s2 x n sketch and the n x n
+Gram) are NCCL allreduces.  Per-rank work is fixed (weak scaling); the value is the
+whole-job aggregate.
 """
 import argparse
 import json
@@ -391,13 +393,18 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2309_05868_gb300 as rq
+    from paper_2309_05868_gb300 import sharded
     import synthetic
 
     m, n = a.m, a.n
     s1, s2 = synthetic.default_sketch_sizes(n)
     prec = rq.FP64 if a.prec == "fp64" else rq.F32X2
     dev = torch.device("cuda", local_rank)
-    if a.gen == "qr":
+    if world > 1 and a.prec != "fp64":
+        raise SystemExit("the row-sharded path (N > 1) runs FP64 row passes only")
+    if world > 1 and a.gen == "qr":
+        V = synthetic.make_v_block_torch(m, n, a.kappa, rank, world, seed=0, device=dev)
+    elif a.gen == "qr":
         V = synthetic.make_v_torch(m, n, a.kappa, seed=rank, device=dev)
     else:
         g = torch.Generator(device=dev)
@@ -412,9 +419,20 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    stages = sharded.DeviceStages(ctx, stream, sync=False)
+    allreduce = sharded.dist_allreduce() if world > 1 else None
+
+    def factor_once(Vin, prec_):
+        if world > 1:
+            _, Rk = sharded.factor_row_sharded(Vin, rank * m, allreduce, s1, s2, seed=0, Q=Q,
+                                               stages=stages)
+            R.copy_(Rk)
+        else:
+            rq.randqr_factor(Vin, s1, s2, seed=0, prec=prec_, Q=Q, R=R, ctx=ctx, sync=False)
+
     def measure(prec_, steps, sample_clocks=False):
         def step():
-            rq.randqr_factor(V, s1, s2, seed=0, prec=prec_, Q=Q, R=R, ctx=ctx, sync=False)
+            factor_once(V, prec_)
 
         for _ in range(max(a.warmup, 3)):
             step()
@@ -446,10 +464,15 @@ def main():
             t = torch.tensor([ms_], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms_ = t.item()
-        # accuracy of the timed result (whole matrix, checked on the device with torch)
+        # accuracy of the timed result (whole matrix, checked on the device with torch; the
+        # row blocks' Q^T Q and squared norms summed over the ranks)
         G = Q.T @ Q
+        sq = torch.stack([torch.linalg.norm(V - Q @ R) ** 2, torch.linalg.norm(V) ** 2])
+        if world > 1:
+            torch.distributed.all_reduce(G)
+            torch.distributed.all_reduce(sq)
         orth = torch.linalg.matrix_norm(G - torch.eye(n, dtype=G.dtype, device=dev), ord=2).item()
-        resid = (torch.linalg.norm(V - Q @ R) / torch.linalg.norm(V)).item()
+        resid = (sq[0] / sq[1]).sqrt().item()
         return ms_, kt_, clk, {"orth_err_2": orth, "resid_rel_F": resid}
 
     ms, kt, clk, acc = measure(prec, a.steps, sample_clocks=True)
@@ -469,21 +492,47 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(a), "m": m, "n": n, "kappa": a.kappa,
                        "s1": s1, "s2": s2, "precision": a.prec,
-                       "parallelism": "replicas" if world > 1 else "single",
+                       "parallelism": f"row-sharded x{world} (NCCL allreduce of the sketch and Gram)"
+                       if world > 1 else "single",
                        "l2": "inputs larger than L2 (V = %.1f GB)" % (8.0 * m * n / 1e9)},
             "roofline": roof, "clocks": clk,
             "gpu_launches": sum(c for _, c in kt.values()),
             "kernels_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()},
             "accuracy": acc}
 
+    if not a.no_extras and world == 1:
+        # the row-sharded decomposition as logical shards on this GPU (sums in shard order)
+        P = 4
+        cuts = sharded.even_cuts(m, P)
+        Qs = Q
+
+        def logical_step():
+            sharded.factor_logical_shards(V, cuts, s1, s2, seed=0, Q=Qs, stages=stages)
+
+        for _ in range(3):
+            logical_step()
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(3):
+            logical_step()
+        h1.record(stream)
+        torch.cuda.synchronize()
+        sh_ms = h0.elapsed_time(h1) / 3
+        st, info = rq.get_status(ctx)
+        line["sharded_logical"] = {"shards": P, "ms_per_step": sh_ms,
+                                   "value": algo_bytes / (sh_ms / 1e3) / 1e9, "unit": "GB/s",
+                                   "over_unsharded": sh_ms / ms, "status": st}
+
     if not a.no_extras:
-        # the other precision of the row passes, on the same matrix
-        other = "f32x2" if a.prec == "fp64" else "fp64"
-        oprec = rq.F32X2 if other == "f32x2" else rq.FP64
-        oms, okt, _, oacc = measure(oprec, a.steps)
-        line["modes"] = {other: {"value": algo_bytes * world / (oms / 1e3) / 1e9, "unit": "GB/s",
-                                 "ms_per_step": oms, "accuracy": oacc,
-                                 "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
+        if world == 1:
+            # the other precision of the row passes, on the same matrix
+            other = "f32x2" if a.prec == "fp64" else "fp64"
+            oprec = rq.F32X2 if other == "f32x2" else rq.FP64
+            oms, okt, _, oacc = measure(oprec, a.steps)
+            line["modes"] = {other: {"value": algo_bytes / (oms / 1e3) / 1e9, "unit": "GB/s",
+                                     "ms_per_step": oms, "accuracy": oacc,
+                                     "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
 
         # end to end through the public API: pinned host V in, Q and R back to pinned host
         Vh = V.cpu().pin_memory()
@@ -494,7 +543,7 @@ def main():
 
         def e2e_step():
             Vd2.copy_(Vh, non_blocking=True)
-            rq.randqr_factor(Vd2, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+            factor_once(Vd2, prec)
             Qh.copy_(Q, non_blocking=True)
             Rh.copy_(R, non_blocking=True)
 
@@ -507,6 +556,10 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = f0.elapsed_time(f1) / ke
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = t.item()
         line["e2e"] = {"value": algo_bytes * world / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
                        "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n,
                        "ms_per_step": e2e_ms}

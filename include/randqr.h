@@ -197,6 +197,50 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
                                      int64_t ldv, double *Q, int64_t ldq, double *R,
                                      int64_t ldr, randqr_info *info, void *stream);
 
+/* ---- Row-sharded rand_cholQR (Sec. 4.1) -----------------------------------------------
+ * V (M x n) split by rows over P shards, shard k holding rows [row0_k, row0_k + m_k).  The
+ * sketch is linear in V and the CountSketch hash is a function of the GLOBAL row index, so
+ * Ws = sum_k S2 S1_k V_k and G = sum_k W_k^T W_k: the method needs exactly two sums of small
+ * buffers across shards (s2 x n, then n x n), which the caller performs (an allreduce, a
+ * host loop, ...).  The stages, in order, every shard with its own context and data:
+ *   1. randqr_shard_sketch -> Ws_k;           caller: Ws = sum_k Ws_k
+ *   2. randqr_sketch_r(Ws) -> R_s            (deterministic: equal on every shard)
+ *   3. randqr_shard_gram(V_k, R_s) -> W_k = V_k R_s^{-1} in Q_k, G_k = W_k^T W_k;
+ *                                             caller: G = sum_k G_k
+ *   4. randqr_shard_finish(Q_k, G, R_s) -> Q_k = W_k R_c^{-1} in place, R = R_c R_s.
+ * With P = 1 (row0 = 0, m_1 = M) the stages compute what randqr_factor computes, kernel for
+ * kernel.  All matrices are row-major device buffers; m_k >= 1 (a shard may hold fewer rows
+ * than columns); 1 <= n <= 128.  Errors as for the calls above (RANDQR_ERR_ARG before
+ * anything is enqueued). */
+
+/* Ws_k = S2 S1_k V_k (s2 x n, ld n): the sketch of shard V_k (m x n, ldv) whose first row is
+ * global row row0 >= 0; S1_k holds the CountSketch columns row0 .. row0 + m - 1 of the global
+ * S1 (seed, s1), S2 as in randqr_sketch (NULL: generated for seed + 1 and cached). */
+randqr_status randqr_shard_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n, int64_t ldv,
+                                  int64_t row0, int64_t s1, int64_t s2, uint64_t seed, const double *S2,
+                                  double *Ws, void *stream);
+
+/* R_s from the summed sketch Ws (s2 x n, ld n, device; not modified): Householder QR
+ * (Algorithm 1 step 2), positive diagonal, written dense to Rs (n x n, ldr, zeros below the
+ * diagonal).  Requires n <= s2 <= 2^20.  With info non-NULL, waits and reports the status. */
+randqr_status randqr_sketch_r(randqr_ctx *ctx, const double *Ws, int64_t s2, int64_t n, double *Rs,
+                              int64_t ldr, randqr_info *info, void *stream);
+
+/* W_k = V_k R_s^{-1} into Q (m x n, ldq; may equal V with ldq == ldv) and G_k = W_k^T W_k
+ * into G (n x n, ldg, both triangles written).  Rs (n x n, ldrs) is read from its upper
+ * triangle.  The solve and the Gram use the same kernels as randqr_factor. */
+randqr_status randqr_shard_gram(randqr_ctx *ctx, const double *V, int64_t m, int64_t n, int64_t ldv,
+                                const double *Rs, int64_t ldrs, double *Q, int64_t ldq, double *G,
+                                int64_t ldg, void *stream);
+
+/* From the summed G (n x n, ldg, upper triangle read): R_c = chol(G) (Algorithm 2 step 2),
+ * Q_k = W_k R_c^{-1} in place (Q, m x n, ldq), and R = R_c R_s (n x n, ldr, dense upper with
+ * zeros below).  RANDQR_ERR_NOT_SPD through info (or randqr_get_status) if G is not
+ * numerically positive definite. */
+randqr_status randqr_shard_finish(randqr_ctx *ctx, double *Q, int64_t m, int64_t n, int64_t ldq,
+                                  const double *G, int64_t ldg, const double *Rs, int64_t ldrs, double *R,
+                                  int64_t ldr, randqr_info *info, void *stream);
+
 /* ---- Batched: many independent rand_cholQR factorizations in one graph launch ----------
  * The paper factors one matrix at a time; this call factors `count` matrices of uneven
  * sizes (Algorithm 3 on each, sketch sizes 0 -> 2(n^2+n), 4n; S2 from seed + 1) with their

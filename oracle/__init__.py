@@ -37,6 +37,9 @@ def _load():
     lib.orc_philox4x64_10.argtypes = [_ct.POINTER(_U64), _ct.POINTER(_U64), _ct.POINTER(_U64)]
     lib.orc_gauss_sketch.argtypes = [_U64, _I64, _I64, _D]
     lib.orc_countsketch.argtypes = [_D, _I64, _I64, _I64, _I64, _U64, _D]
+    lib.orc_countsketch_rows.argtypes = [_D, _I64, _I64, _I64, _I64, _U64, _I64, _D]
+    lib.orc_cs_hash_at.argtypes = [_U64, _I64, _I64, _I64, _ct.POINTER(_ct.c_int32),
+                                   _ct.POINTER(_ct.c_int8)]
     lib.orc_gemm.argtypes = [_D, _D, _I64, _I64, _I64, _D]
     lib.orc_hhqr_r.argtypes = [_D, _I64, _I64, _D]
     lib.orc_householder_qr.argtypes = [_D, _I64, _I64, _I64, _D, _D]
@@ -55,7 +58,7 @@ def _load():
     lib.orc_orth_err.argtypes = [_D, _I64, _I64, _I64, _D, _D]
     lib.orc_resid.restype = _ct.c_double
     lib.orc_resid.argtypes = [_D, _I64, _I64, _I64, _D, _I64, _D]
-    for name in ("orc_countsketch", "orc_hhqr_r", "orc_householder_qr", "orc_chol",
+    for name in ("orc_countsketch", "orc_countsketch_rows", "orc_hhqr_r", "orc_householder_qr", "orc_chol",
                  "orc_randqr", "orc_cholqr", "orc_rand_cholqr", "orc_cholqr2", "orc_scholqr3"):
         getattr(lib, name).restype = _ct.c_int
     _lib = lib
@@ -110,6 +113,25 @@ def countsketch(V, s1: int, seed: int):
     W1 = _np.empty((s1, n), dtype=_np.float64)
     _check(_load().orc_countsketch(_p(V), m, n, n, s1, _U64(seed), _p(W1)))
     return W1
+
+
+def countsketch_rows(V, s1: int, seed: int, row0: int):
+    """S1_k V_k for a row block whose first row is global row ``row0`` (Sec. 4.1)."""
+    V = _f64(V)
+    m, n = V.shape
+    W1 = _np.empty((s1, n), dtype=_np.float64)
+    _check(_load().orc_countsketch_rows(_p(V), m, n, n, s1, _U64(seed), _I64(row0), _p(W1)))
+    return W1
+
+
+def cs_hash_at(seed: int, row0: int, m: int, s1: int):
+    """CountSketch buckets and signs of global rows row0 .. row0 + m - 1."""
+    b = _np.empty(m, dtype=_np.int32)
+    s = _np.empty(m, dtype=_np.int8)
+    _load().orc_cs_hash_at(_U64(seed), _I64(row0), m, s1,
+                           b.ctypes.data_as(_ct.POINTER(_ct.c_int32)),
+                           s.ctypes.data_as(_ct.POINTER(_ct.c_int8)))
+    return b, s
 
 
 def gemm(A, B):

@@ -31,6 +31,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+void orc_cs_hash_at(uint64_t seed, int64_t row0, int64_t m, int64_t s1, int32_t *bucket,
+                    int8_t *sign);
+int orc_countsketch_rows(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
+                         uint64_t seed, int64_t row0, double *W1);
+
 #define ORC_OK 0
 #define ORC_NOT_SPD (-2)
 #define ORC_RANK (-3)
@@ -53,8 +58,15 @@ uint64_t orc_splitmix64(uint64_t x) {
  * row and sign are uniform): x = splitmix64(seed XOR splitmix64(i)); row (bucket) =
  * floor(hi32(x) * s1 / 2^32); sign = -1 if the low bit of x is set, else +1. */
 void orc_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign) {
+  orc_cs_hash_at(seed, 0, m, s1, bucket, sign);
+}
+
+/* The same columns row0 .. row0 + m - 1 of S1: a row block V_k of a matrix split by rows
+ * (Sec. 4.1, the distributed sketch) is sketched with the S1 columns of its global rows. */
+void orc_cs_hash_at(uint64_t seed, int64_t row0, int64_t m, int64_t s1, int32_t *bucket,
+                    int8_t *sign) {
   for (int64_t i = 0; i < m; ++i) {
-    uint64_t x = orc_splitmix64(seed ^ orc_splitmix64((uint64_t)i));
+    uint64_t x = orc_splitmix64(seed ^ orc_splitmix64((uint64_t)(row0 + i)));
     bucket[i] = (int32_t)(((x >> 32) * (uint64_t)s1) >> 32);
     sign[i] = (x & 1ULL) ? (int8_t)-1 : (int8_t)1;
   }
@@ -112,10 +124,17 @@ void orc_gauss_sketch(uint64_t seed, int64_t s2, int64_t s1, double *S2) {
  * row bucket(i) of W1, rows taken in ascending i. */
 int orc_countsketch(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
                     uint64_t seed, double *W1) {
+  return orc_countsketch_rows(V, m, n, ldv, s1, seed, 0, W1);
+}
+
+/* W1_k = S1_k V_k for a row block whose first row is global row row0 (Sec. 4.1): the S1
+ * columns are those of the global rows, so that S1 V = sum_k S1_k V_k. */
+int orc_countsketch_rows(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
+                         uint64_t seed, int64_t row0, double *W1) {
   int32_t *b = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
   int8_t *sg = (int8_t *)malloc((size_t)(m > 0 ? m : 1));
   if (!b || !sg) { free(b); free(sg); return ORC_NOMEM; }
-  orc_cs_hash(seed, m, s1, b, sg);
+  orc_cs_hash_at(seed, row0, m, s1, b, sg);
   memset(W1, 0, sizeof(double) * (size_t)(s1 * n));
   for (int64_t i = 0; i < m; ++i) {
     double s = (double)sg[i];

@@ -13,6 +13,7 @@ import os as _os
 
 __all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_sketch",
            "randqr_factor", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
+           "randqr_shard_sketch", "randqr_sketch_r", "randqr_shard_gram", "randqr_shard_finish",
            "default_sketch_sizes", "library_path", "FP64", "F32X2"]
 
 FP64, F32X2 = 0, 1
@@ -70,6 +71,11 @@ def _load():
                           _ct.POINTER(Info), vp],
         "randqr_cholqr2": [vp, vp, i64, i64, i64, vp, i64, vp, i64, _ct.POINTER(Info), vp],
         "randqr_shifted_cholqr3": [vp, vp, i64, i64, i64, vp, i64, vp, i64, _ct.POINTER(Info), vp],
+        "randqr_shard_sketch": [vp, vp, i64, i64, i64, i64, i64, i64, u64, vp, vp, vp],
+        "randqr_sketch_r": [vp, vp, i64, i64, vp, i64, _ct.POINTER(Info), vp],
+        "randqr_shard_gram": [vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp],
+        "randqr_shard_finish": [vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64,
+                                _ct.POINTER(Info), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -300,6 +306,74 @@ def randqr_cholqr2(V, Q=None, R=None, ctx=None, stream=None, sync=True):
 def randqr_shifted_cholqr3(V, Q=None, R=None, ctx=None, stream=None, sync=True):
     """Shifted CholeskyQR3: returns (Q, R, info)."""
     return _baseline(_load().randqr_shifted_cholqr3, V, Q, R, ctx, stream, sync)
+
+
+# ---------------------------------------------------------------------------------------
+# Row-sharded rand_cholQR (Sec. 4.1): the stages between the two cross-shard sums.
+# ---------------------------------------------------------------------------------------
+def randqr_shard_sketch(V, row0, s1, s2, seed=0, S2=None, ctx=None, stream=None):
+    """Ws_k = S2 S1_k V_k (s2 x n) of a row block whose first row is global row ``row0``."""
+    import torch
+    ldv = _check_mat(V, "V")
+    m, n = V.shape
+    Ws = torch.empty((s2, n), dtype=torch.float64, device=V.device)
+    if S2 is not None:
+        _check_mat(S2, "S2")
+    c = _ctx(ctx, V)
+    c._check(_load().randqr_shard_sketch(c.handle, _ptr(V), m, n, ldv, int(row0), s1, s2, seed,
+                                         _ptr(S2), _ptr(Ws), _stream(stream)))
+    return Ws
+
+
+def randqr_sketch_r(Ws, Rs=None, ctx=None, stream=None, sync=True):
+    """R_s (n x n, dense upper) from the summed sketch Ws: returns (Rs, info)."""
+    import torch
+    _check_mat(Ws, "Ws")
+    s2, n = Ws.shape
+    if Rs is None:
+        Rs = torch.empty((n, n), dtype=torch.float64, device=Ws.device)
+    ldr = _check_mat(Rs, "Rs")
+    c = _ctx(ctx, Ws)
+    info = Info() if sync else None
+    st = _load().randqr_sketch_r(c.handle, _ptr(Ws), s2, n, _ptr(Rs), ldr,
+                                 _ct.byref(info) if sync else None, _stream(stream))
+    c._check(st, info)
+    return Rs, info
+
+
+def randqr_shard_gram(V, Rs, Q=None, G=None, ctx=None, stream=None):
+    """W_k = V_k R_s^{-1} (into Q; Q may be V) and G_k = W_k^T W_k: returns (Q, G)."""
+    import torch
+    ldv = _check_mat(V, "V")
+    ldrs = _check_mat(Rs, "Rs")
+    m, n = V.shape
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, device=V.device)
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.float64, device=V.device)
+    ldq, ldg = _check_mat(Q, "Q"), _check_mat(G, "G")
+    c = _ctx(ctx, V)
+    c._check(_load().randqr_shard_gram(c.handle, _ptr(V), m, n, ldv, _ptr(Rs), ldrs, _ptr(Q), ldq,
+                                       _ptr(G), ldg, _stream(stream)))
+    return Q, G
+
+
+def randqr_shard_finish(Q, G, Rs, R=None, ctx=None, stream=None, sync=True):
+    """R_c = chol(G), Q_k = W_k R_c^{-1} in place, R = R_c R_s: returns (Q, R, info)."""
+    import torch
+    ldq = _check_mat(Q, "Q")
+    ldg, ldrs = _check_mat(G, "G"), _check_mat(Rs, "Rs")
+    m, n = Q.shape
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, device=Q.device)
+    ldr = _check_mat(R, "R")
+    c = _ctx(ctx, Q)
+    info = Info() if sync else None
+    st = _load().randqr_shard_finish(c.handle, _ptr(Q), m, n, ldq, _ptr(G), ldg, _ptr(Rs), ldrs,
+                                     _ptr(R), ldr, _ct.byref(info) if sync else None,
+                                     _stream(stream))
+    c._check(st, info)
+    return Q, R, info
 
 
 def get_status(ctx, stream=None):

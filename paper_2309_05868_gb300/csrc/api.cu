@@ -146,10 +146,11 @@ size_t span_bytes(int64_t rows, int64_t cols, int64_t ld) {
 }
 
 // Common checks of the factorization entry points.
+// A row shard (Sec. 4.1) may hold fewer rows than columns: `shard` relaxes m >= n to m >= 1.
 bool bad_factor_args(const double *V, int64_t m, int64_t n, int64_t ldv, const double *Q,
-                     int64_t ldq, const double *R, int64_t ldr) {
+                     int64_t ldq, const double *R, int64_t ldr, bool shard = false) {
   if (!V || !Q || !R) return true;
-  if (n < 1 || n > kMaxN || m < n || ldv < n || ldq < n || ldr < n) return true;
+  if (n < 1 || n > kMaxN || m < (shard ? 1 : n) || ldv < n || ldq < n || ldr < n) return true;
   if ((const void *)Q != (const void *)V &&
       ranges_overlap(V, span_bytes(m, n, ldv), Q, span_bytes(m, n, ldq)))
     return true;
@@ -177,7 +178,7 @@ randqr_status finish_call(randqr_ctx *ctx, cudaStream_t s, randqr_info *info) {
 randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                               int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                               const double *S2, const Workspace &w, cudaStream_t s,
-                              bool do_hhqr) {
+                              bool do_hhqr, int64_t row0 = 0) {
   const double *S2p = S2;
   if (!S2p) {
     randqr_status st = ensure_s2(ctx, seed + 1, s1, s2, s, &S2p);
@@ -186,7 +187,7 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
   RQ_CUDA(cudaMemsetAsync(w.W1, 0, sizeof(double) * (size_t)(s1 * n), s));
   RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
   RQ_CUDA(timed(ctx, s, rq::K_CS_SCATTER, [&] {
-    return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, w.W1, ctx->num_sms, ctx->status_dev, s);
+    return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, row0, w.W1, ctx->num_sms, ctx->status_dev, s);
   }));
   RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
     return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
@@ -566,6 +567,99 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt2, nullptr, R, ldr, 3, RANDQR_FP64,
                         w, s, /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
+  return finish_call(ctx, s, info);
+}
+
+// ---- Row-sharded rand_cholQR (Sec. 4.1): the stages between the two reductions ----------
+
+randqr_status randqr_shard_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n, int64_t ldv,
+                                  int64_t row0, int64_t s1, int64_t s2, uint64_t seed, const double *S2,
+                                  double *Ws, void *stream) {
+  if (!ctx || !V || !Ws || n < 1 || n > kMaxN || m < 1 || ldv < n || row0 < 0 ||
+      bad_sketch_sizes(n, s1, s2))
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
+  if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, false, row0)) != RANDQR_OK)
+    return st;
+  RQ_CUDA(cudaMemcpyAsync(Ws, w.Ws, sizeof(double) * (size_t)(s2 * n), cudaMemcpyDeviceToDevice, s));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_sketch_r(randqr_ctx *ctx, const double *Ws, int64_t s2, int64_t n, double *Rs,
+                              int64_t ldr, randqr_info *info, void *stream) {
+  if (!ctx || !Ws || !Rs || n < 1 || n > kMaxN || s2 < n || s2 > ((int64_t)1 << 20) || ldr < n)
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, s2, s2, &w)) != RANDQR_OK) return st;
+  RQ_CUDA(cudaMemcpyAsync(w.Ws, Ws, sizeof(double) * (size_t)(s2 * n), cudaMemcpyDeviceToDevice, s));
+  RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack(w.Rs, n, Rs, ldr, ctx->status_dev, s); }));
+  return finish_call(ctx, s, info);
+}
+
+randqr_status randqr_shard_gram(randqr_ctx *ctx, const double *V, int64_t m, int64_t n, int64_t ldv,
+                                const double *Rs, int64_t ldrs, double *Q, int64_t ldq, double *G,
+                                int64_t ldg, void *stream) {
+  if (!ctx || !Rs || !G || ldrs < n || ldg < n || bad_factor_args(V, m, n, ldv, Q, ldq, G, ldg, true))
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
+  RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_pack_upper(Rs, ldrs, n, w.Rs, ctx->status_dev, s); }));
+  // W_k = V_k R_s^{-1} into Q (as in randqr_factor), then G_k = W_k^T W_k
+  if (use_tc_solve(ctx, n)) {
+    RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
+    RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+      return rq::launch_trsm_oz(V, false, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+    }));
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
+      return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
+  RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+  if (ctx->use_tc && rq::gram_oz_supported(n)) {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] { return launch_gram_tc(ctx, Q, false, ldq, m, n, w.G, s); }));
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+      return rq::launch_gram(Q, ldq, m, n, w.G, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
+  RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack_sym(w.G, n, G, ldg, ctx->status_dev, s); }));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_shard_finish(randqr_ctx *ctx, double *Q, int64_t m, int64_t n, int64_t ldq,
+                                  const double *G, int64_t ldg, const double *Rs, int64_t ldrs, double *R,
+                                  int64_t ldr, randqr_info *info, void *stream) {
+  if (!ctx || !G || !Rs || ldg < n || ldrs < n || bad_factor_args(Q, m, n, ldq, Q, ldq, R, ldr, true))
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  randqr_status st = begin_call(ctx, s);
+  if (st != RANDQR_OK) return st;
+  Workspace w;
+  if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
+  RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_pack_upper(Rs, ldrs, n, w.Rs, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_pack_upper(G, ldg, n, w.G, ctx->status_dev, s); }));
+  RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
+    return rq::launch_potrf(w.G, n, 0.0, w.Rc, w.Rs, nullptr, R, ldr, 1, ctx->status_dev, s);
+  }));
+  if (use_tc_solve(ctx, n)) {
+    if ((st = solve_by_inverse_tc(ctx, Q, false, ldq, Q, ldq, m, n, w, s)) != RANDQR_OK) return st;
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
+      return rq::launch_trsm(Q, ldq, Q, ldq, m, n, w.Rc, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
   return finish_call(ctx, s, info);
 }
 

@@ -145,8 +145,9 @@ namespace rq {
 cudaError_t launch_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign,
                            cudaStream_t s);
 cudaError_t launch_gauss_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cudaStream_t s);
+// W1 += S1 V for the rows row0 .. row0 + m - 1 of a larger matrix (the hash takes the global index)
 cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
-                              uint64_t seed, double *W1, int num_sms, const DevStatus *st,
+                              uint64_t seed, int64_t row0, double *W1, int num_sms, const DevStatus *st,
                               cudaStream_t s);
 cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, int64_t s1,
                                int64_t n, double *Ws, int num_sms, const DevStatus *st,
@@ -159,6 +160,11 @@ cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, dou
 cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,
                          const double *Rprev_packed, double *Rout_packed, double *Rout,
                          int64_t ldr, int32_t stage, DevStatus *st, cudaStream_t s);
+// dense upper triangle (row-major, ld) -> packed; packed -> dense with zeros (or mirrored) below
+cudaError_t launch_pack_upper(const double *R, int64_t ldr, int64_t n, double *Rpacked, const DevStatus *st,
+                              cudaStream_t s);
+cudaError_t launch_unpack_sym(const double *Rpacked, int64_t n, double *R, int64_t ldr, const DevStatus *st,
+                              cudaStream_t s);
 cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t ldr,
                           const DevStatus *st, cudaStream_t s);
 cudaError_t launch_trsm(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m,

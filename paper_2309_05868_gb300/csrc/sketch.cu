@@ -66,7 +66,7 @@ cudaError_t launch_gauss_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, 
 template <int CPL>  // columns per lane: n <= 32 * CPL
 __global__ void __launch_bounds__(256) k_cs_scatter(const double *__restrict__ V, int64_t m, int n,
                                                     int64_t ldv, uint32_t s1, uint64_t seed,
-                                                    double *__restrict__ W1,
+                                                    int64_t row0, double *__restrict__ W1,
                                                     const DevStatus *st) {
   if (status_failed(st)) return;
   constexpr int RG = 4;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_cs_scatter(const double *__restrict__ V
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < m; base += nwarps * 32) {
     const int64_t mine = base + lane;
-    const uint32_t bs = (mine < m) ? cs_bucket_sign(seed, (uint64_t)mine, s1) : 0u;
+    const uint32_t bs = (mine < m) ? cs_bucket_sign(seed, (uint64_t)(row0 + mine), s1) : 0u;
     const int rows = (int)imin64(32, m - base);
     for (int r0 = 0; r0 < rows; r0 += RG) {
       double v[RG][CPL];
@@ -105,15 +105,15 @@ __global__ void __launch_bounds__(256) k_cs_scatter(const double *__restrict__ V
 }
 
 cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
-                              uint64_t seed, double *W1, int num_sms, const DevStatus *st,
+                              uint64_t seed, int64_t row0, double *W1, int num_sms, const DevStatus *st,
                               cudaStream_t s) {
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 256), (int64_t)num_sms * 8));
   if (n <= 32)
-    k_cs_scatter<1><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, W1, st);
+    k_cs_scatter<1><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
   else if (n <= 64)
-    k_cs_scatter<2><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, W1, st);
+    k_cs_scatter<2><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
   else
-    k_cs_scatter<4><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, W1, st);
+    k_cs_scatter<4><<<blocks, 256, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
   return cudaGetLastError();
 }
 

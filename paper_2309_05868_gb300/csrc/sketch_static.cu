@@ -77,7 +77,7 @@ extern "C" randqr_status randqr_sketch_static(const double *V, int64_t m, int64_
   if (cudaMemsetAsync(slot.status, 0, sizeof(rq::DevStatus), s) != cudaSuccess ||
       cudaMemsetAsync(slot.w1, 0, sizeof(double) * (size_t)(s1 * n), s) != cudaSuccess ||
       cudaMemsetAsync(Ws, 0, sizeof(double) * (size_t)(s2 * n), s) != cudaSuccess ||
-      rq::launch_cs_scatter(V, m, n, ldv, s1, seed, slot.w1, slot.num_sms, slot.status, s) !=
+      rq::launch_cs_scatter(V, m, n, ldv, s1, seed, 0, slot.w1, slot.num_sms, slot.status, s) !=
           cudaSuccess ||
       rq::launch_sketch_gemm(S2, slot.w1, s2, s1, n, Ws, slot.num_sms, slot.status, s) !=
           cudaSuccess) {

@@ -380,6 +380,34 @@ __global__ void k_unpack(const double *Rp, int n, double *R, int64_t ldr, const 
   }
 }
 
+__global__ void k_pack_upper(const double *R, int64_t ldr, int n, double *Rp, const DevStatus *st) {
+  if (status_failed(st)) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e % n;
+    if (j >= i) Rp[tri_idx(i, j)] = R[(int64_t)i * ldr + j];
+  }
+}
+
+__global__ void k_unpack_sym(const double *Rp, int n, double *R, int64_t ldr, const DevStatus *st) {
+  if (status_failed(st)) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e % n;
+    R[(int64_t)i * ldr + j] = Rp[j >= i ? tri_idx(i, j) : tri_idx(j, i)];
+  }
+}
+
+cudaError_t launch_pack_upper(const double *R, int64_t ldr, int64_t n, double *Rpacked, const DevStatus *st,
+                              cudaStream_t s) {
+  k_pack_upper<<<(unsigned)ceil_div(n * n, 256), 256, 0, s>>>(R, ldr, (int)n, Rpacked, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_sym(const double *Rpacked, int64_t n, double *R, int64_t ldr, const DevStatus *st,
+                              cudaStream_t s) {
+  k_unpack_sym<<<(unsigned)ceil_div(n * n, 256), 256, 0, s>>>(Rpacked, (int)n, R, ldr, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t ldr,
                           const DevStatus *st, cudaStream_t s) {
   k_unpack<<<(unsigned)ceil_div(n * n, 256), 256, 0, s>>>(Rpacked, (int)n, R, ldr, st);

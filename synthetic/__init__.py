@@ -15,7 +15,7 @@ import math
 
 import numpy as np
 
-__all__ = ["sigmas", "make_v", "make_v_torch", "integer_matrix", "default_sketch_sizes",
+__all__ = ["sigmas", "make_v", "make_v_torch", "make_v_block_torch", "integer_matrix", "default_sketch_sizes",
            "paper_multisketch_sizes", "rng"]
 
 
@@ -54,6 +54,27 @@ def make_v_torch(m: int, n: int, kappa: float, seed: int = 0, device="cuda"):
     H = torch.randn((n, n), generator=g, device=device, dtype=torch.float64)
     W, _ = torch.linalg.qr(H)
     s = torch.as_tensor(sigmas(n, kappa), device=device, dtype=torch.float64)
+    U.mul_(s)
+    return (U @ W.T).contiguous()
+
+
+def make_v_block_torch(m: int, n: int, kappa: float, shard: int, shards: int, seed: int = 0,
+                       device="cuda"):
+    """Rows [shard m, (shard + 1) m) of an (shards m) x n matrix V = U diag(sigma) W^T with
+    kappa(V) = kappa, drawn without the other blocks: U = [U_0; ...; U_{P-1}] / sqrt(P) with
+    each U_k the orthonormal factor of its own seeded N(0, 1) block (so U^T U = I), and W
+    common to all blocks.  With shards = 1 this is another draw of the same recipe."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + 7919 * (shard + 1))
+    G = torch.randn((m, n), generator=g, device=device, dtype=torch.float64)
+    U, _ = torch.linalg.qr(G)
+    del G
+    gw = torch.Generator(device=device)
+    gw.manual_seed(int(seed) * 1000003 + 5)
+    H = torch.randn((n, n), generator=gw, device=device, dtype=torch.float64)
+    W, _ = torch.linalg.qr(H)
+    s = torch.as_tensor(sigmas(n, kappa) / math.sqrt(shards), device=device, dtype=torch.float64)
     U.mul_(s)
     return (U @ W.T).contiguous()
 

@@ -119,6 +119,29 @@ def test_countsketch_vs_explicit_matrix_float():
     assert (np.abs(W1 - ref) <= tol).all()
 
 
+def test_cs_hash_at_is_a_window_of_the_global_hash():
+    # Sec. 4.1: a row block is sketched with the S1 columns of its global rows.
+    b, s = oracle.cs_hash(5, 1000, 313)
+    for row0, m in ((0, 10), (1, 999), (517, 200), (999, 1)):
+        bk, sk = oracle.cs_hash_at(5, row0, m, 313)
+        np.testing.assert_array_equal(bk, b[row0:row0 + m])
+        np.testing.assert_array_equal(sk, s[row0:row0 + m])
+
+
+def test_countsketch_rows_blocks_sum_to_the_global_sketch():
+    m, n, s1 = 2500, 6, 41
+    V = synthetic.integer_matrix(m, n, seed=3)
+    b, s = oracle.cs_hash(11, m, s1)
+    S1 = _dense_s1(b, s, s1)
+    cuts = [0, 1, 700, 701, 2500]
+    total = np.zeros((s1, n))
+    for r0, r1 in zip(cuts[:-1], cuts[1:]):
+        Wk = oracle.countsketch_rows(V[r0:r1], s1, 11, r0)
+        np.testing.assert_array_equal(Wk, S1[:, r0:r1] @ V[r0:r1])
+        total += Wk
+    np.testing.assert_array_equal(total, S1 @ V)
+
+
 def test_gemm_vs_numpy():
     A = synthetic.rng(3).standard_normal((33, 129))
     B = synthetic.rng(4).standard_normal((129, 17))
