@@ -203,12 +203,12 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
 // Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores: only where R_c is well
 // conditioned by construction (rand_cholQR's solves, the last pass of CholeskyQR2 and of
 // shifted CholeskyQR3); R_c^{-1} goes to w.Rt2 (after the Cholesky kernel has read it).
-randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const void *X, bool x_df, int64_t ldx, double *Y,
+randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y,
                                   int64_t ldy, int64_t m, int64_t n, const Workspace &w,
                                   cudaStream_t s) {
   RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz(X, x_df, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+    return rq::launch_trsm_oz(X, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
   }));
   return RANDQR_OK;
 }
@@ -243,7 +243,7 @@ randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double 
                             ctx->status_dev, s);
   }));
   if (well_conditioned && use_tc_solve(ctx, n))
-    return solve_by_inverse_tc(ctx, X, false, ldx, Y, ldy, m, n, w, s);
+    return solve_by_inverse_tc(ctx, X, ldx, Y, ldy, m, n, w, s);
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
     return rq::launch_trsm(X, ldx, Y, ldy, m, n, w.Rc, prec, ctx->num_sms, ctx->status_dev, s);
   }));
@@ -449,11 +449,6 @@ static randqr_status factor_df(randqr_ctx *ctx, const double *V, int64_t m, int6
   RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
     return rq::launch_potrf(w.G, n, 0.0, w.Rc, w.Rs, nullptr, R, ldr, 1, ctx->status_dev, s);
   }));
-  if (use_tc_solve(ctx, n)) {
-    randqr_status st = solve_by_inverse_tc(ctx, Q, true, ldq, Q, ldq, m, n, w, s);
-    if (st != RANDQR_OK) return st;
-    return finish_call(ctx, s, info);
-  }
   RQ_CUDA(timed(ctx, s, rq::K_PACK_DF, [&] { return rq::launch_pack_df(w.Rc, n, w.Rdf, w.rinv, ctx->status_dev, s); }));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_DF, [&] {
     return rq::launch_trsm_df(Q, false, ldq, Q, true, ldq, m, n, w.Rdf, w.rinv, ctx->num_sms,
@@ -482,7 +477,7 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
     // V (R_s^{-1}) into Q, then the Cholesky pass on W in place.
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
     RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-      return rq::launch_trsm_oz(V, false, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+      return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
     }));
     if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
                           /*well_conditioned=*/true)) != RANDQR_OK)
@@ -619,7 +614,7 @@ randqr_status randqr_shard_gram(randqr_ctx *ctx, const double *V, int64_t m, int
   if (use_tc_solve(ctx, n)) {
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
     RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-      return rq::launch_trsm_oz(V, false, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+      return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
     }));
   } else {
     RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
@@ -654,7 +649,7 @@ randqr_status randqr_shard_finish(randqr_ctx *ctx, double *Q, int64_t m, int64_t
     return rq::launch_potrf(w.G, n, 0.0, w.Rc, w.Rs, nullptr, R, ldr, 1, ctx->status_dev, s);
   }));
   if (use_tc_solve(ctx, n)) {
-    if ((st = solve_by_inverse_tc(ctx, Q, false, ldq, Q, ldq, m, n, w, s)) != RANDQR_OK) return st;
+    if ((st = solve_by_inverse_tc(ctx, Q, ldq, Q, ldq, m, n, w, s)) != RANDQR_OK) return st;
   } else {
     RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
       return rq::launch_trsm(Q, ldq, Q, ldq, m, n, w.Rc, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);

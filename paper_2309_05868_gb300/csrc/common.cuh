@@ -187,11 +187,11 @@ cudaError_t launch_gram_df(const float2 *W, int64_t ldw, int64_t m, int64_t n, d
 // X = R^{-1} for packed upper-triangular R (small.cu)
 cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, const DevStatus *st,
                            cudaStream_t s);
-// Q = W X from exact split products on the tensor cores (trsm_tc.cu), n <= 64
+// Y = X B (B upper triangular, packed) from exact split products on the tensor cores
+// (trsm_tc.cu), n <= 64; Y may equal X (same ld)
 bool trsm_oz_supported(int64_t n);
-cudaError_t launch_trsm_oz(const void *W, bool in_df, int64_t ldw, double *Q, int64_t ldq, int64_t m,
-                           int64_t n, const double *Xpacked, int num_sms, DevStatus *st,
-                           cudaStream_t s);
+cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
+                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s);
 // Gram from exact split products on the tensor cores, n <= 64 (gram_split.cu)
 bool gram_split_supported(int64_t n);
 cudaError_t launch_gram_split(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n, double *Gpacked,

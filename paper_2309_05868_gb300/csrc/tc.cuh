@@ -121,6 +121,14 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(addr));
 }
+// 16 tensor-memory lanes x 8 consecutive columns: thread t gets lanes t / 4 and t / 4 + 8 of the
+// 16, columns 2 (t % 4) and 2 (t % 4) + 1: r = {(t/4, 2(t%4)), (t/4, 2(t%4)+1), (t/4+8, 2(t%4)),
+// (t/4+8, 2(t%4)+1)}.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Orders uses of tcgen05.ld destination registers after the tcgen05.wait::ld that completes
@@ -343,6 +351,84 @@ __device__ __forceinline__ double int_times_pow2(long long t, int e) {
   const unsigned long long ex = (unsigned long long)(1023 + 63 - lz + carry + e);
   const unsigned long long bits = (sgn << 63) | (ex << 52) | ((r >> 11) & 0xFFFFFFFFFFFFFULL);
   return t == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+}  // namespace tc
+}  // namespace rq
+
+namespace rq {
+namespace tc {
+
+// ---------------------------------------------------------------------------------------
+// Balanced byte digits (f16 operands) of the triangular products.  An integer X with
+// |X| < 2^54 is written as X = sum_{p=0}^{6} d_p 2^(8p) with d_p in [-128, 127] (the leading
+// digit then lies in [-64, 64]): byte p of X + BIAS8, BIAS8 = sum_p 128 * 2^(8p), is d_p + 128.
+// f16 holds every digit exactly; a product of two digits is at most 2^14 in magnitude, and
+// at most 2^13 when one of them is a leading digit.
+// ---------------------------------------------------------------------------------------
+constexpr int NDIG8 = 7;
+constexpr unsigned long long BIAS8 = 0x80808080808080ULL;
+
+// Digit words of two fixed-point values: w[p] = f16(d_p(xa)) | f16(d_p(xb)) << 16.  One byte
+// permute puts byte p of both values in the low bytes of the two halves; f16(1024 + y) is
+// 0x6400 | y, and subtracting f16(1152) leaves y - 128 exactly.
+__device__ __forceinline__ void digits8_biased(unsigned long long ya, unsigned long long yb, uint32_t (&w)[NDIG8]) {
+  const uint32_t la = (uint32_t)ya, ha = (uint32_t)(ya >> 32);
+  const uint32_t lb = (uint32_t)yb, hb = (uint32_t)(yb >> 32);
+#pragma unroll
+  for (int p = 0; p < NDIG8; ++p) {
+    const uint32_t q = (uint32_t)(p & 3);
+    const uint32_t sel = q | ((q + 4u) << 8);
+    const uint32_t v = p < 4 ? __byte_perm(la, lb, sel) : __byte_perm(ha, hb, sel);
+    w[p] = hsub2_bits((v & 0x00FF00FFu) | 0x64006400u, 0x64806480u);
+  }
+}
+__device__ __forceinline__ void digits8(long long xa, long long xb, uint32_t (&w)[NDIG8]) {
+  digits8_biased((unsigned long long)xa + BIAS8, (unsigned long long)xb + BIAS8, w);
+}
+
+// X + BIAS8 (mod 2^64) for the FP64 value with bit pattern b, X = trunc(|x| 2^(54 - E)) with the
+// sign of x, for |x| < 2^E (what digits8 of fix54(x, E) starts from).  With x = m 2^(ef - 1075)
+// (m the 53-bit significand), X = (2m) >> (1022 + E - ef), a shift of at least 0; zeros and
+// subnormals (ef = 0) shift everything out.  The sign is applied as (v ^ s) - s with s = 0 or -1.
+__device__ __forceinline__ unsigned long long fix54_biased(unsigned long long b, int E) {
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const int ef = (int)((hi >> 20) & 0x7ffu);
+  const int amt = min(1022 + E - ef, 63);
+  const unsigned long long m2 = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 33) | ((unsigned long long)lo << 1);
+  const unsigned long long v = m2 >> amt;
+  const unsigned long long sgn = (unsigned long long)((long long)b >> 63);
+  return (v ^ sgn) + (BIAS8 - sgn);
+}
+
+// T / 2^12 from eight region accumulators of byte-digit products, T = sum_g 2^(8 (7 - g)) D_g,
+// each D_g an exact FP32 integer with |D_g| <= 2^22 for g <= 4 and |D_g| < 2^23 for g >= 5.
+// Regions 0-4 go through the 1.5 * 2^23 offset (bit pattern 0x4B400000 + D_g).  Region 5 is
+// split into an even part, through the 1.5 * 2^24 offset (0x4BC00000 + D_5 / 2), and a
+// remainder in {-1, 0, 1}.  The remainder and regions 6 and 7 are merged by two FP32 fused
+// multiply-adds (|r| < 2^31) and taken at a resolution of 2^9 through the 1.5 * 2^32 offset:
+// an error of at most 2^8 units of region 7, far below T's last unit.  The patterns are summed
+// with 32 x 32 -> 64-bit multiply-adds and the offsets removed by two constants.
+__device__ __forceinline__ long long recombine_b8(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
+                                                  uint32_t d5, uint32_t d6, uint32_t d7) {
+  constexpr unsigned long long OFF_H = 0x4B400000ULL * ((1ULL << 24) + (1ULL << 16) + (1ULL << 8) + 1ULL);
+  constexpr unsigned long long OFF_L = 0x4B400000ULL * (1ULL << 24) + 0x4BC00000ULL * (1ULL << 17) +
+                                       0x4FC00000ULL * (1ULL << 9);
+  const float M24 = 25165824.0f, M32 = 6442450944.0f;
+  const float v5 = __uint_as_float(d5);
+  const float c5 = __fadd_rn(v5, M24);
+  const float lo = __fsub_rn(v5, __fsub_rn(c5, M24));
+  const float r = __fmaf_rn(lo, 65536.0f, __fmaf_rn(__uint_as_float(d6), 256.0f, __uint_as_float(d7)));
+  const uint32_t q5 = __float_as_uint(c5), qr = __float_as_uint(__fadd_rn(r, M32));
+  unsigned long long h = mad_wide(acc_bits(d0), 1u << 24, 0ULL);
+  h = mad_wide(acc_bits(d1), 1u << 16, h);
+  h = mad_wide(acc_bits(d2), 1u << 8, h);
+  h += acc_bits(d3);
+  unsigned long long l = mad_wide(acc_bits(d4), 1u << 24, 0ULL);
+  l = mad_wide(q5, 1u << 17, l);
+  l = mad_wide(qr, 1u << 9, l);
+  const long long th = (long long)(h - OFF_H), tl = (long long)(l - OFF_L);
+  return (th << 20) + (tl >> 12);
 }
 
 }  // namespace tc

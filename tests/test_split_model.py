@@ -2,8 +2,8 @@
 exact arithmetic, and a small rand_cholQR built on it.
 
 This pins the numerical design of the tensor-core path (products with explicit triangular
-inverses, Algorithm 3's two solves; eight balanced 7-bit digits of a 54-bit fixed point; slice
-pairs s + t <= 7 kept exactly, s + t = 8 folded in at weight 2^-7; integer recombination) on
+inverses, Algorithm 3's two solves; seven balanced byte digits of a 54-bit fixed point; slice
+pairs s + t <= 7 kept exactly; integer recombination) on
 the CPU.  It is a model written from that description, independent of the CUDA sources and of
 the oracle; the GPU tests check the kernels themselves against the oracle.
 """
@@ -15,7 +15,8 @@ from scipy.linalg import cholesky, solve_triangular
 
 import synthetic
 
-BIAS = sum(64 << (7 * p) for p in range(8))
+BIAS = sum(128 << (8 * p) for p in range(7))
+M23, M24, M32 = np.float32(1.5 * 2 ** 23), np.float32(1.5 * 2 ** 24), np.float32(1.5 * 2 ** 32)
 
 
 def scale_exp(A, axis):
@@ -33,33 +34,74 @@ def fix54(A, E):
 
 
 def digits(Xi):
-    """Balanced digits d_p in [-64, 63], X = sum_p d_p 2^(7p); returned by slice s = 7 - p."""
+    """Balanced byte digits d_p in [-128, 127], X = sum_p d_p 2^(8p); by slice s = 6 - p.
+    |X| < 2^54 keeps the leading digit within [-64, 64]."""
     Y = Xi + BIAS
     assert Y.min() >= 0 and Y.max() < 2 ** 56
-    return [((Y >> (7 * (7 - s))) & 127) - 64 for s in range(8)]
+    d = [((Y >> (8 * (6 - s))) & 255) - 128 for s in range(7)]
+    assert np.abs(d[0]).max() <= 64
+    return d
+
+
+def _bits(f32):
+    return np.asarray(f32, dtype=np.float32).view(np.uint32).astype(np.int64)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def recombine(D):
+    """T / 2^12 from the eight region accumulators (exact FP32 integers), T = sum_g D_g 2^(8(7-g)),
+    with the kernel's FP32 steps: regions 0-4 through the 1.5 * 2^23 offset (exact for
+    |D| <= 2^22); region 5 split into an even part (1.5 * 2^24 offset) and a remainder in
+    {-1, 0, 1}; the remainder, region 6 and region 7 merged by two FP32 fused multiply-adds
+    (|r| < 2^31) and taken at a resolution of 2^9 (1.5 * 2^32 offset)."""
+    v = [_f32(d) for d in D]
+    for g in range(8):
+        assert np.array_equal(v[g].astype(np.int64), D[g])           # exact in FP32
+    a = [_bits(v[g] + M23) - 0x4B400000 for g in range(5)]
+    for g in range(5):
+        assert np.array_equal(a[g], D[g])
+    c5 = (v[5] + M24).astype(np.float32)
+    q5 = _bits(c5) - 0x4BC00000
+    lo = (v[5] - (c5 - M24).astype(np.float32)).astype(np.float32)
+    assert np.array_equal(2 * q5 + lo.astype(np.int64), D[5])
+    r = _f32(v[6].astype(np.float64) * 256 + v[7].astype(np.float64))        # fmaf
+    r = _f32(lo.astype(np.float64) * 65536 + r.astype(np.float64))             # fmaf
+    assert np.abs(r).max() < 2 ** 31
+    qr = _bits((r + M32).astype(np.float32)) - 0x4FC00000
+    h = (a[0] << 24) + (a[1] << 16) + (a[2] << 8) + a[3]
+    l = (a[4] << 24) + (q5 << 17) + (qr << 9)
+    assert np.abs(h).max() < 2 ** 43 and np.abs(l).max() < 2 ** 62
+    return (h << 20) + (l >> 12)
 
 
 def split_product(X, B):
-    """Y = X B the way the solve kernel forms it (row scales of X, column scales of B)."""
-    E, F = scale_exp(X, 1), scale_exp(B, 0)
-    dx, db = digits(fix54(X, E)), digits(fix54(B, F))
-    D = []
-    for g in range(9):
-        acc = np.zeros((X.shape[0], B.shape[1]), dtype=np.int64)
-        for s in range(8):
-            t = g - s
-            if 0 <= t < 8:
-                acc += dx[s] @ db[t]
-        assert np.abs(acc).max() <= 2 ** 21
-        D.append(acc)
-    # region 8 summed first in region 7's FP32 accumulator, scaled by 2^-7 (scale-input-d),
-    # then region 7's products added: one FP32 rounding, then the exact integer conversion
-    r7 = (D[7].astype(np.float32) + D[8].astype(np.float32) * np.float32(2.0 ** -7)).astype(np.float32)
-    D7 = np.rint(r7.astype(np.float64)).astype(np.int64)
-    th = (D[0] << 21) + (D[1] << 14) + (D[2] << 7) + D[3]
-    tl = (D[4] << 21) + (D[5] << 14) + (D[6] << 7) + D7
-    t = (th << 25) + (tl >> 3)  # T / 8
-    return np.ldexp(t.astype(np.float64), E + F - 56)
+    """Y = X B the way the solve kernel forms it: row scales of X, column scales of B, byte
+    digits, slice pairs s + t <= 7 in eight regions per column half; half h (columns
+    32h .. 32h + 31) takes the K range j < 32 (h + 1) that an upper-triangular B reaches."""
+    m, n = X.shape
+    assert B.shape == (n, n) and n <= 64
+    Xp = np.zeros((m, 64)); Xp[:, :n] = X
+    Bp = np.zeros((64, 64)); Bp[:n, :n] = B
+    assert np.array_equal(Bp, np.triu(Bp))
+    E, F = scale_exp(Xp, 1), scale_exp(Bp, 0)
+    dx, db = digits(fix54(Xp, E)), digits(fix54(Bp, F))
+    T = np.zeros((m, 64), dtype=np.int64)
+    for h in range(2):
+        kk, jj = slice(32 * h, 32 * h + 32), slice(0, 32 * (h + 1))
+        D = []
+        for g in range(8):
+            acc = np.zeros((m, 32), dtype=np.int64)
+            for s in range(7):
+                t = g - s
+                if 0 <= t < 7:
+                    acc += dx[s][:, jj] @ db[t][jj, kk]
+            assert np.abs(acc).max() <= (2 ** 22 if g <= 4 else 2 ** 23 - 1)
+            D.append(acc)
+        T[:, kk] = recombine(D)
+    return np.ldexp(T.astype(np.float64), E + F - 56)[:, :n]
 
 
 def test_split_product_error_is_below_the_scale_product():
@@ -79,6 +121,22 @@ def test_split_product_error_is_below_the_scale_product():
             worst = max(worst, float(err))
     assert np.all(Y[3] == 0.0)
     assert worst <= 2.0 ** -50, worst
+
+
+def test_split_product_at_the_digit_extremes():
+    # every digit below the leading one at -128 (products of +2^14) and the leading digit at
+    # -63: the region sums come within a few percent of the bounds the recombination relies on
+    X0 = 63 * 2 ** 48 + sum(128 << (8 * p) for p in range(6))
+    x0 = -np.ldexp(float(X0), -54)
+    assert np.ldexp(float(X0), -54) < 1.0 and int(np.ldexp(-x0, 54)) == X0
+    n = 64
+    X = np.full((3, n), x0)
+    B = np.triu(np.full((n, n), x0))
+    Y = split_product(X, B)
+    exact = [sum(Fraction(x0) * Fraction(x0) for _ in range(k + 1)) for k in range(n)]
+    # the final rounding to FP64 of results up to 64 x0^2 dominates
+    for k in range(n):
+        assert abs(Fraction(float(Y[0, k])) - exact[k]) <= Fraction(2) ** -52 * abs(exact[k])
 
 
 def test_split_product_is_exact_on_short_integers():
