@@ -314,7 +314,10 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
             const int ra = r0 + 2 * u, rb = ra + 1;
             const unsigned long long ba = (cj && ra < cnt) ? *(const unsigned long long *)(src + ra * 512) : 0ULL;
             const unsigned long long bb = (cj && rb < cnt) ? *(const unsigned long long *)(src + rb * 512) : 0ULL;
-            digits2(g_fix<IN_DF>(ba, E), g_fix<IN_DF>(bb, E), w[u]);
+            if (IN_DF)
+              digits2(g_fix<IN_DF>(ba, E), g_fix<IN_DF>(bb, E), w[u]);
+            else
+              digits2_biased(fix54_biased<DIG_BIAS>(ba, E), fix54_biased<DIG_BIAS>(bb, E), w[u]);
           }
           const int kg = (GS_SUB * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the tile
 #pragma unroll

@@ -273,10 +273,9 @@ __device__ __forceinline__ uint32_t hsub2_bits(uint32_t a, uint32_t b) {
   return d;
 }
 
-// Digit words of two fixed-point values: w[p] = f16(d_p(xa)) | f16(d_p(xb)) << 16.
-__device__ __forceinline__ void digits2(long long xa, long long xb, uint32_t (&w)[NDIG]) {
-  const unsigned long long ya = (unsigned long long)xa + DIG_BIAS;
-  const unsigned long long yb = (unsigned long long)xb + DIG_BIAS;
+// Digit words of two fixed-point values already offset by DIG_BIAS (ya = xa + DIG_BIAS):
+// w[p] = f16(d_p(xa)) | f16(d_p(xb)) << 16.
+__device__ __forceinline__ void digits2_biased(unsigned long long ya, unsigned long long yb, uint32_t (&w)[NDIG]) {
   const uint32_t la = (uint32_t)ya, ha = (uint32_t)(ya >> 32);
   const uint32_t lb = (uint32_t)yb, hb = (uint32_t)(yb >> 32);
   uint32_t win[4];  // window q: bits 14q .. 14q + 13 of each value, one per 16-bit half
@@ -290,6 +289,9 @@ __device__ __forceinline__ void digits2(long long xa, long long xb, uint32_t (&w
     w[2 * q] = hsub2_bits((win[q] & 0x007F007Fu) | 0x64006400u, 0x64406440u);
     w[2 * q + 1] = hsub2_bits(((win[q] >> 7) & 0x007F007Fu) | 0x64006400u, 0x64406440u);
   }
+}
+__device__ __forceinline__ void digits2(long long xa, long long xb, uint32_t (&w)[NDIG]) {
+  digits2_biased((unsigned long long)xa + DIG_BIAS, (unsigned long long)xb + DIG_BIAS, w);
 }
 
 // The integer value of an FP32 accumulator that holds an exact integer of magnitude < 2^22.
@@ -334,7 +336,8 @@ __device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32
 // slots are the scarce resource.
 __device__ __forceinline__ double int_times_pow2_cvt(long long t, int e) {
   const double y = (double)t;
-  return t != 0 ? __hiloint2double(__double2hiint(y) + (e << 20), __double2loint(y)) : 0.0;
+  const int hi = __double2hiint(y);  // nonzero exactly when t is
+  return __hiloint2double(hi + (hi != 0 ? (e << 20) : 0), __double2loint(y));
 }
 
 // (double) t * 2^e, rounded to nearest (ties away from zero), for |t| < 2^63 and a result in
@@ -387,10 +390,12 @@ __device__ __forceinline__ void digits8(long long xa, long long xb, uint32_t (&w
   digits8_biased((unsigned long long)xa + BIAS8, (unsigned long long)xb + BIAS8, w);
 }
 
-// X + BIAS8 (mod 2^64) for the FP64 value with bit pattern b, X = trunc(|x| 2^(54 - E)) with the
-// sign of x, for |x| < 2^E (what digits8 of fix54(x, E) starts from).  With x = m 2^(ef - 1075)
+// X + BIAS (mod 2^64) for the FP64 value with bit pattern b, X = trunc(|x| 2^(54 - E)) with the
+// sign of x, for |x| < 2^E (what digits8 of fix54(x, E) starts from, with BIAS = BIAS8, and
+// digits2 with BIAS = DIG_BIAS).  With x = m 2^(ef - 1075)
 // (m the 53-bit significand), X = (2m) >> (1022 + E - ef), a shift of at least 0; zeros and
 // subnormals (ef = 0) shift everything out.  The sign is applied as (v ^ s) - s with s = 0 or -1.
+template <unsigned long long BIAS = BIAS8>
 __device__ __forceinline__ unsigned long long fix54_biased(unsigned long long b, int E) {
   const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
   const int ef = (int)((hi >> 20) & 0x7ffu);
@@ -398,7 +403,7 @@ __device__ __forceinline__ unsigned long long fix54_biased(unsigned long long b,
   const unsigned long long m2 = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 33) | ((unsigned long long)lo << 1);
   const unsigned long long v = m2 >> amt;
   const unsigned long long sgn = (unsigned long long)((long long)b >> 63);
-  return (v ^ sgn) + (BIAS8 - sgn);
+  return (v ^ sgn) + (BIAS - sgn);
 }
 
 // T / 2^12 from eight region accumulators of byte-digit products, T = sum_g 2^(8 (7 - g)) D_g,
@@ -420,15 +425,15 @@ __device__ __forceinline__ long long recombine_b8(uint32_t d0, uint32_t d1, uint
   const float lo = __fsub_rn(v5, __fsub_rn(c5, M24));
   const float r = __fmaf_rn(lo, 65536.0f, __fmaf_rn(__uint_as_float(d6), 256.0f, __uint_as_float(d7)));
   const uint32_t q5 = __float_as_uint(c5), qr = __float_as_uint(__fadd_rn(r, M32));
-  unsigned long long h = mad_wide(acc_bits(d0), 1u << 24, 0ULL);
+  // the offsets ride in the chains' initial values (arithmetic mod 2^64)
+  unsigned long long h = mad_wide(acc_bits(d0), 1u << 24, 0ULL - OFF_H);
   h = mad_wide(acc_bits(d1), 1u << 16, h);
   h = mad_wide(acc_bits(d2), 1u << 8, h);
   h += acc_bits(d3);
-  unsigned long long l = mad_wide(acc_bits(d4), 1u << 24, 0ULL);
+  unsigned long long l = mad_wide(acc_bits(d4), 1u << 24, 0ULL - OFF_L);
   l = mad_wide(q5, 1u << 17, l);
   l = mad_wide(qr, 1u << 9, l);
-  const long long th = (long long)(h - OFF_H), tl = (long long)(l - OFF_L);
-  return (th << 20) + (tl >> 12);
+  return ((long long)h << 20) + ((long long)l >> 12);
 }
 
 }  // namespace tc
