@@ -407,33 +407,34 @@ __device__ __forceinline__ unsigned long long fix54_biased(unsigned long long b,
 }
 
 // T / 2^12 from eight region accumulators of byte-digit products, T = sum_g 2^(8 (7 - g)) D_g,
-// each D_g an exact FP32 integer with |D_g| <= 2^22 for g <= 4 and |D_g| < 2^23 for g >= 5.
-// Regions 0-4 go through the 1.5 * 2^23 offset (bit pattern 0x4B400000 + D_g).  Region 5 is
-// split into an even part, through the 1.5 * 2^24 offset (0x4BC00000 + D_5 / 2), and a
-// remainder in {-1, 0, 1}.  The remainder and regions 6 and 7 are merged by two FP32 fused
-// multiply-adds (|r| < 2^31) and taken at a resolution of 2^9 through the 1.5 * 2^32 offset:
-// an error of at most 2^8 units of region 7, far below T's last unit.  The patterns are summed
-// with 32 x 32 -> 64-bit multiply-adds and the offsets removed by two constants.
+// each D_g an exact FP32 integer with |D_g| <= 2^22 for g <= 4 and |D_g| < 2^23 for g >= 5, and
+// |T| < 2^74.  Regions 0-4 go through the 1.5 * 2^23 offset (bit pattern 0x4B400000 + D_g).
+// Region 5 is split into an even part, through the 1.5 * 2^24 offset (0x4BC00000 + D_5 / 2),
+// and a remainder in {-1, 0, 1}.  The remainder and regions 6 and 7 are merged by two FP32
+// fused multiply-adds (|r| < 2^31) and taken at a resolution of 2^12 through the 1.5 * 2^35
+// offset: an error below 2^11 units of region 7, far below the result's last unit.  The bit
+// patterns are then summed with integer multiply-adds modulo 2^64 (the offsets cancel
+// through one constant per word): regions 0 and 1 land in the high word (32-bit products),
+// the rest in a 64-bit chain, so that combining them costs one add.
 __device__ __forceinline__ long long recombine_b8(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
                                                   uint32_t d5, uint32_t d6, uint32_t d7) {
-  constexpr unsigned long long OFF_H = 0x4B400000ULL * ((1ULL << 24) + (1ULL << 16) + (1ULL << 8) + 1ULL);
-  constexpr unsigned long long OFF_L = 0x4B400000ULL * (1ULL << 24) + 0x4BC00000ULL * (1ULL << 17) +
-                                       0x4FC00000ULL * (1ULL << 9);
-  const float M24 = 25165824.0f, M32 = 6442450944.0f;
+  constexpr uint32_t O23 = 0x4B400000u, O24 = 0x4BC00000u, O35 = 0x51400000u;  // 1.5 * 2^23, 2^24, 2^35
+  constexpr uint32_t C_HI = (uint32_t)(O23 * 4096ull + O23 * 16ull);
+  constexpr unsigned long long C_LO = (unsigned long long)O23 * (1ull << 28) + (unsigned long long)O23 * (1ull << 20) +
+                                      (unsigned long long)O23 * (1ull << 12) + (unsigned long long)O24 * 32ull + O35;
+  const float M24 = 25165824.0f, M35 = 51539607552.0f;
   const float v5 = __uint_as_float(d5);
   const float c5 = __fadd_rn(v5, M24);
   const float lo = __fsub_rn(v5, __fsub_rn(c5, M24));
   const float r = __fmaf_rn(lo, 65536.0f, __fmaf_rn(__uint_as_float(d6), 256.0f, __uint_as_float(d7)));
-  const uint32_t q5 = __float_as_uint(c5), qr = __float_as_uint(__fadd_rn(r, M32));
-  // the offsets ride in the chains' initial values (arithmetic mod 2^64)
-  unsigned long long h = mad_wide(acc_bits(d0), 1u << 24, 0ULL - OFF_H);
-  h = mad_wide(acc_bits(d1), 1u << 16, h);
-  h = mad_wide(acc_bits(d2), 1u << 8, h);
-  h += acc_bits(d3);
-  unsigned long long l = mad_wide(acc_bits(d4), 1u << 24, 0ULL - OFF_L);
-  l = mad_wide(q5, 1u << 17, l);
-  l = mad_wide(qr, 1u << 9, l);
-  return ((long long)h << 20) + ((long long)l >> 12);
+  const uint32_t q5 = __float_as_uint(c5), qr = __float_as_uint(__fadd_rn(r, M35));
+  const uint32_t hw = acc_bits(d0) * 4096u + acc_bits(d1) * 16u - C_HI;  // modulo 2^32
+  unsigned long long lw = mad_wide(qr, 1u, 0ULL - C_LO);
+  lw = mad_wide(q5, 32u, lw);
+  lw = mad_wide(acc_bits(d4), 1u << 12, lw);
+  lw = mad_wide(acc_bits(d3), 1u << 20, lw);
+  lw = mad_wide(acc_bits(d2), 1u << 28, lw);
+  return (long long)(lw + ((unsigned long long)hw << 32));
 }
 
 }  // namespace tc

@@ -36,6 +36,8 @@
 // handing tiles over through mbarriers.  B's digit slices are built once per CTA.  A's K-block
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
 // completed.  In place (Y == X) is safe: a tile's rows are read before any are written.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -61,10 +63,11 @@ __host__ __device__ constexpr uint32_t b_block(int h, int c) {
   return h == 0 ? (c == 0 ? 0u : 8u * B_TSLICE) : (15u + (c == 0 ? 0u : 8u + 7u * (uint32_t)(c - 1))) * B_TSLICE;
 }
 constexpr uint32_t B_BYTES = b_block(1, 3) + 7 * B_TSLICE;
-// Staged rows are 528 bytes apart (512 + 16): the slicers' 16-byte reads of eight rows at one
-// K offset then fall into eight different bank groups.
-constexpr uint32_t STAGE_PITCH = 528;
-constexpr uint32_t STAGE_BYTES = TQ_SUB * STAGE_PITCH;
+// A staged 32-row sub-tile is four boxes of 16 columns (4 KB each, 128-byte rows) in the
+// tensor-map copy's 128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r & 7),
+// so the slicers' reads of eight rows at one column fall into eight different bank groups.
+constexpr uint32_t STAGE_BOX = TQ_SUB * 128;
+constexpr uint32_t STAGE_BYTES = 4 * STAGE_BOX;
 constexpr size_t OFF_B = 0;
 constexpr size_t OFF_A = OFF_B + B_BYTES;
 constexpr size_t OFF_STAGE = OFF_A + (size_t)NDIG8 * A_SLICE;
@@ -76,10 +79,24 @@ constexpr int BAR_FULL = 0, BAR_EMPTY = 4, BAR_AFULL = 8, BAR_KFREE = 12, BAR_HD
               BAR_DRAIN = 20, NBARS = 21;
 constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;  // tmem slot, abort flag
 constexpr size_t TQ_SMEM = OFF_MISC + 16;
-static_assert(OFF_A % 1024 == 0 && B_BYTES == 45056, "layout");
+static_assert(OFF_A % 1024 == 0 && OFF_STAGE % 1024 == 0 && B_BYTES == 45056, "layout");
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
-enum LoadMode { LOAD_ROWS = 0, LOAD_PLAIN = 1 };
+enum LoadMode { LOAD_TMA = 0, LOAD_PLAIN = 1 };
+
+// Byte offset of element (row r, column col) of a staged sub-tile.
+__device__ __forceinline__ uint32_t stage_off(int r, int col) {
+  return (uint32_t)(col >> 4) * STAGE_BOX + (uint32_t)r * 128u + ((((uint32_t)col >> 1) & 7u) ^ ((uint32_t)r & 7u)) * 16u +
+         ((uint32_t)col & 1u) * 8u;
+}
+
+// Tensor-map copy of a box (16 columns x 32 rows of FP64) at column x, row y into shared memory.
+__device__ __forceinline__ void tma_load_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
 
 __device__ __forceinline__ void set_abort(volatile int *abort_flag, DevStatus *st) {
   *abort_flag = 1;
@@ -106,9 +123,9 @@ __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uin
 }  // namespace
 
 __global__ void __launch_bounds__(TQ_THREADS, 1)
-    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int n,
-              const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode, bool vec_store,
-              DevStatus *st) {
+    k_trsm_oz(const __grid_constant__ CUtensorMap xmap, const double *__restrict__ X, int64_t ldx, double *Y,
+              int64_t ldy, int64_t m, int n, const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode,
+              bool vec_store, DevStatus *st) {
   if (status_failed(st)) return;
   extern __shared__ __align__(1024) uint8_t tq_smem[];
   uint8_t *Bs = tq_smem + OFF_B;
@@ -201,15 +218,17 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int cnt = sub_rows(i, q);
         uint8_t *dst = stage + (size_t)q * STAGE_BYTES;
         const uint32_t fb = bar(BAR_FULL + q);
-        if (cnt > 0 && load_mode == LOAD_ROWS) {
-          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
-          __syncwarp();
-          for (int r = lane; r < cnt; r += 32)
-            bulk_load(smem_addr(dst + r * STAGE_PITCH), X + (size_t)(r0 + r) * (size_t)ldx, (uint32_t)n * 8u, fb);
+        if (cnt > 0 && load_mode == LOAD_TMA) {
+          // boxes of the n columns (rows past m arrive as zeros)
+          const int nbox = (n + 15) >> 4;
+          if (lane == 0) {
+            mbar_expect_tx(fb, (uint32_t)nbox * STAGE_BOX);
+            for (int b = 0; b < nbox; ++b) tma_load_box(smem_addr(dst + b * STAGE_BOX), &xmap, 16 * b, (int)r0, fb);
+          }
         } else {
           for (int e = lane; e < cnt * n; e += 32) {
             const int r = e / n, cc = e - r * n;
-            *(double *)(dst + r * STAGE_PITCH + 8 * cc) = X[(r0 + r) * ldx + cc];
+            *(double *)(dst + stage_off(r, cc)) = X[(r0 + r) * ldx + cc];
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(fb);
@@ -217,6 +236,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         last_i[q] = i;
       }
       if (!ok) break;
+
     }
     // copies still in flight (only after an abort) land before the CTA leaves
     if (lane == 0)
@@ -284,14 +304,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       if (!ok) break;
       const int rr = 8 * sg + r;  // row within the sub-tile
       const bool live = rr < sub_rows(i, q);
-      const uint8_t *src = stage + (size_t)q * STAGE_BYTES + rr * STAGE_PITCH;
+      const uint8_t *src = stage + (size_t)q * STAGE_BYTES;
       int mx = 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int kg = 2 * c + kk;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const ulonglong2 raw = *(const ulonglong2 *)(src + 64 * kg + 16 * u);
+          const ulonglong2 raw = *(const ulonglong2 *)(src + stage_off(rr, 8 * kg + 2 * u));
           const int c0 = 8 * kg + 2 * u;
           e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
           e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
           for (int rg = 0; rg < 2; ++rg)
 #pragma unroll
             for (int hr = 0; hr < 2; ++hr) er[rg][hr] = rowexp[(i % 3) * TQ_ROWS + 32 * quad + 16 * rg + 8 * hr + tr];
-#pragma unroll
+#pragma unroll 1
         for (int rg = 0; rg < 2; ++rg) {  // 16-row group
           uint32_t v[2][8][4];
           const uint32_t ta = tmem + ((uint32_t)(32 * quad + 16 * rg) << 16) + (uint32_t)(256 * h + 16 * cq);
@@ -407,17 +427,50 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once (NULL if the driver does not provide it).
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+}  // namespace
+
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
                            const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s) {
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
-  const bool aligned = ((uintptr_t)X & 15) == 0;
-  const int load_mode = (aligned && (n * 8) % 16 == 0 && (ldx * 8) % 16 == 0) ? LOAD_ROWS : LOAD_PLAIN;
+  // X as a 2-D tensor (n columns, m rows, row pitch 8 ldx bytes) for the box copies; row
+  // coordinates are 32-bit, the base and pitch must be 16-byte multiples
+  alignas(64) CUtensorMap xmap;
+  memset(&xmap, 0, sizeof xmap);
+  int load_mode = LOAD_PLAIN;
+  const EncodeTiledFn enc = encode_tiled();
+  if (enc && ((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && m + TQ_ROWS < ((int64_t)1 << 31)) {
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    const cuuint64_t strides[1] = {(cuuint64_t)ldx * 8};
+    const cuuint32_t box[2] = {16, (cuuint32_t)TQ_SUB}, estride[2] = {1, 1};
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      load_mode = LOAD_TMA;
+  }
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0;
   cudaError_t e = cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  k_trsm_oz<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta, load_mode,
+  k_trsm_oz<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta, load_mode,
                                                          vec_store, st);
   return cudaGetLastError();
 }

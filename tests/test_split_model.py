@@ -16,7 +16,7 @@ from scipy.linalg import cholesky, solve_triangular
 import synthetic
 
 BIAS = sum(128 << (8 * p) for p in range(7))
-M23, M24, M32 = np.float32(1.5 * 2 ** 23), np.float32(1.5 * 2 ** 24), np.float32(1.5 * 2 ** 32)
+M23, M24, M35 = np.float32(1.5 * 2 ** 23), np.float32(1.5 * 2 ** 24), np.float32(1.5 * 2 ** 35)
 
 
 def scale_exp(A, axis):
@@ -53,28 +53,36 @@ def _f32(x):
 
 def recombine(D):
     """T / 2^12 from the eight region accumulators (exact FP32 integers), T = sum_g D_g 2^(8(7-g)),
-    with the kernel's FP32 steps: regions 0-4 through the 1.5 * 2^23 offset (exact for
+    with the kernel's steps: regions 0-4 through the 1.5 * 2^23 offset (exact for
     |D| <= 2^22); region 5 split into an even part (1.5 * 2^24 offset) and a remainder in
     {-1, 0, 1}; the remainder, region 6 and region 7 merged by two FP32 fused multiply-adds
-    (|r| < 2^31) and taken at a resolution of 2^9 (1.5 * 2^32 offset)."""
+    (|r| < 2^31) and taken at a resolution of 2^12 (1.5 * 2^35 offset); the bit patterns summed
+    modulo 2^64, regions 0 and 1 in the high word."""
     v = [_f32(d) for d in D]
     for g in range(8):
         assert np.array_equal(v[g].astype(np.int64), D[g])           # exact in FP32
-    a = [_bits(v[g] + M23) - 0x4B400000 for g in range(5)]
+    a = [_bits(v[g] + M23) for g in range(5)]
     for g in range(5):
-        assert np.array_equal(a[g], D[g])
+        assert np.array_equal(a[g] - 0x4B400000, D[g])
     c5 = (v[5] + M24).astype(np.float32)
-    q5 = _bits(c5) - 0x4BC00000
+    q5 = _bits(c5)
     lo = (v[5] - (c5 - M24).astype(np.float32)).astype(np.float32)
-    assert np.array_equal(2 * q5 + lo.astype(np.int64), D[5])
+    assert np.array_equal(2 * (q5 - 0x4BC00000) + lo.astype(np.int64), D[5])
     r = _f32(v[6].astype(np.float64) * 256 + v[7].astype(np.float64))        # fmaf
     r = _f32(lo.astype(np.float64) * 65536 + r.astype(np.float64))             # fmaf
     assert np.abs(r).max() < 2 ** 31
-    qr = _bits((r + M32).astype(np.float32)) - 0x4FC00000
-    h = (a[0] << 24) + (a[1] << 16) + (a[2] << 8) + a[3]
-    l = (a[4] << 24) + (q5 << 17) + (qr << 9)
-    assert np.abs(h).max() < 2 ** 43 and np.abs(l).max() < 2 ** 62
-    return (h << 20) + (l >> 12)
+    qr = _bits((r + M35).astype(np.float32))
+    o23, o24, o35 = 0x4B400000, 0x4BC00000, 0x51400000
+    c_hi = (o23 * 4096 + o23 * 16) % 2 ** 32
+    c_lo = (o23 * 2 ** 28 + o23 * 2 ** 20 + o23 * 2 ** 12 + o24 * 32 + o35) % 2 ** 64
+    out = np.empty(D[0].shape, dtype=np.int64)
+    for idx in np.ndindex(D[0].shape):  # Python integers: exact modular arithmetic
+        hw = (int(a[0][idx]) * 4096 + int(a[1][idx]) * 16 - c_hi) % 2 ** 32
+        lw = (int(qr[idx]) + int(q5[idx]) * 32 + int(a[4][idx]) * 2 ** 12 + int(a[3][idx]) * 2 ** 20 +
+              int(a[2][idx]) * 2 ** 28 - c_lo) % 2 ** 64
+        t = (lw + (hw << 32)) % 2 ** 64
+        out[idx] = t - 2 ** 64 if t >= 2 ** 63 else t
+    return out
 
 
 def split_product(X, B):
