@@ -15,10 +15,9 @@
 // 4 x 256 digit products, |D| <= 2^22, exact in FP32.  With
 //   T_p(j, k) = sum_g' 2^(7 (7 - g')) D_g'(64p + j, k),
 // the event's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
-// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p is formed in 64-bit integers (T / 64:
-// an even-slice partial value is below 2^55, so |T_p| < 2^68), converted with integer
-// instructions and added to per-thread FP64 sums; one FP64 atomic per entry (j <= k) and
-// parity at the end.
+// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p / 64 is formed in 64-bit integers
+// (tc::recombine_g7), converted on the FP64 pipe and added to per-thread FP64 sums; one FP64
+// atomic per entry (j <= k) and parity at the end.
 //
 // One CTA per SM, persistent over its row range; warps specialise:
 //   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
@@ -383,8 +382,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           tmem_regs_ready(v);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const long long t = recombine8<6>(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
-            const double y = int_times_pow2(t, ebase + ce[k0 + c]);  // T / 64 (|T| < 2^68)
+            const long long t = recombine_g7(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+            const double y = int_times_pow2_cvt(t, ebase + ce[k0 + c]);  // T / 64 (|T| < 2^69)
             S[4 * h4 + c] += y;
           }
         }

@@ -331,6 +331,31 @@ __device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32
   return (th << (28 - SH)) + (tl >> SH);
 }
 
+// T / 64 from eight region accumulators of 7-bit-digit products, T = sum_g 2^(7 (7 - g)) D_g,
+// each D_g an exact FP32 integer with |D_g| <= 2^22 and |D_0| <= 2^19 (a leading digit in
+// every product of region 0), |T| < 2^69.  Regions 0-5 go through the 1.5 * 2^23 offset (bit
+// pattern 0x4B400000 + D_g); regions 6 and 7 are merged by one FP32 fused multiply-add
+// (|r| < 2^30) and taken at a resolution of 2^8 through the 1.5 * 2^31 offset (an error of at
+// most 2^7 units of region 7).  The patterns are summed modulo 2^64, regions 0 and 1 in the
+// high word.
+__device__ __forceinline__ long long recombine_g7(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
+                                                  uint32_t d5, uint32_t d6, uint32_t d7) {
+  constexpr uint32_t O23 = 0x4B400000u, O31 = 0x4F400000u;  // 1.5 * 2^23, 1.5 * 2^31
+  constexpr uint32_t C_HI = (uint32_t)(O23 * 2048ull + O23 * 16ull);
+  constexpr unsigned long long C_LO = (unsigned long long)O23 * (1ull << 29) + (unsigned long long)O23 * (1ull << 22) +
+                                      (unsigned long long)O23 * (1ull << 15) + (unsigned long long)O23 * 256ull +
+                                      (unsigned long long)O31 * 4ull;
+  const float r = __fmaf_rn(__uint_as_float(d6), 128.0f, __uint_as_float(d7));
+  const uint32_t qr = __float_as_uint(__fadd_rn(r, 3221225472.0f));
+  const uint32_t hw = acc_bits(d0) * 2048u + acc_bits(d1) * 16u - C_HI;  // modulo 2^32
+  unsigned long long lw = mad_wide(qr, 4u, 0ULL - C_LO);
+  lw = mad_wide(acc_bits(d5), 1u << 8, lw);
+  lw = mad_wide(acc_bits(d4), 1u << 15, lw);
+  lw = mad_wide(acc_bits(d3), 1u << 22, lw);
+  lw = mad_wide(acc_bits(d2), 1u << 29, lw);
+  return (long long)(lw + ((unsigned long long)hw << 32));
+}
+
 // (double) t * 2^e for |t| < 2^63 and a result in the normal range (0 for t == 0), through the
 // FP64 pipe's int64 conversion: for kernels whose FP64 pipe is otherwise idle and whose issue
 // slots are the scarce resource.
