@@ -132,6 +132,21 @@ randqr_status randqr_cs_hash(randqr_ctx *ctx, uint64_t seed, int64_t m, int64_t 
 randqr_status randqr_gauss_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
                                   double *S2_dev, void *stream);
 
+/* Rademacher sketch S2 (s2 x s1, row-major, device) with entries +-1/sqrt(s2), the dense
+ * alternative to the Gaussian the paper mentions (Sec. 7): entry (r, c) is -1/sqrt(s2) when bit
+ * (c mod 64) of splitmix64(seed XOR splitmix64(r * ceil(s1 / 64) + floor(c / 64))) is set, else
+ * +1/sqrt(s2).  Integer arithmetic only: bit-exact with any host implementation. */
+randqr_status randqr_rademacher_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
+                                      double *S2_dev, void *stream);
+
+/* Which sketch the context generates (and caches per (seed, s1, s2, kind)) for calls that pass
+ * S2 = NULL: RANDQR_SKETCH_GAUSSIAN (default, randqr_gauss_sketch) or RANDQR_SKETCH_RADEMACHER
+ * (randqr_rademacher_sketch), both for seed + 1.  Applies to randqr_sketch, randqr_factor,
+ * randqr_randqr and randqr_shard_sketch on this context; the batched and serving calls keep
+ * the Gaussian sketch. */
+typedef enum { RANDQR_SKETCH_GAUSSIAN = 0, RANDQR_SKETCH_RADEMACHER = 1 } randqr_sketch_kind;
+randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind);
+
 /* Ws = S2 S1 V (Algorithm 1 step 1), s2 x n row-major (ld n) in device memory.
  * W1 = S1 V is formed in the context's workspace by a scatter-add of V's rows (CountSketch
  * with `seed`), then Ws = S2 W1.  S2 may be NULL: the context then uses (and caches) the

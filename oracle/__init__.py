@@ -36,6 +36,7 @@ def _load():
     lib.orc_cs_hash.argtypes = [_U64, _I64, _I64, _ct.POINTER(_ct.c_int32), _ct.POINTER(_ct.c_int8)]
     lib.orc_philox4x64_10.argtypes = [_ct.POINTER(_U64), _ct.POINTER(_U64), _ct.POINTER(_U64)]
     lib.orc_gauss_sketch.argtypes = [_U64, _I64, _I64, _D]
+    lib.orc_rademacher_sketch.argtypes = [_U64, _I64, _I64, _D]
     lib.orc_countsketch.argtypes = [_D, _I64, _I64, _I64, _I64, _U64, _D]
     lib.orc_countsketch_rows.argtypes = [_D, _I64, _I64, _I64, _I64, _U64, _I64, _D]
     lib.orc_cs_hash_at.argtypes = [_U64, _I64, _I64, _I64, _ct.POINTER(_ct.c_int32),
@@ -103,6 +104,13 @@ def philox4x64_10(ctr, key):
 def gauss_sketch(seed: int, s2: int, s1: int):
     S2 = _np.empty((s2, s1), dtype=_np.float64)
     _load().orc_gauss_sketch(_U64(seed), s2, s1, _p(S2))
+    return S2
+
+
+def rademacher_sketch(seed: int, s2: int, s1: int):
+    """Rademacher S2 (s2 x s1) with entries +-1/sqrt(s2) from splitmix64 sign words."""
+    S2 = _np.empty((s2, s1), dtype=_np.float64)
+    _load().orc_rademacher_sketch(_U64(seed), s2, s1, _p(S2))
     return S2
 
 

@@ -116,6 +116,20 @@ void orc_gauss_sketch(uint64_t seed, int64_t s2, int64_t s1, double *S2) {
   }
 }
 
+/* Rademacher sketch S2 in R^{s2 x s1} with entries +-1/sqrt(s2) (the paper's alternative
+ * dense sketch, Sec. 7): entry (r, c) is -1/sqrt(s2) when bit (c mod 64) of
+ * splitmix64(seed XOR splitmix64(r * ceil(s1 / 64) + floor(c / 64))) is set, else +1/sqrt(s2). */
+void orc_rademacher_sketch(uint64_t seed, int64_t s2, int64_t s1, double *S2) {
+  const double scale = 1.0 / sqrt((double)s2);
+  const int64_t nw = (s1 + 63) / 64;
+  for (int64_t r = 0; r < s2; ++r) {
+    for (int64_t c = 0; c < s1; ++c) {
+      uint64_t word = orc_splitmix64(seed ^ orc_splitmix64((uint64_t)(r * nw + c / 64)));
+      S2[r * s1 + c] = ((word >> (c % 64)) & 1ULL) ? -scale : scale;
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------------------
  * Algorithm 1 (randQR), step 1: W = S2 S1 V, split as W1 = S1 V then W = S2 W1 (Sec. 4.2).
  * ---------------------------------------------------------------------------------- */

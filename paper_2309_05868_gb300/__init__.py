@@ -11,12 +11,14 @@ is m x n (m rows), sketch sizes s1 (CountSketch) and s2 (Gaussian).
 import ctypes as _ct
 import os as _os
 
-__all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_sketch",
+__all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_rademacher_sketch",
+           "randqr_sketch", "SKETCH_GAUSSIAN", "SKETCH_RADEMACHER",
            "randqr_factor", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
            "randqr_shard_sketch", "randqr_sketch_r", "randqr_shard_gram", "randqr_shard_finish",
            "default_sketch_sizes", "library_path", "FP64", "F32X2"]
 
 FP64, F32X2 = 0, 1
+SKETCH_GAUSSIAN, SKETCH_RADEMACHER = 0, 1
 _HERE = _os.path.dirname(_os.path.abspath(__file__))
 _LIB_PATH = _os.path.join(_HERE, "_build", "librandqr.so")
 _lib = None
@@ -63,6 +65,8 @@ def _load():
         "randqr_get_status": [vp, vp, _ct.POINTER(Info)],
         "randqr_cs_hash": [vp, u64, i64, i64, vp, vp, vp],
         "randqr_gauss_sketch": [vp, u64, i64, i64, vp, vp],
+        "randqr_rademacher_sketch": [vp, u64, i64, i64, vp, vp],
+        "randqr_set_sketch_kind": [vp, i32],
         "randqr_sketch": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
         "randqr_sketch_static": [vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
         "randqr_factor": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
@@ -142,6 +146,11 @@ class Context:
         L.randqr_set_tensor_cores.restype = _ct.c_int32
         self._check(L.randqr_set_tensor_cores(self._h, int(bool(enable))))
 
+    def set_sketch_kind(self, kind):
+        """The S2 the context generates for calls without an explicit S2 (SKETCH_GAUSSIAN or
+        SKETCH_RADEMACHER)."""
+        self._check(_load().randqr_set_sketch_kind(self._h, int(kind)))
+
     def kernel_times(self):
         """{kernel name: (total device ms, launches)} recorded since the last read."""
         L = _load()
@@ -206,6 +215,15 @@ def randqr_gauss_sketch(seed, s2, s1, device=0, ctx=None, stream=None):
     S2 = torch.empty((s2, s1), dtype=torch.float64, device=f"cuda:{device}")
     c = _ctx(ctx, S2)
     c._check(_load().randqr_gauss_sketch(c.handle, seed, s2, s1, _ptr(S2), _stream(stream)))
+    return S2
+
+
+def randqr_rademacher_sketch(seed, s2, s1, device=0, ctx=None, stream=None):
+    """Rademacher sketch S2 (s2 x s1, entries +-1/sqrt(s2)) on the device."""
+    import torch
+    S2 = torch.empty((s2, s1), dtype=torch.float64, device=f"cuda:{device}")
+    c = _ctx(ctx, S2)
+    c._check(_load().randqr_rademacher_sketch(c.handle, seed, s2, s1, _ptr(S2), _stream(stream)))
     return S2
 
 

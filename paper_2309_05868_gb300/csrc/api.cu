@@ -112,7 +112,8 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
 // The cached S2 for (seed, s1, s2), generated on `s` if missing.
 randqr_status ensure_s2(randqr_ctx *ctx, uint64_t seed, int64_t s1, int64_t s2, cudaStream_t s,
                         const double **out) {
-  if (!(ctx->s2_valid && ctx->s2_seed == seed && ctx->s2_s1 == s1 && ctx->s2_s2 == s2)) {
+  if (!(ctx->s2_valid && ctx->s2_seed == seed && ctx->s2_s1 == s1 && ctx->s2_s2 == s2 &&
+        ctx->s2_kind_cached == ctx->s2_kind)) {
     const size_t bytes = sizeof(double) * (size_t)(s1 * s2);
     if (bytes > ctx->s2_bytes) {
       if (ctx->budget && bytes + ctx->ws_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
@@ -126,8 +127,12 @@ randqr_status ensure_s2(randqr_ctx *ctx, uint64_t seed, int64_t s1, int64_t s2, 
       }
       ctx->s2_bytes = bytes;
     }
-    RQ_CUDA(timed(ctx, s, rq::K_GAUSS_GEN, [&] { return rq::launch_gauss_gen(seed, s2, s1, ctx->s2_buf, s); }));
+    RQ_CUDA(timed(ctx, s, rq::K_GAUSS_GEN, [&] {
+      return ctx->s2_kind == RANDQR_SKETCH_RADEMACHER ? rq::launch_rad_gen(seed, s2, s1, ctx->s2_buf, s)
+                                                      : rq::launch_gauss_gen(seed, s2, s1, ctx->s2_buf, s);
+    }));
     ctx->s2_valid = true;
+    ctx->s2_kind_cached = ctx->s2_kind;
     ctx->s2_seed = seed;
     ctx->s2_s1 = s1;
     ctx->s2_s2 = s2;
@@ -406,6 +411,22 @@ randqr_status randqr_gauss_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, in
   RQ_CUDA(timed(ctx, (cudaStream_t)stream, rq::K_GAUSS_GEN, [&] {
     return rq::launch_gauss_gen(seed, s2, s1, S2_dev, (cudaStream_t)stream);
   }));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_rademacher_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
+                                      double *S2_dev, void *stream) {
+  if (!ctx || !S2_dev || s2 < 1 || s1 < 1) return RANDQR_ERR_ARG;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  RQ_CUDA(timed(ctx, (cudaStream_t)stream, rq::K_GAUSS_GEN, [&] {
+    return rq::launch_rad_gen(seed, s2, s1, S2_dev, (cudaStream_t)stream);
+  }));
+  return RANDQR_OK;
+}
+
+randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind) {
+  if (!ctx || (kind != RANDQR_SKETCH_GAUSSIAN && kind != RANDQR_SKETCH_RADEMACHER)) return RANDQR_ERR_ARG;
+  ctx->s2_kind = kind;
   return RANDQR_OK;
 }
 

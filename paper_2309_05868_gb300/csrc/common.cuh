@@ -107,6 +107,8 @@ struct randqr_ctx {
   bool s2_valid = false;
   uint64_t s2_seed = 0;
   int64_t s2_s1 = 0, s2_s2 = 0;
+  int32_t s2_kind_cached = 0;  // randqr_sketch_kind of the cached S2
+  int32_t s2_kind = 0;         // randqr_sketch_kind generated when a call passes S2 = NULL
   // status word on the device, and a pinned host copy
   rq::DevStatus *status_dev = nullptr;
   rq::DevStatus *status_host = nullptr;
@@ -145,6 +147,7 @@ namespace rq {
 cudaError_t launch_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign,
                            cudaStream_t s);
 cudaError_t launch_gauss_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cudaStream_t s);
+cudaError_t launch_rad_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cudaStream_t s);
 // W1 += S1 V for the rows row0 .. row0 + m - 1 of a larger matrix (the hash takes the global index)
 cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
                               uint64_t seed, int64_t row0, double *W1, int num_sms, const DevStatus *st,

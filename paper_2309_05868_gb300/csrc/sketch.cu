@@ -56,6 +56,27 @@ cudaError_t launch_gauss_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, 
 }
 
 // ---------------------------------------------------------------------------------------
+// Rademacher S2 with entries +-1/sqrt(s2): entry (r, c) is negative when bit c % 64 of
+// splitmix64(seed ^ splitmix64(r * ceil(s1 / 64) + c / 64)) is set.  One thread per entry.
+// ---------------------------------------------------------------------------------------
+__global__ void k_rad_gen(uint64_t seed, int64_t s2, int64_t s1, double scale, double *S2) {
+  const int64_t total = s2 * s1, nw = (s1 + 63) / 64;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / s1, c = idx - r * s1;
+    const uint64_t word = splitmix64(seed ^ splitmix64((uint64_t)(r * nw + (c >> 6))));
+    S2[idx] = ((word >> (c & 63)) & 1ULL) ? -scale : scale;
+  }
+}
+
+cudaError_t launch_rad_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cudaStream_t s) {
+  const int64_t total = s2 * s1;
+  const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 8192);
+  k_rad_gen<<<blocks, 256, 0, s>>>(seed, s2, s1, 1.0 / sqrt((double)s2), S2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
 // CountSketch scatter-add: W1[bucket(i), :] += sign(i) V[i, :].
 // One warp takes 32 consecutive rows: each lane hashes one of them, then the warp walks the
 // rows, broadcasting (bucket, sign) with a shuffle, lanes striding over the columns so the

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import synthetic
+from gpu_util import parity_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -85,3 +86,34 @@ def test_sketch_uses_cached_seeded_s2(rq):
                          S2=rq.randqr_gauss_sketch(22, s2, s1)).cpu().numpy()
     Wo = oracle.gemm(oracle.gauss_sketch(22, s2, s1), oracle.countsketch(V, s1, 21))
     assert np.abs(a - b).max() < 1e-13 and np.abs(a - Wo).max() < 1e-12
+
+
+@pytest.mark.parametrize("s2,s1", [(1, 1), (64, 544), (256, 8320), (37, 1001), (776, 34279)])
+def test_rademacher_sketch_bit_exact(rq, s2, s1):
+    S2 = rq.randqr_rademacher_sketch(11, s2, s1).cpu().numpy()
+    np.testing.assert_array_equal(S2, oracle.rademacher_sketch(11, s2, s1))
+
+
+def test_rand_cholqr_with_rademacher_sketch_kind(rq):
+    # the context's generated S2 (seed + 1) is the Rademacher sketch: same factors as the
+    # explicit sketch, and parity with the oracle run on that sketch
+    m, n = 20000, 16
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e10, seed=2)
+    Vd = torch.from_numpy(V).cuda()
+    ctx = rq.Context(0)
+    ctx.set_sketch_kind(rq.SKETCH_RADEMACHER)
+    Q, R, _ = rq.randqr_factor(Vd, s1, s2, seed=5, ctx=ctx)
+    S2 = oracle.rademacher_sketch(6, s2, s1)
+    Q2, R2, _ = rq.randqr_factor(Vd, s1, s2, seed=5, S2=torch.from_numpy(S2).cuda(), ctx=ctx)
+    assert (Q - Q2).abs().max().item() <= 1e-13
+    Q_ref, R_ref = oracle.rand_cholqr(V, s1, s2, 5, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q.cpu().numpy() - Q_ref).max() <= tq
+    assert np.abs(R.cpu().numpy() - R_ref).max() / np.abs(R_ref).max() <= tr
+    ctx.set_sketch_kind(rq.SKETCH_GAUSSIAN)
+    Qg, _, _ = rq.randqr_factor(Vd, s1, s2, seed=5, ctx=ctx)
+    Qg2, _, _ = rq.randqr_factor(Vd, s1, s2, seed=5, S2=rq.randqr_gauss_sketch(6, s2, s1), ctx=ctx)
+    assert (Qg - Qg2).abs().max().item() <= 1e-13
+    with pytest.raises(rq.RandQRError):
+        ctx.set_sketch_kind(7)

@@ -84,6 +84,49 @@ def test_gauss_sketch_distribution():
     assert abs((z.reshape(s2, s1).mean(axis=1) * math.sqrt(s1)).std() - 1) < 0.3
 
 
+def test_rademacher_sketch_entries_and_moments():
+    s2, s1 = 48, 5000
+    S2 = oracle.rademacher_sketch(9, s2, s1)
+    scale = 1.0 / math.sqrt(s2)
+    assert set(np.unique(S2)) == {-scale, scale}
+    z = np.sign(S2)
+    # unbiased overall, in every bit position of the sign words, and in every row
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    per_bit = np.array([z[:, b::64].mean() for b in range(64)])
+    assert np.abs(per_bit).max() < 5 / math.sqrt(z.size / 64)
+    assert np.abs(z.mean(axis=1)).max() < 5 / math.sqrt(s1)
+    # neighbours uncorrelated: along a row (inside and across sign words) and across rows
+    k = (s1 - 1 - 63) // 64 + 1  # pairs (63 + 64 i, 64 + 64 i) inside the row
+    for a, b in ((z[:, :-1], z[:, 1:]), (z[:, 63::64][:, :k], z[:, 64::64][:, :k]), (z[:-1], z[1:])):
+        assert abs((a * b).mean()) < 5 / math.sqrt(a.size)
+    # S2^T S2 has an exact unit diagonal and off-diagonal entries of variance 1/s2
+    C = S2.T[:400] @ S2[:, :400]
+    np.testing.assert_allclose(np.diag(C), 1.0, rtol=0, atol=1e-15)
+    off = C[np.triu_indices(400, 1)]
+    assert abs(off.std() * math.sqrt(s2) - 1) < 0.05
+
+
+def test_rademacher_sketch_embeds_a_subspace():
+    # subspace embedding (Sec. 2): singular values of S2 U within 1 +- eps for orthonormal U
+    s1, n = 3000, 8
+    U, _ = np.linalg.qr(synthetic.rng(4).standard_normal((s1, n)))
+    for s2 in (128, 512):
+        sv = np.linalg.svd(oracle.rademacher_sketch(2, s2, s1) @ U, compute_uv=False)
+        eps = 3.0 * math.sqrt(n / s2)
+        assert sv.max() < 1 + eps and sv.min() > 1 - eps
+
+
+def test_rand_cholqr_with_a_rademacher_sketch(kappa=1e12):
+    m, n = 4000, 12
+    s1, s2 = 2 * (n * n + n), 4 * n
+    V = synthetic.make_v(m, n, kappa, seed=8)
+    Q, R = oracle.rand_cholqr(V, s1, s2, 0, S2=oracle.rademacher_sketch(1, s2, s1))
+    e2, _ = oracle.orth_err(Q)
+    assert e2 <= 1e-13 and oracle.resid(V, Q, R) <= 1e-14
+    Qh, Rh = oracle.householder_qr(V)
+    np.testing.assert_allclose(R, _posdiag(Rh), rtol=0, atol=1e-12 * kappa * 1e-3 * np.abs(R).max())
+
+
 def test_gauss_sketch_counter_layout():
     # entry (r, c) depends only on (seed, r*s1 + c): a wider sketch with the same flat
     # counters gives the same numbers up to the 1/sqrt(s2) scaling.
