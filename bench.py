@@ -524,6 +524,28 @@ def main():
                                    "value": algo_bytes / (sh_ms / 1e3) / 1e9, "unit": "GB/s",
                                    "over_unsharded": sh_ms / ms, "status": st}
 
+    if not a.no_extras and world == 1:
+        # the paper's multisketch sizes (Sec. 6.2) on the same matrix: a larger sketch GEMM
+        p1, p2 = synthetic.paper_multisketch_sizes(n)
+        for _ in range(2):
+            rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+        torch.cuda.synchronize()
+        ctx.kernel_times()
+        ctx.set_profiling(True)
+        p0, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(3):
+            rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+        pe.record(stream)
+        torch.cuda.synchronize()
+        ctx.set_profiling(False)
+        pkt = ctx.kernel_times()
+        pms = p0.elapsed_time(pe) / 3
+        st, _ = rq.get_status(ctx)
+        line["paper_sketch_sizes"] = {"s1": p1, "s2": p2, "ms_per_step": pms, "status": st,
+                                      "value": algo_bytes / (pms / 1e3) / 1e9, "unit": "GB/s",
+                                      "kernels_ms_per_step": {k: v[0] / 3 for k, v in pkt.items()}}
+
     if not a.no_extras:
         if world == 1:
             # the other precision of the row passes, on the same matrix

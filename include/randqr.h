@@ -139,12 +139,25 @@ randqr_status randqr_gauss_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, in
 randqr_status randqr_rademacher_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s2, int64_t s1,
                                       double *S2_dev, void *stream);
 
-/* Which sketch the context generates (and caches per (seed, s1, s2, kind)) for calls that pass
- * S2 = NULL: RANDQR_SKETCH_GAUSSIAN (default, randqr_gauss_sketch) or RANDQR_SKETCH_RADEMACHER
- * (randqr_rademacher_sketch), both for seed + 1.  Applies to randqr_sketch, randqr_factor,
- * randqr_randqr and randqr_shard_sketch on this context; the batched and serving calls keep
- * the Gaussian sketch. */
-typedef enum { RANDQR_SKETCH_GAUSSIAN = 0, RANDQR_SKETCH_RADEMACHER = 1 } randqr_sketch_kind;
+/* The sketch of Algorithm 1 step 1 on this context:
+ *   RANDQR_SKETCH_GAUSSIAN (default): S2 S1 with S2 from randqr_gauss_sketch(seed + 1) when the
+ *     call passes S2 = NULL;
+ *   RANDQR_SKETCH_RADEMACHER: the same with S2 from randqr_rademacher_sketch(seed + 1);
+ *   RANDQR_SKETCH_COUNT_ONLY: the single CountSketch S1 (S2 = I; the call must pass s2 == s1,
+ *     and any S2 is ignored);
+ *   RANDQR_SKETCH_GAUSSIAN_ONLY: the single Gaussian sketch S2 (S1 = I; the call must pass
+ *     s1 == m; S2 is s2 x m; not for randqr_shard_sketch).
+ * The single-sketch kinds are the paper's comparison points (Sec. 6.2, sizes ceil(6.8 (n^2+n))
+ * and ceil(36.01 ln n)); a call whose sizes do not fit the kind returns RANDQR_ERR_ARG.
+ * Generated sketches are cached per (seed, s1, s2, kind).  Applies to randqr_sketch,
+ * randqr_factor, randqr_randqr and randqr_shard_sketch on this context; the batched and
+ * serving calls keep the Gaussian multisketch. */
+typedef enum {
+  RANDQR_SKETCH_GAUSSIAN = 0,
+  RANDQR_SKETCH_RADEMACHER = 1,
+  RANDQR_SKETCH_COUNT_ONLY = 2,
+  RANDQR_SKETCH_GAUSSIAN_ONLY = 3
+} randqr_sketch_kind;
 randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind);
 
 /* Ws = S2 S1 V (Algorithm 1 step 1), s2 x n row-major (ld n) in device memory.

@@ -12,13 +12,14 @@ import ctypes as _ct
 import os as _os
 
 __all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_rademacher_sketch",
-           "randqr_sketch", "SKETCH_GAUSSIAN", "SKETCH_RADEMACHER",
+           "randqr_sketch", "SKETCH_GAUSSIAN", "SKETCH_RADEMACHER", "SKETCH_COUNT_ONLY",
+           "SKETCH_GAUSSIAN_ONLY",
            "randqr_factor", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
            "randqr_shard_sketch", "randqr_sketch_r", "randqr_shard_gram", "randqr_shard_finish",
            "default_sketch_sizes", "library_path", "FP64", "F32X2"]
 
 FP64, F32X2 = 0, 1
-SKETCH_GAUSSIAN, SKETCH_RADEMACHER = 0, 1
+SKETCH_GAUSSIAN, SKETCH_RADEMACHER, SKETCH_COUNT_ONLY, SKETCH_GAUSSIAN_ONLY = 0, 1, 2, 3
 _HERE = _os.path.dirname(_os.path.abspath(__file__))
 _LIB_PATH = _os.path.join(_HERE, "_build", "librandqr.so")
 _lib = None
@@ -147,8 +148,9 @@ class Context:
         self._check(L.randqr_set_tensor_cores(self._h, int(bool(enable))))
 
     def set_sketch_kind(self, kind):
-        """The S2 the context generates for calls without an explicit S2 (SKETCH_GAUSSIAN or
-        SKETCH_RADEMACHER)."""
+        """The sketch of Algorithm 1 step 1: SKETCH_GAUSSIAN or SKETCH_RADEMACHER multisketch
+        (S2 generated when a call passes none), SKETCH_COUNT_ONLY (S2 = I, s2 == s1) or
+        SKETCH_GAUSSIAN_ONLY (S1 = I, s1 == m)."""
         self._check(_load().randqr_set_sketch_kind(self._h, int(kind)))
 
     def kernel_times(self):

@@ -168,6 +168,14 @@ bool bad_sketch_sizes(int64_t n, int64_t s1, int64_t s2) {
   return s2 < n || s1 < s2 || s1 >= ((int64_t)1 << 31) || s2 > ((int64_t)1 << 20);
 }
 
+// The single-sketch kinds fix one size: S2 = I needs s2 == s1, S1 = I needs s1 == m (and no
+// row offset: a row block of V does not carry its columns of a dense S2).
+bool bad_sketch_kind(const randqr_ctx *ctx, int64_t m, int64_t s1, int64_t s2, int64_t row0) {
+  if (ctx->s2_kind == RANDQR_SKETCH_COUNT_ONLY) return s2 != s1;
+  if (ctx->s2_kind == RANDQR_SKETCH_GAUSSIAN_ONLY) return s1 != m || row0 != 0;
+  return false;
+}
+
 randqr_status begin_call(randqr_ctx *ctx, cudaStream_t s) {
   RQ_CUDA(cudaSetDevice(ctx->device));
   RQ_CUDA(cudaMemsetAsync(ctx->status_dev, 0, sizeof(DevStatus), s));
@@ -184,10 +192,36 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
                               int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                               const double *S2, const Workspace &w, cudaStream_t s,
                               bool do_hhqr, int64_t row0 = 0) {
+  if (ctx->s2_kind == RANDQR_SKETCH_COUNT_ONLY) {
+    // single CountSketch (S2 = I, s2 == s1): the scatter goes straight into Ws
+    RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
+    RQ_CUDA(timed(ctx, s, rq::K_CS_SCATTER, [&] {
+      return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, row0, w.Ws, ctx->num_sms, ctx->status_dev, s);
+    }));
+    if (do_hhqr)
+      RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));
+    return RANDQR_OK;
+  }
   const double *S2p = S2;
   if (!S2p) {
     randqr_status st = ensure_s2(ctx, seed + 1, s1, s2, s, &S2p);
     if (st != RANDQR_OK) return st;
+  }
+  if (ctx->s2_kind == RANDQR_SKETCH_GAUSSIAN_ONLY) {
+    // single Gaussian sketch (S1 = I, s1 == m): Ws = S2 V, V packed to ld n in W1 if needed
+    const double *B = V;
+    if (ldv != n) {
+      RQ_CUDA(cudaMemcpy2DAsync(w.W1, sizeof(double) * (size_t)n, V, sizeof(double) * (size_t)ldv,
+                                sizeof(double) * (size_t)n, (size_t)m, cudaMemcpyDeviceToDevice, s));
+      B = w.W1;
+    }
+    RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
+    RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
+      return rq::launch_sketch_gemm(S2p, B, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
+    }));
+    if (do_hhqr)
+      RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));
+    return RANDQR_OK;
   }
   RQ_CUDA(cudaMemsetAsync(w.W1, 0, sizeof(double) * (size_t)(s1 * n), s));
   RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
@@ -425,7 +459,7 @@ randqr_status randqr_rademacher_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s
 }
 
 randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind) {
-  if (!ctx || (kind != RANDQR_SKETCH_GAUSSIAN && kind != RANDQR_SKETCH_RADEMACHER)) return RANDQR_ERR_ARG;
+  if (!ctx || kind < RANDQR_SKETCH_GAUSSIAN || kind > RANDQR_SKETCH_GAUSSIAN_ONLY) return RANDQR_ERR_ARG;
   ctx->s2_kind = kind;
   return RANDQR_OK;
 }
@@ -433,7 +467,8 @@ randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind) {
 randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                             int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                             const double *S2, double *Ws, void *stream) {
-  if (!ctx || !V || !Ws || n < 1 || m < 1 || ldv < n || bad_sketch_sizes(n, s1, s2))
+  if (!ctx || !V || !Ws || n < 1 || m < 1 || ldv < n || bad_sketch_sizes(n, s1, s2) ||
+      bad_sketch_kind(ctx, m, s1, s2, 0))
     return RANDQR_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   randqr_status st = begin_call(ctx, s);
@@ -484,6 +519,7 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
                                  double *R, int64_t ldr, randqr_info *info, void *stream,
                                  bool second_pass) {
   if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr) || bad_sketch_sizes(n, s1, s2) ||
+      bad_sketch_kind(ctx, m, s1, s2, 0) ||
       (prec != RANDQR_FP64 && prec != RANDQR_F32X2) || s2 > m)
     return RANDQR_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -592,7 +628,8 @@ randqr_status randqr_shard_sketch(randqr_ctx *ctx, const double *V, int64_t m, i
                                   int64_t row0, int64_t s1, int64_t s2, uint64_t seed, const double *S2,
                                   double *Ws, void *stream) {
   if (!ctx || !V || !Ws || n < 1 || n > kMaxN || m < 1 || ldv < n || row0 < 0 ||
-      bad_sketch_sizes(n, s1, s2))
+      bad_sketch_sizes(n, s1, s2) || bad_sketch_kind(ctx, m, s1, s2, row0) ||
+      ctx->s2_kind == RANDQR_SKETCH_GAUSSIAN_ONLY)
     return RANDQR_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   randqr_status st = begin_call(ctx, s);

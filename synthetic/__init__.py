@@ -16,7 +16,7 @@ import math
 import numpy as np
 
 __all__ = ["sigmas", "make_v", "make_v_torch", "make_v_block_torch", "integer_matrix", "default_sketch_sizes",
-           "paper_multisketch_sizes", "rng"]
+           "paper_multisketch_sizes", "paper_single_sketch_sizes", "rng"]
 
 
 def rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -96,3 +96,9 @@ def paper_multisketch_sizes(n: int):
     p1 = math.ceil(8.24 * (n * n + n))
     p2 = math.ceil(74.3 * math.log(p1))
     return p1, p2
+
+
+def paper_single_sketch_sizes(n: int):
+    """The paper's single-sketch sizes (Sec. 6.2): a CountSketch alone with ceil(6.8 (n^2 + n))
+    rows, a Gaussian alone with ceil(36.01 ln n) rows (natural log; at least n)."""
+    return math.ceil(6.8 * (n * n + n)), max(n, math.ceil(36.01 * math.log(n)))

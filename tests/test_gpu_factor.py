@@ -60,6 +60,21 @@ def test_rand_cholqr_parity(rq, m, n, kappa):
     assert np.abs(R - Ro).max() / np.abs(Ro).max() <= tr
 
 
+@pytest.mark.parametrize("m,n,kappa", [(20000, 8, 1e12), (20000, 32, 1e14), (30000, 64, 1e12)])
+def test_rand_cholqr_parity_paper_sketch_sizes(rq, m, n, kappa):
+    # the paper's multisketch sizes (Sec. 6.2): s1 = ceil(8.24 (n^2 + n)), s2 = ceil(74.3 ln s1)
+    s1, s2 = synthetic.paper_multisketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=n)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, _ = _run(rq, V, s1, s2, 0, S2)
+    e2, _ = oracle.orth_err(Q)
+    assert e2 <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+    Qo, Ro = oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q - Qo).max() <= tq
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= tr
+
+
 @pytest.mark.parametrize("ld_pad,inplace", [(1, False), (5, True), (0, True)])
 def test_leading_dims_and_in_place(rq, ld_pad, inplace):
     m, n = 7777, 24
@@ -257,3 +272,46 @@ def test_tensor_core_gram_cholqr2_exact_on_orthonormal_columns(rq):
     R = R.cpu().numpy()
     np.testing.assert_allclose(np.abs(np.diag(R)), 1.0, rtol=1e-14)
     assert np.abs(np.triu(R, 1)).max() < 1e-14
+
+
+def test_single_countsketch_kind(rq):
+    # S2 = I: rand_cholQR with the CountSketch alone, against the oracle on an explicit identity
+    m, n = 20000, 16
+    s1, _ = synthetic.paper_single_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e6, seed=3)  # kappa <= 1e8: the 1e-10 parity bar applies
+    ctx = rq.Context(0)
+    ctx.set_sketch_kind(rq.SKETCH_COUNT_ONLY)
+    Q, R, _ = rq.randqr_factor(torch.from_numpy(V).cuda(), s1, s1, seed=4, ctx=ctx)
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    e2, _ = oracle.orth_err(Q)
+    assert e2 <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+    Qo, Ro = oracle.rand_cholqr(V, s1, s1, seed=4, S2=np.eye(s1))
+    assert np.abs(Q - Qo).max() <= 1e-10
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10
+    with pytest.raises(rq.RandQRError):  # s2 != s1
+        rq.randqr_factor(torch.from_numpy(V).cuda(), s1, 64, seed=4, ctx=ctx)
+
+
+def test_single_gaussian_kind(rq):
+    # S1 = I: the Gaussian sketch of V itself, against the oracle's steps (Algorithm 3 with
+    # Ws = S2 V)
+    m, n = 5000, 16
+    _, s2 = synthetic.paper_single_sketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e6, seed=6)  # kappa <= 1e8: the 1e-10 parity bar applies
+    S2 = oracle.gauss_sketch(2, s2, m)
+    ctx = rq.Context(0)
+    ctx.set_sketch_kind(rq.SKETCH_GAUSSIAN_ONLY)
+    buf = torch.zeros((m, n + 3), dtype=torch.float64, device="cuda")
+    buf[:, :n] = torch.from_numpy(V).cuda()  # ld != n: packed internally
+    Q, R, _ = rq.randqr_factor(buf[:, :n], m, s2, seed=0, S2=torch.from_numpy(S2).cuda(), ctx=ctx)
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    e2, _ = oracle.orth_err(Q)
+    assert e2 <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+    Rs = oracle.hhqr_r(oracle.gemm(S2, V))
+    W = oracle.trsm(V, Rs)
+    Rc = oracle.chol(oracle.gram(W))
+    Qo, Ro = oracle.trsm(W, Rc), oracle.trmm(Rc, Rs)
+    assert np.abs(Q - Qo).max() <= 1e-10
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10
+    with pytest.raises(rq.RandQRError):  # s1 != m
+        rq.randqr_factor(torch.from_numpy(V).cuda(), 544, s2, seed=0, ctx=ctx)
