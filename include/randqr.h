@@ -115,7 +115,7 @@ randqr_status randqr_get_kernel_times(randqr_ctx *ctx, int32_t max_kinds, double
 const char *randqr_kernel_name(int32_t kind);
 
 /* ---- Step 1 of Algorithm 1, split into its parts (Sec. 4.2) --------------------------
- * CountSketch S1 (Sec. 2: one +-1 per column of S1, row and sign uniform): column i of
+ * CountSketch S1 (Sec. 3: one +-1 per column of S1, row and sign uniform): column i of
  * S1 has its nonzero in row bucket[i] with value sign[i], where
  *   x = splitmix64(seed XOR splitmix64(i)),  bucket = floor(hi32(x) * s1 / 2^32),
  *   sign = -1 if (x & 1) else +1,
@@ -124,7 +124,7 @@ const char *randqr_kernel_name(int32_t kind);
 randqr_status randqr_cs_hash(randqr_ctx *ctx, uint64_t seed, int64_t m, int64_t s1,
                              int32_t *bucket_dev, int8_t *sign_dev, void *stream);
 
-/* Gaussian sketch S2 (s2 x s1, row-major, device) with N(0, 1/s2) entries (Sec. 2,
+/* Gaussian sketch S2 (s2 x s1, row-major, device) with N(0, 1/s2) entries (Sec. 3,
  * S = G / sqrt(p)).  Entry (r, c) takes Philox4x64-10 (Salmon et al. 2011) at counter
  * (r*s1 + c, 0, 0, 0) with key (seed, 0), u1 = ((x0>>11)+1) 2^-53, u2 = (x1>>11) 2^-53,
  * and Box-Muller z = sqrt(-2 ln u1) cos(2 pi u2).  The integers are exact; the

@@ -54,7 +54,7 @@ uint64_t orc_splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-/* CountSketch column i of S1 (Sec. 2, the sparse embedding with one +-1 per column whose
+/* CountSketch column i of S1 (Sec. 3, the sparse embedding with one +-1 per column whose
  * row and sign are uniform): x = splitmix64(seed XOR splitmix64(i)); row (bucket) =
  * floor(hi32(x) * s1 / 2^32); sign = -1 if the low bit of x is set, else +1. */
 void orc_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign) {
@@ -96,7 +96,7 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Gaussian sketch S2 in R^{s2 x s1} with entries N(0, 1/s2) (Sec. 2: S = G / sqrt(p)).
+/* Gaussian sketch S2 in R^{s2 x s1} with entries N(0, 1/s2) (Sec. 3: S = G / sqrt(p)).
  * Entry (r, c) takes Philox4x64-10 at counter (r*s1 + c, 0, 0, 0) with key (seed, 0);
  * u1 = (x0>>11 + 1) 2^-53 in (0,1], u2 = (x1>>11) 2^-53 in [0,1), and the Box-Muller
  * transform z = sqrt(-2 ln u1) cos(2 pi u2). */

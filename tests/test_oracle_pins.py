@@ -107,7 +107,7 @@ def test_rademacher_sketch_entries_and_moments():
 
 
 def test_rademacher_sketch_embeds_a_subspace():
-    # subspace embedding (Sec. 2): singular values of S2 U within 1 +- eps for orthonormal U
+    # subspace embedding (Sec. 3): singular values of S2 U within 1 +- eps for orthonormal U
     s1, n = 3000, 8
     U, _ = np.linalg.qr(synthetic.rng(4).standard_normal((s1, n)))
     for s2 in (128, 512):
