@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, doub
   extern __shared__ double A[];  // packed upper, n(n+1)/2
   __shared__ double red[32];
   __shared__ int s_fail;
+  __shared__ double s_inv;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int P = n * (n + 1) / 2;
   for (int e = tid; e < P; e += nt) A[e] = Gp[e];
@@ -321,13 +322,17 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, doub
       if (!(d > 0.0) || !isfinite(d)) {
         s_fail = j + 1;
       } else {
-        A[tri_idx(j, j)] = sqrt(d);
+        const double r = sqrt(d);
+        A[tri_idx(j, j)] = r;
+        s_inv = 1.0 / r;
       }
     }
     __syncthreads();
     if (s_fail) break;
-    const double rjj = A[tri_idx(j, j)];
-    for (int l = j + 1 + tid; l < n; l += nt) A[tri_idx(j, l)] /= rjj;
+    // row j of R by the pivot's reciprocal (one multiply per entry; the single FP64 pipe of
+    // this SM is the limit here, not the latency), then the trailing update
+    const double inv = s_inv;
+    for (int l = j + 1 + tid; l < n; l += nt) A[tri_idx(j, l)] *= inv;
     __syncthreads();
     const int m = n - j - 1;  // trailing k, l in (j, n)
     for (int e = tid; e < m * m; e += nt) {
@@ -418,9 +423,12 @@ cudaError_t launch_unpack(const double *Rpacked, int64_t n, double *R, int64_t l
 // R x = e_k by back substitution, x_k = 1 / r_kk, x_i = -(sum_{l=i+1..k} r_il x_l) / r_ii for
 // i = k-1 .. 0.  Then R X = I + F with |F| <= gamma |R| |X|: the computed inverse is
 // R^{-1} (I + F), a perturbation that stays on the right of a product V X, so V X = W (I + F)
-// keeps W's conditioning.  One warp per column, lanes split each dot product; the pivots'
-// reciprocals are formed once.
+// keeps W's conditioning.  One warp per column; lane t owns the partial sums of rows t, t + 32,
+// ... and adds r_il x_l to them as soon as x_l is known (the column-oriented form of the same
+// recurrence), so one step costs a broadcast, a multiply and a fused multiply-add in
+// sequence.  The pivots' reciprocals are formed once.
 constexpr int TRI_COLS = 8;  // columns (warps) per CTA
+constexpr int TRI_SLOTS = 4;  // rows per lane: n <= 128
 
 __global__ void __launch_bounds__(TRI_COLS * 32) k_tri_inv(const double *Rp, int n, double *Xp,
                                                          const DevStatus *st) {
@@ -435,16 +443,28 @@ __global__ void __launch_bounds__(TRI_COLS * 32) k_tri_inv(const double *Rp, int
   __syncthreads();
   const int lane = threadIdx.x & 31, k = blockIdx.x * TRI_COLS + (threadIdx.x >> 5);
   if (k >= n) return;
-  if (lane == 0) x[k] = rdiag[k];
-  __syncwarp();
-  for (int i = k - 1; i >= 0; --i) {
-    double acc = 0.0;
-    for (int l = i + 1 + lane; l <= k; l += 32) acc = fma(R[tri_idx(i, l)], x[l], acc);
+  const double xk = rdiag[k];
+  double acc[TRI_SLOTS];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[i] = -acc * rdiag[i];
-    __syncwarp();
+  for (int q = 0; q < TRI_SLOTS; ++q) {
+    const int i = lane + 32 * q;
+    acc[q] = i < k ? R[tri_idx(i, k)] * xk : 0.0;
   }
+  if (lane == 0) x[k] = xk;
+  for (int l = k - 1; l >= 0; --l) {
+    double mine = acc[0];
+#pragma unroll
+    for (int q = 1; q < TRI_SLOTS; ++q)
+      if ((l >> 5) == q) mine = acc[q];
+    const double xl = -__shfl_sync(0xffffffffu, mine, l & 31) * rdiag[l];
+    if (lane == 0) x[l] = xl;
+#pragma unroll
+    for (int q = 0; q < TRI_SLOTS; ++q) {
+      const int i = lane + 32 * q;
+      if (i < l) acc[q] = fma(R[tri_idx(i, l)], xl, acc[q]);
+    }
+  }
+  __syncwarp();
   for (int i = lane; i <= k; i += 32) Xp[tri_idx(i, k)] = x[i];
 }
 
