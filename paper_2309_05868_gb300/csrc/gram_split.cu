@@ -9,15 +9,17 @@
 // regions.  Region g' (64 columns of tensor memory) gathers the pairs (a, t) with 2a + t = g':
 // lanes 0-63 then hold D_g for g = g', lanes 64-127 hold g = g' + 1 (odd s).
 //
-// Groups go in pairs: the first takes its column maxima plus one bit of headroom as scales, the
-// second keeps those scales unless one of its columns outgrew them.  A pair with common scales
-// accumulates in the same regions (an event of 256 rows), so every D is a sum of at most
-// 4 x 256 digit products, |D| <= 2^22, exact in FP32.  With
+// Groups form events: the first group of an event takes its column maxima plus one bit of
+// headroom as scales, and the following groups keep those scales unless one of their columns
+// outgrew them, up to 8 groups.  An event's groups accumulate in the same regions (at most 1024
+// rows), so every D is a sum of at most 4 x 1024 digit products of at most 2^12, |D| <= 2^24,
+// exact in FP32.  With
 //   T_p(j, k) = sum_g' 2^(7 (7 - g')) D_g'(64p + j, k),
 // the event's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
-// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p / 64 is formed in 64-bit integers
-// (tc::recombine_g7), converted on the FP64 pipe and added to per-thread FP64 sums; one FP64
-// atomic per entry (j <= k) and parity at the end.
+// are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p / 256 is formed in 64-bit integers
+// (tc::recombine_g7w), converted on the FP64 pipe and added to per-thread FP64 sums; one FP64
+// atomic per entry (j <= k) and parity at the end.  Longer events mean fewer read-backs, and the
+// next event's products wait for a read-back to finish (tensor memory holds one event).
 //
 // One CTA per SM, persistent over its row range; warps specialise:
 //   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
@@ -26,7 +28,7 @@
 //     [32 h, 32 h + 32) with h = (w - 4) / 4) and keep the FP64 sums,
 //   warp 12 loads 32-row sub-tiles into a four-slot ring with bulk copies,
 //   warp 13 owns tensor memory and issues the MMAs (24 per 64-row tile), closing an event
-//     (commit to the recombination warps) after one group or a merged pair.
+//     (commit to the recombination warps) when the next group starts a new one.
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -36,6 +38,9 @@ namespace {
 using namespace tc;
 
 constexpr int GS_SUB = 32, GS_NP = 64, GS_GROUP = 128;
+// Groups per tensor-memory accumulation: 1024 rows keep every region within 4 x 1024 digit
+// products of at most 2^12, |D| <= 2^24, exact in FP32.
+constexpr int GS_EV_GROUPS = 8;
 constexpr int GS_THREADS = 448;
 constexpr int GW_LOAD = 12, GW_MMA = 13;
 constexpr uint32_t GS_TMEM_COLS = 512;
@@ -193,12 +198,13 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     if (lane == 0) {
       const uint64_t dA = umma_desc(smem_addr(slices), 128, 1024);
       const uint64_t dB = umma_desc(smem_addr(slices + GS_BUF), 128, 1024);
-      // Events: one tensor-memory accumulation = one group, or two when the second keeps the
-      // first's scales.  evt[8 + (ev & 3)] names the event's first group for the recombination.
-      int ev = 0, pending_g = -1;
+      // Events: one tensor-memory accumulation = one group, or up to GS_EV_GROUPS consecutive
+      // groups with common scales.  evt[8 + (ev & 3)] names the event's last group (whose scale
+      // slot the recombination reads).
+      int ev = 0, pending_g = -1, last_g = -1;
       bool ok = true;
       auto close_event = [&]() {
-        evt[8 + (ev & 3)] = pending_g;
+        evt[8 + (ev & 3)] = last_g;
         umma_commit(t_full);
         mbar_arrive(ev_bar);
         ++ev;
@@ -222,6 +228,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         uint64_t d = dA;
         asm volatile("" : "+l"(d));
         gram_issue_tile(tmem, d, !merge);
+        last_g = g;
         umma_commit(sle0);
         if (!mbar_wait_or_abort(slf0 + 8, g & 1, abort_flag)) {
           ok = false;
@@ -232,7 +239,6 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         asm volatile("" : "+l"(d));
         gram_issue_tile(tmem, d, false);
         umma_commit(sle0 + 8);
-        if (merge) close_event();
       }
       if (ok && pending_g >= 0) close_event();
       if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {
@@ -250,6 +256,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     // ------------------------------------------------------------------ scales and slices
     const int j = 16 * warp + (lane & 15), h = lane >> 4;
     const bool cj = j < n;
+    int ev_len = 0, n_scale_syncs = 0;  // the same in every slicer thread
     for (int g = 0; g < ngroups; ++g) {
       bool ok = true;
       for (int q = 0; q < 4 && ok; ++q) ok = mbar_wait_or_abort(full0 + 8 * q, g & 1, abort_flag);
@@ -273,29 +280,34 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
       }
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-      // Scales: the first group of a pair takes one bit of headroom; the second keeps the first's
-      // scales (so both accumulate in the same tensor-memory regions) unless a column outgrew them.
+      // Scales: the first group of an event takes one bit of headroom; the next ones keep its
+      // scales (so they accumulate in the same tensor-memory regions) unless a column outgrew
+      // them, up to GS_EV_GROUPS groups per event.
       const int Eg = scale_exp(mx);
       int E = Eg + 1;
-      if (g & 1) {
+      bool merge = false;
+      if (g > 0 && ev_len < GS_EV_GROUPS) {
         const int Eprev = colE[((g - 1) & 3) * GS_NP + j];
         const bool grows = __any_sync(0xffffffffu, cj && Eg > Eprev);
         if (lane == 0 && grows) atomicMax((int *)&evt[3 + g % 3], g + 1);
         __syncwarp();
         if (lane == 0) mbar_arrive(scale_bar);  // the four slicer warps meet here
-        if (!mbar_wait_or_abort(scale_bar, (g >> 1) & 1, abort_flag)) {
+        if (!mbar_wait_or_abort(scale_bar, (uint32_t)(n_scale_syncs & 1), abort_flag)) {
           if (lane == 0 && !*abort_flag) {
             *abort_flag = 1;
             status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
           }
           break;
         }
-        if (evt[3 + g % 3] != g + 1) E = Eprev;
+        ++n_scale_syncs;
+        merge = evt[3 + g % 3] != g + 1;
+        if (merge) E = Eprev;
       }
-      // four scale slots: a merged event reads its first group's slot until the slicers are two
-      // groups further on (they wait for the event's read-back before slicing the next pair)
+      ev_len = merge ? ev_len + 1 : 1;
+      // four scale slots: an event's read-back uses the slot of its last group, and the slicers
+      // cannot get further than two groups past that group before the read-back is done
       if (h == 0) colE[(g & 3) * GS_NP + j] = E;
-      if (warp == 0 && lane == 0) evt[g % 3] = (g & 1) && evt[3 + g % 3] != g + 1;  // merge with g - 1
+      if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
       // pass 2: the two 64-row tiles into slice buffers 0 and 1
       for (int tb = 0; tb < 2; ++tb) {
         if (!mbar_wait_or_abort(sle0 + 8 * tb, (g & 1) ^ 1, abort_flag)) {
@@ -370,7 +382,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       fence_after_sync();
       if (active) {
         const int *ce = colE + (g & 3) * GS_NP;
-        const int ebase = ce[j] - 53 - 7 * par;
+        const int ebase = ce[j] - 51 - 7 * par;
 #pragma unroll
         for (int h4 = 0; h4 < 8; ++h4) {
           const int k0 = 32 * kh + 4 * h4;
@@ -382,8 +394,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           tmem_regs_ready(v);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const long long t = recombine_g7(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
-            const double y = int_times_pow2_cvt(t, ebase + ce[k0 + c]);  // T / 64 (|T| < 2^69)
+            const long long t = recombine_g7w(v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c], v[7][c]);
+            const double y = int_times_pow2_cvt(t, ebase + ce[k0 + c]);  // T / 256 (|T| < 2^71)
             S[4 * h4 + c] += y;
           }
         }

@@ -331,29 +331,25 @@ __device__ __forceinline__ long long recombine8(uint32_t d0, uint32_t d1, uint32
   return (th << (28 - SH)) + (tl >> SH);
 }
 
-// T / 64 from eight region accumulators of 7-bit-digit products, T = sum_g 2^(7 (7 - g)) D_g,
-// each D_g an exact FP32 integer with |D_g| <= 2^22 and |D_0| <= 2^19 (a leading digit in
-// every product of region 0), |T| < 2^69.  Regions 0-5 go through the 1.5 * 2^23 offset (bit
-// pattern 0x4B400000 + D_g); regions 6 and 7 are merged by one FP32 fused multiply-add
-// (|r| < 2^30) and taken at a resolution of 2^8 through the 1.5 * 2^31 offset (an error of at
-// most 2^7 units of region 7).  The patterns are summed modulo 2^64, regions 0 and 1 in the
-// high word.
-__device__ __forceinline__ long long recombine_g7(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
-                                                  uint32_t d5, uint32_t d6, uint32_t d7) {
-  constexpr uint32_t O23 = 0x4B400000u, O31 = 0x4F400000u;  // 1.5 * 2^23, 1.5 * 2^31
-  constexpr uint32_t C_HI = (uint32_t)(O23 * 2048ull + O23 * 16ull);
-  constexpr unsigned long long C_LO = (unsigned long long)O23 * (1ull << 29) + (unsigned long long)O23 * (1ull << 22) +
-                                      (unsigned long long)O23 * (1ull << 15) + (unsigned long long)O23 * 256ull +
-                                      (unsigned long long)O31 * 4ull;
-  const float r = __fmaf_rn(__uint_as_float(d6), 128.0f, __uint_as_float(d7));
-  const uint32_t qr = __float_as_uint(__fadd_rn(r, 3221225472.0f));
-  const uint32_t hw = acc_bits(d0) * 2048u + acc_bits(d1) * 16u - C_HI;  // modulo 2^32
-  unsigned long long lw = mad_wide(qr, 4u, 0ULL - C_LO);
-  lw = mad_wide(acc_bits(d5), 1u << 8, lw);
-  lw = mad_wide(acc_bits(d4), 1u << 15, lw);
-  lw = mad_wide(acc_bits(d3), 1u << 22, lw);
-  lw = mad_wide(acc_bits(d2), 1u << 29, lw);
-  return (long long)(lw + ((unsigned long long)hw << 32));
+// T / 256 from eight region accumulators of 7-bit-digit products over up to 1024 rows,
+// T = sum_g 2^(7 (7 - g)) D_g, each D_g an exact FP32 integer with |D_g| <= 2^24,
+// |D_1| <= 2^22 and |D_0| <= 2^21 (the leading digits are at most 32 in magnitude).  The
+// regions are converted exactly to int32 and combined: regions 0 and 1 in the high word
+// (D_0 2^9 + D_1 2^2 < 2^31), the rest in a 64-bit sum; regions 6 and 7 enter as
+// floor((128 D_6 + D_7) / 256), an error below one unit of T / 256.
+__device__ __forceinline__ long long recombine_g7w(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3, uint32_t d4,
+                                                   uint32_t d5, uint32_t d6, uint32_t d7) {
+  const int D0 = __float2int_rz(__uint_as_float(d0)), D1 = __float2int_rz(__uint_as_float(d1));
+  const int D2 = __float2int_rz(__uint_as_float(d2)), D3 = __float2int_rz(__uint_as_float(d3));
+  const int D4 = __float2int_rz(__uint_as_float(d4)), D5 = __float2int_rz(__uint_as_float(d5));
+  const int D6 = __float2int_rz(__uint_as_float(d6)), D7 = __float2int_rz(__uint_as_float(d7));
+  const int hw = D0 * 512 + D1 * 4;
+  long long lw = ((long long)D6 * 128 + D7) >> 8;
+  lw += (long long)D5 * 64;
+  lw += (long long)D4 * (1LL << 13);
+  lw += (long long)D3 * (1LL << 20);
+  lw += (long long)D2 * (1LL << 27);
+  return (long long)((unsigned long long)lw + ((unsigned long long)(unsigned)hw << 32));
 }
 
 // (double) t * 2^e for |t| < 2^63 and a result in the normal range (0 for t == 0), through the

@@ -189,3 +189,28 @@ def test_rand_cholqr_with_split_solves_meets_the_targets(kappa):
     Rc2 = cholesky(W2.T @ W2, lower=False)
     Q2 = solve_triangular(Rc2, W2.T, trans="T").T
     assert np.linalg.norm(V - Q2 @ (Rc2 @ Rs)) / np.linalg.norm(V) <= 1e-15
+
+
+def test_gram_recombination_bounds():
+    """The Gram's read-back (events of up to 1024 rows, 7-bit digits): every region is an exact
+    FP32 integer (|D| <= 2^24; |D_1| <= 2^22, |D_0| <= 2^21 because leading digits are at most
+    32), the high word D_0 2^9 + D_1 2^2 fits in 32 bits, and the int64 result is T / 256 to
+    within one unit, for random and extreme region values."""
+    rng = synthetic.rng(21)
+    bounds = [2 ** 21, 2 ** 22] + [2 ** 24] * 6
+    # extreme digit products reach the bounds: 4 pairs x 1024 rows x 64 x 64
+    assert 4 * 1024 * 64 * 64 == 2 ** 24 and 1024 * 32 * 64 == 2 ** 21 and 1024 * 64 * 64 == 2 ** 22
+    for trial in range(2000):
+        if trial < 16:
+            D = [int(b) * (1 if (trial >> (i % 4)) & 1 else -1) for i, b in enumerate(bounds)]
+        else:
+            D = [int(rng.integers(-b, b + 1)) for b in bounds]
+        for d in D:
+            assert float(np.float32(d)) == d
+        hw = D[0] * 512 + D[1] * 4
+        assert -2 ** 31 <= hw < 2 ** 31
+        lw = ((D[6] * 128 + D[7]) >> 8) + D[5] * 64 + D[4] * 2 ** 13 + D[3] * 2 ** 20 + D[2] * 2 ** 27
+        t = (lw + (hw << 32)) % 2 ** 64
+        t = t - 2 ** 64 if t >= 2 ** 63 else t
+        exact = sum(D[g] * 2 ** (7 * (7 - g)) for g in range(8))
+        assert abs(t * 256 - exact) < 256
