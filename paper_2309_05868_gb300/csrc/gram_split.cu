@@ -1,7 +1,7 @@
 // gram_split.cu -- G = W^T W (Algorithm 2 step 1, the Gram of each Cholesky pass) for n <= 64
 // from exact split products on the tensor cores.
 //
-// Rows are taken in groups of 128.  Column j of a group gets a scale 2^E_j > max_r |w_rj| and
+// Rows are taken in groups of 64.  Column j of a group gets a scale 2^E_j > max_r |w_rj| and
 // w_rj = 2^(E_j - 54) X_rj up to truncation, with X_rj = trunc(w_rj 2^(54 - E_j)) written in
 // eight balanced 7-bit digits d_p (tc.cuh; slice s = 7 - p).  Slices s = 2a and 2a + 1 of all
 // 64 columns stack into the 128 rows of A-tile a (TMEM lane 64 * (s & 1) + j); slices t of the
@@ -11,7 +11,7 @@
 //
 // Groups form events: the first group of an event takes its column maxima plus one bit of
 // headroom as scales, and the following groups keep those scales unless one of their columns
-// outgrew them, up to 8 groups.  An event's groups accumulate in the same regions (at most 1024
+// outgrew them, up to 16 groups.  An event's groups accumulate in the same regions (at most 1024
 // rows), so every D is a sum of at most 4 x 1024 digit products of at most 2^12, |D| <= 2^24,
 // exact in FP32.  With
 //   T_p(j, k) = sum_g' 2^(7 (7 - g')) D_g'(64p + j, k),
@@ -23,11 +23,12 @@
 //
 // One CTA per SM, persistent over its row range; warps specialise:
 //   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
-//     two 64-row tiles into digit slices (second pass; two slice buffers, 64 KB each),
+//     group into digit slices (second pass; two 64 KB slice buffers, alternating groups),
 //   warps 4-11 read the regions back (warp w: TMEM lanes 32 (w & 3) .., columns k in
 //     [32 h, 32 h + 32) with h = (w - 4) / 4) and keep the FP64 sums,
-//   warp 12 loads 32-row sub-tiles into a four-slot ring with bulk copies,
-//   warp 13 owns tensor memory and issues the MMAs (24 per 64-row tile), closing an event
+//   warp 12 loads 32-row sub-tiles into a four-slot ring with bulk copies (two groups in
+//     flight, so a group's rows arrive while the previous one is cut),
+//   warp 13 owns tensor memory and issues the MMAs (24 per group), closing an event
 //     (commit to the recombination warps) when the next group starts a new one.
 #include "common.cuh"
 #include "tc.cuh"
@@ -37,10 +38,10 @@ namespace rq {
 namespace {
 using namespace tc;
 
-constexpr int GS_SUB = 32, GS_NP = 64, GS_GROUP = 128;
+constexpr int GS_SUB = 32, GS_NP = 64, GS_GROUP = 64;
 // Groups per tensor-memory accumulation: 1024 rows keep every region within 4 x 1024 digit
 // products of at most 2^12, |D| <= 2^24, exact in FP32.
-constexpr int GS_EV_GROUPS = 8;
+constexpr int GS_EV_GROUPS = 16;
 constexpr int GS_THREADS = 448;
 constexpr int GW_LOAD = 12, GW_MMA = 13;
 constexpr uint32_t GS_TMEM_COLS = 512;
@@ -150,11 +151,13 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
 
   if (warp == GW_LOAD) {
     // ------------------------------------------------------------------ loader
+    // group g uses slots 2 (g & 1) and 2 (g & 1) + 1: two groups in flight
     int last_g[4] = {-1, -1, -1, -1};
     for (int g = 0; g < ngroups && !*abort_flag; ++g) {
       bool ok = true;
-      for (int q = 0; q < 4; ++q) {
-        if (!mbar_wait_or_abort(empty0 + 8 * q, (g & 1) ^ 1, abort_flag)) {
+      for (int qq = 0; qq < 2; ++qq) {
+        const int q = 2 * (g & 1) + qq;
+        if (!mbar_wait_or_abort(empty0 + 8 * q, ((g >> 1) & 1) ^ 1, abort_flag)) {
           if (lane == 0 && !*abort_flag) {
             *abort_flag = 1;
             status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           ok = false;
           break;
         }
-        const int64_t r0 = r_begin + (int64_t)g * GS_GROUP + GS_SUB * q;
-        const int cnt = sub_rows(g, q);
+        const int64_t r0 = r_begin + (int64_t)g * GS_GROUP + GS_SUB * qq;
+        const int cnt = sub_rows(g, qq);
         uint8_t *dst = stage + (size_t)q * GS_STAGE;
         const uint32_t fb = full0 + 8 * q;
         if (cnt > 0 && load_mode == GLOAD_BLOCK) {
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     }
     if (lane == 0)
       for (int q = 0; q < 4; ++q)
-        if (last_g[q] >= 0) mbar_wait(full0 + 8 * q, last_g[q] & 1);
+        if (last_g[q] >= 0) mbar_wait(full0 + 8 * q, (last_g[q] >> 1) & 1);
   } else if (warp == GW_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -211,7 +214,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         pending_g = -1;
       };
       for (int g = 0; g < ngroups && ok; ++g) {
-        if (!mbar_wait_or_abort(slf0, g & 1, abort_flag)) {
+        const int b = g & 1;  // slice buffer
+        if (!mbar_wait_or_abort(slf0 + 8 * b, (g >> 1) & 1, abort_flag)) {
           ok = false;
           break;
         }
@@ -225,20 +229,11 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           pending_g = g;
         }
         fence_after_sync();
-        uint64_t d = dA;
+        uint64_t d = b ? dB : dA;
         asm volatile("" : "+l"(d));
         gram_issue_tile(tmem, d, !merge);
         last_g = g;
-        umma_commit(sle0);
-        if (!mbar_wait_or_abort(slf0 + 8, g & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        fence_after_sync();
-        d = dB;
-        asm volatile("" : "+l"(d));
-        gram_issue_tile(tmem, d, false);
-        umma_commit(sle0 + 8);
+        umma_commit(sle0 + 8 * b);
       }
       if (ok && pending_g >= 0) close_event();
       if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {
@@ -258,8 +253,9 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     const bool cj = j < n;
     int ev_len = 0, n_scale_syncs = 0;  // the same in every slicer thread
     for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1, q = 2 * b + h;  // slice buffer, this lane's staged sub-tile
       bool ok = true;
-      for (int q = 0; q < 4 && ok; ++q) ok = mbar_wait_or_abort(full0 + 8 * q, g & 1, abort_flag);
+      for (int qq = 0; qq < 2 && ok; ++qq) ok = mbar_wait_or_abort(full0 + 8 * (2 * b + qq), (g >> 1) & 1, abort_flag);
       if (!ok) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
@@ -267,17 +263,14 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
         break;
       }
-      // pass 1: column scale over the group's 128 rows (this lane: sub-tiles h and 2 + h)
+      // pass 1: column scale over the group's 64 rows (this lane: sub-tile h)
+      const int cnt = sub_rows(g, h);
+      const uint8_t *src = stage + (size_t)q * GS_STAGE + 8 * j;
       int mx = 0;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int q = 2 * half + h, cnt = sub_rows(g, q);
-        const uint8_t *src = stage + (size_t)q * GS_STAGE + 8 * j;
 #pragma unroll 8
-        for (int r = 0; r < GS_SUB; ++r) {
-          const unsigned long long b = (cj && r < cnt) ? *(const unsigned long long *)(src + r * 512) : 0ULL;
-          mx = max(mx, g_expfield<IN_DF>(b));
-        }
+      for (int r = 0; r < GS_SUB; ++r) {
+        const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(src + r * 512) : 0ULL;
+        mx = max(mx, g_expfield<IN_DF>(bits));
       }
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
       // Scales: the first group of an event takes one bit of headroom; the next ones keep its
@@ -305,18 +298,14 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       }
       ev_len = merge ? ev_len + 1 : 1;
       // four scale slots: an event's read-back uses the slot of its last group, and the slicers
-      // cannot get further than two groups past that group before the read-back is done
+      // cannot get further than three groups past that group before the read-back is done
       if (h == 0) colE[(g & 3) * GS_NP + j] = E;
       if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
-      // pass 2: the two 64-row tiles into slice buffers 0 and 1
-      for (int tb = 0; tb < 2; ++tb) {
-        if (!mbar_wait_or_abort(sle0 + 8 * tb, (g & 1) ^ 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        const int q = 2 * tb + h, cnt = sub_rows(g, q);
-        const uint8_t *src = stage + (size_t)q * GS_STAGE + 8 * j;
-        uint8_t *buf = slices + (size_t)tb * GS_BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
+      // pass 2: the group's 64 rows into slice buffer b
+      if (!mbar_wait_or_abort(sle0 + 8 * b, ((g >> 1) & 1) ^ 1, abort_flag)) {
+        ok = false;
+      } else {
+        uint8_t *buf = slices + (size_t)b * GS_BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
 #pragma unroll 1
         for (int r0 = 0; r0 < GS_SUB; r0 += 8) {
           uint32_t w[4][NDIG];
@@ -337,12 +326,12 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(empty0 + 8 * (2 * tb));
-          mbar_arrive(empty0 + 8 * (2 * tb + 1));
+          mbar_arrive(empty0 + 8 * (2 * b));
+          mbar_arrive(empty0 + 8 * (2 * b + 1));
         }
         fence_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(slf0 + 8 * tb);
+        if (lane == 0) mbar_arrive(slf0 + 8 * b);
       }
       if (!ok) {
         if (lane == 0 && !*abort_flag) {
