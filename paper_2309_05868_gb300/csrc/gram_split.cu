@@ -263,75 +263,84 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
         break;
       }
-      // pass 1: column scale over the group's 64 rows (this lane: sub-tile h)
+      // Scales.  The first group of an event takes its column maxima (a first pass over the staged
+      // rows) plus one bit of headroom; a later group is cut with the event's scales straight
+      // away and keeps them unless one of its values reached 2^E, in which case it is cut
+      // again with its own maxima and starts a new event (up to GS_EV_GROUPS groups per event).
       const int cnt = sub_rows(g, h);
       const uint8_t *src = stage + (size_t)q * GS_STAGE + 8 * j;
-      int mx = 0;
+      const bool spec = g > 0 && ev_len < GS_EV_GROUPS;
+      int E;
+      if (spec) {
+        E = colE[((g - 1) & 3) * GS_NP + j];
+      } else {
+        int mx = 0;
 #pragma unroll 8
-      for (int r = 0; r < GS_SUB; ++r) {
-        const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(src + r * 512) : 0ULL;
-        mx = max(mx, g_expfield<IN_DF>(bits));
-      }
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-      // Scales: the first group of an event takes one bit of headroom; the next ones keep its
-      // scales (so they accumulate in the same tensor-memory regions) unless a column outgrew
-      // them, up to GS_EV_GROUPS groups per event.
-      const int Eg = scale_exp(mx);
-      int E = Eg + 1;
-      bool merge = false;
-      if (g > 0 && ev_len < GS_EV_GROUPS) {
-        const int Eprev = colE[((g - 1) & 3) * GS_NP + j];
-        const bool grows = __any_sync(0xffffffffu, cj && Eg > Eprev);
-        if (lane == 0 && grows) atomicMax((int *)&evt[3 + g % 3], g + 1);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(scale_bar);  // the four slicer warps meet here
-        if (!mbar_wait_or_abort(scale_bar, (uint32_t)(n_scale_syncs & 1), abort_flag)) {
-          if (lane == 0 && !*abort_flag) {
-            *abort_flag = 1;
-            status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-          }
-          break;
+        for (int r = 0; r < GS_SUB; ++r) {
+          const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(src + r * 512) : 0ULL;
+          mx = max(mx, g_expfield<IN_DF>(bits));
         }
-        ++n_scale_syncs;
-        merge = evt[3 + g % 3] != g + 1;
-        if (merge) E = Eprev;
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        E = scale_exp(mx) + 1;
       }
-      ev_len = merge ? ev_len + 1 : 1;
-      // four scale slots: an event's read-back uses the slot of its last group, and the slicers
-      // cannot get further than three groups past that group before the read-back is done
-      if (h == 0) colE[(g & 3) * GS_NP + j] = E;
-      if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
-      // pass 2: the group's 64 rows into slice buffer b
       if (!mbar_wait_or_abort(sle0 + 8 * b, ((g >> 1) & 1) ^ 1, abort_flag)) {
         ok = false;
       } else {
         uint8_t *buf = slices + (size_t)b * GS_BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
+        bool merge = false;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          // pass 2: the group's 64 rows into slice buffer b (and this lane's largest exponent)
+          int mxe = 0;
 #pragma unroll 1
-        for (int r0 = 0; r0 < GS_SUB; r0 += 8) {
-          uint32_t w[4][NDIG];
+          for (int r0 = 0; r0 < GS_SUB; r0 += 8) {
+            uint32_t w[4][NDIG];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int ra = r0 + 2 * u, rb = ra + 1;
-            const unsigned long long ba = (cj && ra < cnt) ? *(const unsigned long long *)(src + ra * 512) : 0ULL;
-            const unsigned long long bb = (cj && rb < cnt) ? *(const unsigned long long *)(src + rb * 512) : 0ULL;
-            if (IN_DF)
-              digits2(g_fix<IN_DF>(ba, E), g_fix<IN_DF>(bb, E), w[u]);
-            else
-              digits2_biased(fix54_biased<DIG_BIAS>(ba, E), fix54_biased<DIG_BIAS>(bb, E), w[u]);
+            for (int u = 0; u < 4; ++u) {
+              const int ra = r0 + 2 * u, rb = ra + 1;
+              const unsigned long long ba = (cj && ra < cnt) ? *(const unsigned long long *)(src + ra * 512) : 0ULL;
+              const unsigned long long bb = (cj && rb < cnt) ? *(const unsigned long long *)(src + rb * 512) : 0ULL;
+              mxe = max(mxe, max(g_expfield<IN_DF>(ba), g_expfield<IN_DF>(bb)));
+              if (IN_DF)
+                digits2(g_fix<IN_DF>(ba, E), g_fix<IN_DF>(bb, E), w[u]);
+              else
+                digits2_biased(fix54_biased<DIG_BIAS>(ba, E), fix54_biased<DIG_BIAS>(bb, E), w[u]);
+            }
+            const int kg = (GS_SUB * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the tile
+#pragma unroll
+            for (int p = 0; p < NDIG; ++p)
+              *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * GS_SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
           }
-          const int kg = (GS_SUB * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the tile
-#pragma unroll
-          for (int p = 0; p < NDIG; ++p)
-            *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * GS_SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
+          if (!spec || attempt == 1) break;
+          // did any value of the group reach the event's scale?  (the four slicer warps meet)
+          const bool over = __any_sync(0xffffffffu, cj && mxe >= E + 1023);
+          if (lane == 0 && over) atomicMax((int *)&evt[3 + g % 3], g + 1);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(scale_bar);
+          if (!mbar_wait_or_abort(scale_bar, (uint32_t)(n_scale_syncs & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          ++n_scale_syncs;
+          merge = evt[3 + g % 3] != g + 1;
+          if (merge) break;
+          mxe = max(mxe, __shfl_xor_sync(0xffffffffu, mxe, 16));
+          E = scale_exp(mxe) + 1;  // cut again with the group's own scales
         }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(empty0 + 8 * (2 * b));
-          mbar_arrive(empty0 + 8 * (2 * b + 1));
+        if (ok) {
+          ev_len = merge ? ev_len + 1 : 1;
+          // four scale slots: an event's read-back uses the slot of its last group, and the
+          // slicers cannot get further than three groups past that group before it is done
+          if (h == 0) colE[(g & 3) * GS_NP + j] = E;
+          if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(empty0 + 8 * (2 * b));
+            mbar_arrive(empty0 + 8 * (2 * b + 1));
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(slf0 + 8 * b);
         }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(slf0 + 8 * b);
       }
       if (!ok) {
         if (lane == 0 && !*abort_flag) {

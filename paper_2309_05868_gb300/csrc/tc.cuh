@@ -420,7 +420,8 @@ template <unsigned long long BIAS = BIAS8>
 __device__ __forceinline__ unsigned long long fix54_biased(unsigned long long b, int E) {
   const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
   const int ef = (int)((hi >> 20) & 0x7ffu);
-  const int amt = min(1022 + E - ef, 63);
+  // a value at or above 2^E (only possible where a caller guesses E) shifts everything out
+  const unsigned amt = min((unsigned)(1022 + E - ef), 63u);
   const unsigned long long m2 = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 33) | ((unsigned long long)lo << 1);
   const unsigned long long v = m2 >> amt;
   const unsigned long long sgn = (unsigned long long)((long long)b >> 63);
