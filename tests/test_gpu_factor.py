@@ -315,3 +315,26 @@ def test_single_gaussian_kind(rq):
     assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10
     with pytest.raises(rq.RandQRError):  # s1 != m
         rq.randqr_factor(torch.from_numpy(V).cuda(), 544, s2, seed=0, ctx=ctx)
+
+
+def test_tensor_core_gram_rows_of_changing_magnitude(rq):
+    # 64-row blocks scaled by 1, 2^3, 2^6, 2^9, 2^12, 1, ...: later groups of an event outgrow the
+    # event's column scales (cut again with their own) or fall far below them; both Gram paths
+    # and the oracle agree
+    m, n = 50000, 32
+    V = synthetic.make_v(m, n, 10.0, seed=11)
+    V *= np.ldexp(1.0, 3 * ((np.arange(m) // 64) % 5))[:, None]
+    Vd = torch.from_numpy(V).cuda()
+    Qo, Ro = oracle.cholqr2(V)
+    for tc in (True, False):
+        ctx = rq.Context(0)
+        ctx.set_tensor_cores(tc)
+        Q, R, _ = rq.randqr_cholqr2(Vd, ctx=ctx)
+        Q, R = Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+        assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10  # kappa(V) ~ 1e4: u kappa ~ 1e-12
+        Q, R, _ = rq.randqr_factor(Vd, seed=2, ctx=ctx)
+        Q, R = Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
+        assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10
+        ctx.close()
