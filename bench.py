@@ -47,8 +47,8 @@ def roofline_model(kind, n):
 # DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
 # m = 2^20, n = 64 with --set full, divided by m), scaled to a launch by the rows it processes.
 # Valid for n = 64 and the kernels as captured.
-MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.0e6 + 485.0e6) / 1048576,
-                                   "gram_tc": (537.03e6 + 3.31e6) / 1048576}
+MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.01e6 + 484.83e6) / 1048576,
+                                   "gram_tc": (537.01e6 + 3.06e6) / 1048576}
 
 
 def kernel_roofline(kind, avg_ms, m, n):
