@@ -217,7 +217,7 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
     }
     RQ_CUDA(cudaMemsetAsync(w.Ws, 0, sizeof(double) * (size_t)(s2 * n), s));
     RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
-      return rq::launch_sketch_gemm(S2p, B, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
+      return rq::launch_sketch_gemm(S2p, B, s2, s1, n, w.Ws, ctx->use_tc, ctx->num_sms, ctx->status_dev, s);
     }));
     if (do_hhqr)
       RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));
@@ -229,7 +229,7 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
     return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, row0, w.W1, ctx->num_sms, ctx->status_dev, s);
   }));
   RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
-    return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
+    return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->use_tc, ctx->num_sms, ctx->status_dev, s);
   }));
   if (do_hhqr)
     RQ_CUDA(timed(ctx, s, rq::K_HHQR, [&] { return rq::launch_hhqr(w.Ws, s2, n, w.Rs, w.hq, ctx->status_dev, s); }));

@@ -152,9 +152,14 @@ cudaError_t launch_rad_gen(uint64_t seed, int64_t s2, int64_t s1, double *S2, cu
 cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
                               uint64_t seed, int64_t row0, double *W1, int num_sms, const DevStatus *st,
                               cudaStream_t s);
+// Ws += S2 W1 ((s2 x s1)(s1 x n), Ws zeroed by the caller): split products on the tensor cores
+// for n <= 64 when use_tc, else FP64 tiles on the CUDA cores
 cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, int64_t s1,
-                               int64_t n, double *Ws, int num_sms, const DevStatus *st,
+                               int64_t n, double *Ws, bool use_tc, int num_sms, DevStatus *st,
                                cudaStream_t s);
+bool sketch_oz_supported(int64_t n);
+cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
+                             int64_t n, double *C, int num_sms, DevStatus *st, cudaStream_t s);
 // Householder R of the rows x n sketch; with scratch (hhqr_scratch_doubles) and n >= 32 it runs
 // on several co-resident CTAs, otherwise on one.
 size_t hhqr_scratch_doubles(int64_t rows, int64_t n);

@@ -191,8 +191,9 @@ __global__ void __launch_bounds__(256) k_sketch_gemm(const double *__restrict__ 
 }
 
 cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, int64_t s1,
-                               int64_t n, double *Ws, int num_sms, const DevStatus *st,
+                               int64_t n, double *Ws, bool use_tc, int num_sms, DevStatus *st,
                                cudaStream_t s) {
+  if (use_tc && sketch_oz_supported(n)) return launch_sketch_oz(S2, s1, W1, n, s2, s1, n, Ws, num_sms, st, s);
   const int64_t tiles = ceil_div(s2, GB) * ceil_div(n, GB);
   int64_t split = std::max<int64_t>(1, (2 * (int64_t)num_sms) / tiles);
   split = std::min<int64_t>(split, ceil_div(s1, GK));

@@ -79,7 +79,7 @@ extern "C" randqr_status randqr_sketch_static(const double *V, int64_t m, int64_
       cudaMemsetAsync(Ws, 0, sizeof(double) * (size_t)(s2 * n), s) != cudaSuccess ||
       rq::launch_cs_scatter(V, m, n, ldv, s1, seed, 0, slot.w1, slot.num_sms, slot.status, s) !=
           cudaSuccess ||
-      rq::launch_sketch_gemm(S2, slot.w1, s2, s1, n, Ws, slot.num_sms, slot.status, s) !=
+      rq::launch_sketch_gemm(S2, slot.w1, s2, s1, n, Ws, true, slot.num_sms, slot.status, s) !=
           cudaSuccess) {
     cudaGetLastError();
     return RANDQR_ERR_CUDA;

@@ -119,3 +119,75 @@ def test_rand_cholqr_with_rademacher_sketch_kind(rq):
     assert (Qg - Qg2).abs().max().item() <= 1e-12
     with pytest.raises(rq.RandQRError):
         ctx.set_sketch_kind(7)
+
+
+# ---- the Gaussian sketch GEMM as split products on the tensor cores (n <= 64) ------------
+
+def _gaussian_only_ctx(rq, tensor_cores=True):
+    ctx = rq.Context(0)
+    ctx.set_sketch_kind(rq.SKETCH_GAUSSIAN_ONLY)  # Ws = S2 V: the GEMM alone, K = m
+    ctx.set_tensor_cores(tensor_cores)
+    return ctx
+
+
+@pytest.mark.parametrize("m,n,s2", [(64, 1, 1), (1037, 5, 130), (4099, 33, 257), (20000, 64, 64),
+                                    (70001, 64, 300)])
+def test_sketch_gemm_exact_on_integers(rq, m, n, s2):
+    # +-1 S2 and integer V: every digit product and every sum is an exact integer, so the
+    # split product equals S2 V bit for bit (ragged chunks of K, ragged 128-row tiles)
+    V = synthetic.integer_matrix(m, n, bound=2 ** 12, seed=m % 97)
+    S2 = np.where(synthetic.rng(s2 + 5).random((s2, m)) < 0.5, -1.0, 1.0)
+    ctx = _gaussian_only_ctx(rq)
+    Ws = rq.randqr_sketch(torch.from_numpy(V).cuda(), m, s2, S2=torch.from_numpy(S2).cuda(), ctx=ctx)
+    np.testing.assert_array_equal(Ws.cpu().numpy(), S2 @ V)  # integer sums below 2^53: exact
+
+
+def _split_product_bound(S2, V, chunk=64):
+    # The split product's error for chunk c of K: each term is cut relative to the chunk's
+    # largest |a_ik| and |b_kj| (scales 2^E < 2 max), truncation 2^-54 of the scale on each
+    # factor and the dropped digit pairs below 2^-58 of the product of the scales; then one
+    # rounding per chunk and the FP64 sum of the chunks.
+    s2, m = S2.shape
+    bound = np.zeros((s2, V.shape[1]))
+    for c0 in range(0, m, chunk):
+        a = np.abs(S2[:, c0:c0 + chunk]).max(axis=1)
+        b = np.abs(V[c0:c0 + chunk]).max(axis=0)
+        L = min(chunk, m - c0)
+        bound += np.outer(2 * a, 2 * b) * L * (2 * 2.0 ** -54 + 2.0 ** -58)
+    nchunks = -(-m // chunk)
+    return bound + (nchunks + 1) * 2.0 ** -52 * (np.abs(S2) @ np.abs(V))
+
+
+@pytest.mark.parametrize("m,n,s2", [(3000, 16, 64), (9001, 64, 130)])
+def test_sketch_gemm_within_split_bound(rq, m, n, s2):
+    # rows of V spread over 2^-60 .. 2^60 and a Gaussian S2: the result against S2 V in
+    # extended precision, within the split product's bound, for the tensor-core and the
+    # CUDA-core GEMM alike
+    rng = synthetic.rng(m)
+    V = rng.standard_normal((m, n)) * np.exp2(rng.integers(-60, 61, size=(m, 1)).astype(float))
+    S2 = oracle.gauss_sketch(3, s2, m)
+    exact = (S2.astype(np.longdouble) @ V.astype(np.longdouble)).astype(np.float64)
+    bound = _split_product_bound(S2, V)
+    for tc in (True, False):
+        ctx = _gaussian_only_ctx(rq, tc)
+        Ws = rq.randqr_sketch(torch.from_numpy(V).cuda(), m, s2, S2=torch.from_numpy(S2).cuda(), ctx=ctx)
+        err = np.abs(Ws.cpu().numpy() - exact)
+        assert (err <= bound).all(), (tc, (err / bound).max())
+
+
+@pytest.mark.parametrize("n", [8, 64])
+def test_sketch_at_paper_sizes_within_product_bound(rq, n):
+    # the paper's multisketch sizes (Sec. 6.2): s1 odd for n = 64 (34279), so the rows of S2
+    # start at every alignment
+    m = 60000
+    s1, s2 = synthetic.paper_multisketch_sizes(n)
+    V = synthetic.make_v(m, n, 1e8, seed=n)
+    S2 = oracle.gauss_sketch(4, s2, s1)
+    Ws = rq.randqr_sketch(torch.from_numpy(V).cuda(), s1, s2, seed=5, S2=torch.from_numpy(S2).cuda()).cpu().numpy()
+    W1 = oracle.countsketch(V, s1, 5)
+    Wo = oracle.gemm(S2, W1)
+    b, _ = oracle.cs_hash(5, m, s1)
+    absW1 = np.zeros((s1, n))
+    np.add.at(absW1, b, np.abs(V))
+    bound = _split_product_bound(S2, W1) + 2 * (s1 + m / s1 + 8) * 2.0 ** -53 * (np.abs(S2) @ absW1)
+    assert (np.abs(Ws - Wo) <= bound).all()
