@@ -164,7 +164,12 @@ randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind);
  * W1 = S1 V is formed in the context's workspace by a scatter-add of V's rows (CountSketch
  * with `seed`), then Ws = S2 W1.  S2 may be NULL: the context then uses (and caches) the
  * sketch randqr_gauss_sketch would give for seed + 1.  Requires 1 <= n <= s2 <= s1,
- * m >= 1, ldv >= n. */
+ * m >= 1, ldv >= n.
+ * Accuracy of Ws = S2 W1: with the tensor cores on (the default) and n <= 64, the product is
+ * formed from exact integer digit products over chunks of 64 along s1; each term carries an
+ * error below 2^-53 of the chunk's largest |S2| entry in its row times the chunk's largest
+ * |W1| entry in its column, and integer W1 with +-1 S2 gives the exact result.  Otherwise an
+ * FP64 GEMM (error below (s1 / splits + splits) u |S2| |W1|). */
 randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                             int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                             const double *S2, double *Ws, void *stream);
