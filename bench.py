@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--m", type=int, default=2**23)
     p.add_argument("--n", type=int, default=64)
     p.add_argument("--kappa", type=float, default=1e12)
+    p.add_argument("--s1", type=int, default=0, help="CountSketch size (default 2 (n^2 + n))")
+    p.add_argument("--s2", type=int, default=0, help="Gaussian sketch size (default 4 n)")
     p.add_argument("--prec", default="fp64", choices=["fp64", "f32x2"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, baselines, CPU baseline (quick runs)")
@@ -98,8 +100,15 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def sketch_sizes(a):
+    """(s1, s2) of the run: the method's 2 (n^2 + n) and 4 n unless given."""
+    d1, d2 = 2 * (a.n * a.n + a.n), 4 * a.n
+    return (a.s1 or d1), (a.s2 or d2)
+
+
 def workload_name(a):
-    return f"rand_cholQR m={a.m} n={a.n} kappa={a.kappa:g} s1={2*(a.n*a.n+a.n)} s2={4*a.n}"
+    s1, s2 = sketch_sizes(a)
+    return f"rand_cholQR m={a.m} n={a.n} kappa={a.kappa:g} s1={s1} s2={s2}"
 
 
 # ---------------------------------------------------------------------------------------
@@ -153,10 +162,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, single-threaded, on a bounded row sample
 # ---------------------------------------------------------------------------------------
-def cpu_baseline(n, kappa, rows):
+def cpu_baseline(n, kappa, rows, s1, s2):
     import oracle
     import synthetic
-    s1, s2 = synthetic.default_sketch_sizes(n)
     V = synthetic.make_v(rows, n, kappa, seed=0)
     S2 = oracle.gauss_sketch(1, s2, s1)
     t0 = time.perf_counter()
@@ -175,7 +183,7 @@ def run_reference(a):
     import oracle
     import synthetic
     rows = 1 << 16
-    s1, s2 = synthetic.default_sketch_sizes(a.n)
+    s1, s2 = sketch_sizes(a)
     V = synthetic.make_v(rows, a.n, a.kappa, seed=0)
     S2 = oracle.gauss_sketch(1, s2, s1)
     for _ in range(a.warmup):
@@ -397,7 +405,7 @@ def main():
     import synthetic
 
     m, n = a.m, a.n
-    s1, s2 = synthetic.default_sketch_sizes(n)
+    s1, s2 = sketch_sizes(a)
     prec = rq.FP64 if a.prec == "fp64" else rq.F32X2
     dev = torch.device("cuda", local_rank)
     if world > 1 and a.prec != "fp64":
@@ -557,67 +565,99 @@ def main():
                                      "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
 
         # end to end through the public API: pinned host V in, Q and R back to pinned host,
-        # every step.  The copies run on their own streams with two device buffer sets, so
-        # step i's factorization overlaps step i + 1's upload and step i - 1's download (the
-        # pipeline a caller streaming matrices through the GPU would use).
+        # every step.  On one GPU that is the host-buffer call randqr_factor_host (its own
+        # upload, factorization in the context's staging area, download); consecutive steps
+        # alternate between two contexts on two streams, so step i + 1's upload overlaps step
+        # i's factorization and download (the pipeline a caller streaming matrices through the
+        # GPU would use).  Row shards (N > 1) copy around the sharded device call the same way.
         Vh = V.cpu().pin_memory()
-        Qh = torch.empty_like(Vh).pin_memory()
-        Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        Vd = [torch.empty_like(V) for _ in range(2)]
-        Qd = [torch.empty_like(V) for _ in range(2)]
-        Rd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
-        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
         ke = max(2, min(a.steps, 6))
+        if world == 1:
+            Qh = [torch.empty_like(Vh).pin_memory() for _ in range(2)]
+            Rh = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+            hctx = [ctx, rq.Context(local_rank)]
+            hst = [torch.cuda.Stream(device=dev) for _ in range(2)]
+            done = [torch.cuda.Event() for _ in range(2)]
 
-        def factor_into(b):
-            if world > 1:
+            def e2e_step(i):
+                b = i % 2
+                rq.randqr_factor_host(Vh, s1, s2, seed=0, prec=prec, Q=Qh[b], R=Rh[b], ctx=hctx[b],
+                                      stream=hst[b], sync=False)
+                done[b].record(hst[b])
+
+            for i in range(2):  # staging areas, workspaces and sketches in place
+                e2e_step(i)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for b in range(2):
+                hst[b].wait_event(f0)
+            for i in range(ke):
+                e2e_step(i)
+            for b in range(2):
+                stream.wait_event(done[b])
+            f1.record(stream)
+            torch.cuda.synchronize()
+            for b in range(2):
+                st_b, _ = rq.get_status(hctx[b], hst[b])
+                if st_b != 0:
+                    raise SystemExit(f"randqr_factor_host failed with status {st_b}")
+            e2e_ms = f0.elapsed_time(f1) / ke
+            del Qh, hctx
+            pipeline = ("randqr_factor_host on pinned host buffers; consecutive steps on two "
+                        "contexts and streams, so uploads, factorizations and downloads overlap")
+        else:
+            Qh = torch.empty_like(Vh).pin_memory()
+            Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+            Vd = [torch.empty_like(V) for _ in range(2)]
+            Qd = [torch.empty_like(V) for _ in range(2)]
+            Rd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
+            s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+            ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
+
+            def e2e_step(i):
+                b = i % 2
+                with torch.cuda.stream(s_in):
+                    if i >= 2:
+                        s_in.wait_event(ev["comp"][b])  # step i - 2 has read Vd[b]
+                    Vd[b].copy_(Vh, non_blocking=True)
+                    ev["in"][b].record(s_in)
+                stream.wait_event(ev["in"][b])
+                if i >= 2:
+                    stream.wait_event(ev["out"][b])  # step i - 2's download has read Qd[b], Rd[b]
                 _, Rk = sharded.factor_row_sharded(Vd[b], rank * m, allreduce, s1, s2, seed=0, Q=Qd[b],
                                                    stages=stages)
                 Rd[b].copy_(Rk)
-            else:
-                rq.randqr_factor(Vd[b], s1, s2, seed=0, prec=prec, Q=Qd[b], R=Rd[b], ctx=ctx, sync=False)
+                ev["comp"][b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev["comp"][b])
+                    Qh.copy_(Qd[b], non_blocking=True)
+                    Rh.copy_(Rd[b], non_blocking=True)
+                    ev["out"][b].record(s_out)
 
-        def e2e_step(i):
-            b = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev["comp"][b])  # step i - 2 has read Vd[b]
-                Vd[b].copy_(Vh, non_blocking=True)
-                ev["in"][b].record(s_in)
-            stream.wait_event(ev["in"][b])
-            if i >= 2:
-                stream.wait_event(ev["out"][b])  # step i - 2's download has read Qd[b], Rd[b]
-            factor_into(b)
-            ev["comp"][b].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev["comp"][b])
-                Qh.copy_(Qd[b], non_blocking=True)
-                Rh.copy_(Rd[b], non_blocking=True)
-                ev["out"][b].record(s_out)
-
-        for i in range(2):
-            e2e_step(i)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        s_in.wait_event(f0)
-        for i in range(ke):
-            e2e_step(i)
-        stream.wait_event(ev["out"][(ke - 1) % 2])
-        stream.wait_event(ev["out"][(ke - 2) % 2])
-        f1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = f0.elapsed_time(f1) / ke
+            for i in range(2):
+                e2e_step(i)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            s_in.wait_event(f0)
+            for i in range(ke):
+                e2e_step(i)
+            stream.wait_event(ev["out"][(ke - 1) % 2])
+            stream.wait_event(ev["out"][(ke - 2) % 2])
+            f1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms = f0.elapsed_time(f1) / ke
+            del Qh, Vd, Qd
+            pipeline = "upload, sharded factorization and download of consecutive steps overlap (3 streams)"
         if world > 1:
             t = torch.tensor([e2e_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = t.item()
         line["e2e"] = {"value": algo_bytes * world / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
                        "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n,
-                       "ms_per_step": e2e_ms,
-                       "pipeline": "upload, factorization and download of consecutive steps overlap (3 streams)"}
-        del Vh, Qh, Vd, Qd
+                       "ms_per_step": e2e_ms, "pipeline": pipeline}
+        del Vh
 
         # GPU baselines on a matrix all three can factor (kappa = 1e4), same size
         Vb = synthetic.make_v_torch(m, n, 1e4, seed=rank + 100, device=dev)
@@ -647,7 +687,7 @@ def main():
             torch.cuda.empty_cache()
             line["batched"] = batch_bench(rq, synthetic, torch, dev)
         if rank == 0:
-            line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18)
+            line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18, s1, s2)
 
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -209,6 +209,22 @@ randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t
                             const double *S2, randqr_precision prec, double *Q, int64_t ldq,
                             double *R, int64_t ldr, randqr_info *info, void *stream);
 
+/* rand_cholQR of a matrix in HOST memory: V (m x n, ldv), Q (m x n, ldq) and R (n x n, ldr)
+ * are host pointers; S2 (optional, as in randqr_factor) is device memory.  On `stream`, the
+ * call uploads V into a staging area of the context (m n doubles plus n^2, kept for later
+ * calls and counted against the HBM budget; growing it waits for the device), runs
+ * randqr_factor in place there, and downloads Q and R.  Q may alias V (ldq == ldv); R must
+ * not overlap V or Q.  With pinned host memory (cudaMallocHost / cudaHostRegister) the
+ * call is asynchronous: V must stay unchanged, and Q and R are complete, only once the
+ * stream has reached the end of the call's work (info != NULL waits for it).  Pageable host
+ * memory works, with copies that block the host.  One call at a time per context (the
+ * staging area is the context's); callers that overlap consecutive factorizations use one
+ * context per stream. */
+randqr_status randqr_factor_host(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                                 int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                                 const double *S2, randqr_precision prec, double *Q, int64_t ldq,
+                                 double *R, int64_t ldr, randqr_info *info, void *stream);
+
 /* randQR alone (Algorithm 1): Q0 = V R_s^{-1} (S2S1-orthogonal, kappa(Q0) = O(1)) and
  * R0 = R_s.  Same arguments as randqr_factor. */
 randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,

@@ -14,7 +14,7 @@ import os as _os
 __all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "randqr_rademacher_sketch",
            "randqr_sketch", "SKETCH_GAUSSIAN", "SKETCH_RADEMACHER", "SKETCH_COUNT_ONLY",
            "SKETCH_GAUSSIAN_ONLY",
-           "randqr_factor", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
+           "randqr_factor", "randqr_factor_host", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
            "randqr_shard_sketch", "randqr_sketch_r", "randqr_shard_gram", "randqr_shard_finish",
            "default_sketch_sizes", "library_path", "FP64", "F32X2"]
 
@@ -72,6 +72,8 @@ def _load():
         "randqr_sketch_static": [vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
         "randqr_factor": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
                           _ct.POINTER(Info), vp],
+        "randqr_factor_host": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
+                               _ct.POINTER(Info), vp],
         "randqr_randqr": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, i64, vp, i64,
                           _ct.POINTER(Info), vp],
         "randqr_cholqr2": [vp, vp, i64, i64, i64, vp, i64, vp, i64, _ct.POINTER(Info), vp],
@@ -286,6 +288,41 @@ def randqr_factor(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=Non
     st = _load().randqr_factor(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), int(prec),
                                _ptr(Q), ldq, _ptr(R), ldr,
                                _ct.byref(info) if sync else None, _stream(stream))
+    c._check(st, info)
+    return Q, R, info
+
+
+def _check_host_mat(t, name):
+    import torch
+    if not (t.device.type == "cpu" and t.dtype == torch.float64 and t.dim() == 2 and t.stride(1) == 1):
+        raise ValueError(f"{name}: need a host float64 matrix with unit column stride")
+    return t.stride(0)
+
+
+def randqr_factor_host(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=None, ctx=None,
+                       device=0, stream=None, sync=True):
+    """rand_cholQR of a host matrix (pinned for asynchronous copies): V is uploaded into the
+    context's staging area, factored there in place, and Q and R come back into host
+    tensors (allocated pinned when not given).  Returns (Q, R, info); with sync=False only
+    enqueued on `stream` (info None): V, Q and R must then stay alive until it completes."""
+    import torch
+    ldv = _check_host_mat(V, "V")
+    m, n = V.shape
+    d1, d2 = default_sketch_sizes(n)
+    s1 = d1 if s1 is None else s1
+    s2 = d2 if s2 is None else s2
+    if S2 is not None:
+        _check_mat(S2, "S2")
+    if Q is None:
+        Q = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+    if R is None:
+        R = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    ldq, ldr = _check_host_mat(Q, "Q"), _check_host_mat(R, "R")
+    c = ctx if ctx is not None else _ctx(None, torch.empty(0, device=f"cuda:{device}"))
+    info = Info() if sync else None
+    st = _load().randqr_factor_host(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), int(prec),
+                                    _ptr(Q), ldq, _ptr(R), ldr,
+                                    _ct.byref(info) if sync else None, _stream(stream))
     c._check(st, info)
     return Q, R, info
 

@@ -69,7 +69,7 @@ size_t align_up(size_t b) { return (b + 255) & ~(size_t)255; }
 // Ensure the slab holds `bytes`; grows by reallocation (after waiting for the device).
 randqr_status ensure_ws(randqr_ctx *ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return RANDQR_OK;
-  if (ctx->budget && bytes + ctx->s2_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
+  if (ctx->budget && bytes + ctx->s2_bytes + ctx->hstage_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
   RQ_CUDA(cudaDeviceSynchronize());
   if (ctx->ws) RQ_CUDA(cudaFree(ctx->ws));
   ctx->ws = nullptr;
@@ -79,6 +79,22 @@ randqr_status ensure_ws(randqr_ctx *ctx, size_t bytes) {
     return RANDQR_ERR_NOMEM;
   }
   ctx->ws_bytes = bytes;
+  return RANDQR_OK;
+}
+
+// Ensure the staging area of randqr_factor_host holds `bytes` (same growth rule as the slab).
+randqr_status ensure_host_stage(randqr_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->hstage_bytes) return RANDQR_OK;
+  if (ctx->budget && bytes + ctx->ws_bytes + ctx->s2_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
+  RQ_CUDA(cudaDeviceSynchronize());
+  if (ctx->hstage) RQ_CUDA(cudaFree(ctx->hstage));
+  ctx->hstage = nullptr;
+  ctx->hstage_bytes = 0;
+  if (cudaMalloc(&ctx->hstage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_NOMEM;
+  }
+  ctx->hstage_bytes = bytes;
   return RANDQR_OK;
 }
 
@@ -116,7 +132,7 @@ randqr_status ensure_s2(randqr_ctx *ctx, uint64_t seed, int64_t s1, int64_t s2, 
         ctx->s2_kind_cached == ctx->s2_kind)) {
     const size_t bytes = sizeof(double) * (size_t)(s1 * s2);
     if (bytes > ctx->s2_bytes) {
-      if (ctx->budget && bytes + ctx->ws_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
+      if (ctx->budget && bytes + ctx->ws_bytes + ctx->hstage_bytes > ctx->budget) return RANDQR_ERR_NOMEM;
       RQ_CUDA(cudaDeviceSynchronize());
       if (ctx->s2_buf) RQ_CUDA(cudaFree(ctx->s2_buf));
       ctx->s2_buf = nullptr;
@@ -327,6 +343,7 @@ randqr_status randqr_destroy(randqr_ctx *ctx) {
   rq_batcher_destroy(ctx);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->hstage) cudaFree(ctx->hstage);
   if (ctx->s2_buf) cudaFree(ctx->s2_buf);
   if (ctx->status_dev) cudaFree(ctx->status_dev);
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
@@ -563,6 +580,32 @@ randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t
                             double *R, int64_t ldr, randqr_info *info, void *stream) {
   return factor_impl(ctx, V, m, n, ldv, s1, s2, seed, S2, prec, Q, ldq, R, ldr, info, stream,
                      true);
+}
+
+randqr_status randqr_factor_host(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
+                                 int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
+                                 const double *S2, randqr_precision prec, double *Q, int64_t ldq,
+                                 double *R, int64_t ldr, randqr_info *info, void *stream) {
+  // the checks of randqr_factor before anything is staged
+  if (!ctx || bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr) ||
+      ranges_overlap(R, span_bytes(n, n, ldr), V, span_bytes(m, n, ldv)) || bad_sketch_sizes(n, s1, s2) ||
+      bad_sketch_kind(ctx, m, s1, s2, 0) || (prec != RANDQR_FP64 && prec != RANDQR_F32X2) || s2 > m)
+    return RANDQR_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  RQ_CUDA(cudaSetDevice(ctx->device));
+  // V (packed to ld n) and R in the context's staging area; the factorization runs in place
+  const size_t vbytes = align_up(sizeof(double) * (size_t)m * (size_t)n);
+  randqr_status st = ensure_host_stage(ctx, vbytes + align_up(sizeof(double) * (size_t)(n * n)));
+  if (st != RANDQR_OK) return st;
+  double *Vd = (double *)ctx->hstage;
+  double *Rd = (double *)((char *)ctx->hstage + vbytes);
+  const size_t row = sizeof(double) * (size_t)n;
+  RQ_CUDA(cudaMemcpy2DAsync(Vd, row, V, sizeof(double) * (size_t)ldv, row, (size_t)m, cudaMemcpyHostToDevice, s));
+  st = factor_impl(ctx, Vd, m, n, n, s1, s2, seed, S2, prec, Vd, n, Rd, n, nullptr, stream, true);
+  if (st != RANDQR_OK) return st;
+  RQ_CUDA(cudaMemcpy2DAsync(Q, sizeof(double) * (size_t)ldq, Vd, row, row, (size_t)m, cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaMemcpy2DAsync(R, sizeof(double) * (size_t)ldr, Rd, row, row, (size_t)n, cudaMemcpyDeviceToHost, s));
+  return finish_call(ctx, s, info);
 }
 
 randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,

@@ -101,6 +101,9 @@ struct randqr_ctx {
   // one growable workspace slab
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  // device staging of randqr_factor_host (V uploaded and factored in place, R)
+  void *hstage = nullptr;
+  size_t hstage_bytes = 0;
   // cached Gaussian sketch S2 (seed, s1, s2)
   double *s2_buf = nullptr;
   size_t s2_bytes = 0;
