@@ -214,3 +214,79 @@ def test_gram_recombination_bounds():
         t = t - 2 ** 64 if t >= 2 ** 63 else t
         exact = sum(D[g] * 2 ** (7 * (7 - g)) for g in range(8))
         assert abs(t * 256 - exact) < 256
+
+
+# ---- the sketch GEMM: dense B, K in chunks of 64 with per-chunk scales ---------------------
+
+def split_gemm(A, B, chunk=64):
+    """C = A B the way the sketch kernel forms it: for each chunk of 64 along K, row scales of
+    A's chunk and column scales of B's chunk, byte digits, slice pairs s + t <= 7 in eight
+    regions, integer recombination; the chunks' FP64 values summed in order."""
+    M, K = A.shape
+    n = B.shape[1]
+    C = np.zeros((M, n))
+    for c0 in range(0, K, chunk):
+        a, b = A[:, c0:c0 + chunk], B[c0:c0 + chunk]
+        E, F = scale_exp(a, 1), scale_exp(b, 0)
+        da, db = digits(fix54(a, E)), digits(fix54(b, F))
+        D = []
+        for g in range(8):
+            acc = np.zeros((M, n), dtype=np.int64)
+            for s in range(7):
+                if 0 <= g - s < 7:
+                    acc += da[s] @ db[g - s]
+            assert np.abs(acc).max() <= (2 ** 22 if g <= 4 else 2 ** 23 - 1)
+            D.append(acc)
+        C += np.ldexp(recombine(D).astype(np.float64), E + F - 56)
+    return C
+
+
+def test_sketch_split_gemm_error_per_chunk():
+    # each term of a chunk errs by less than 2^-51 of (largest |a| in the chunk's row) x
+    # (largest |b| in the chunk's column), whatever the spread inside the chunk: truncation of
+    # both factors (2^-53 each, the scales being below twice the maxima), the dropped digit
+    # pairs and the recombination's last unit; checked exactly
+    rng = synthetic.rng(31)
+    M, K, n = 6, 150, 5  # a ragged last chunk
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-25, 25, (1, K)))
+    B = rng.standard_normal((K, n)) * np.exp(rng.uniform(-25, 25, (K, 1)))
+    A[2] = 0.0
+    C = split_gemm(A, B)
+    for i in range(M):
+        for j in range(n):
+            exact = sum(Fraction(float(A[i, k])) * Fraction(float(B[k, j])) for k in range(K))
+            allowed = Fraction(0)
+            for c0 in range(0, K, 64):
+                L = min(64, K - c0)
+                amax = np.abs(A[i, c0:c0 + 64]).max()
+                bmax = np.abs(B[c0:c0 + 64, j]).max()
+                allowed += L * Fraction(float(amax)) * Fraction(float(bmax)) * Fraction(2) ** -51
+            # plus the roundings of the chunk values and of their FP64 sum
+            allowed += 4 * Fraction(2) ** -53 * sum(abs(Fraction(float(A[i, k])) * Fraction(float(B[k, j])))
+                                                    for k in range(K))
+            assert abs(Fraction(float(C[i, j])) - exact) <= allowed
+    assert np.all(C[2] == 0.0)
+
+
+def test_sketch_split_gemm_exact_for_signs_times_integers():
+    # +-1 entries of A (and the identity) with integer B: every chunk value is an exact
+    # integer, so the result equals A B exactly (the GPU test's bit-exact case)
+    rng = synthetic.rng(32)
+    K, n = 200, 7
+    A = np.where(rng.random((9, K)) < 0.5, -1.0, 1.0)
+    B = rng.integers(-2 ** 20, 2 ** 20, (K, n)).astype(np.float64)
+    np.testing.assert_array_equal(split_gemm(A, B), A @ B)
+    I = np.eye(K)[:70]
+    np.testing.assert_array_equal(split_gemm(I, B), B[:70])
+
+
+def test_sketch_split_gemm_at_the_digit_extremes():
+    # a full chunk of entries whose lower digits are all -128 on both sides: the region sums
+    # reach the recombination's bounds (asserted inside split_gemm) and the result is right
+    X0 = 63 * 2 ** 48 + sum(128 << (8 * p) for p in range(6))
+    x0 = -np.ldexp(float(X0), -54)
+    A = np.full((2, 64), x0)
+    B = np.full((64, 3), x0)
+    C = split_gemm(A, B)
+    exact = 64 * Fraction(x0) * Fraction(x0)
+    assert abs(Fraction(float(C[0, 0])) - exact) <= Fraction(2) ** -52 * exact
