@@ -46,9 +46,9 @@ def roofline_model(kind, n):
 
 # DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
 # m = 2^20, n = 64 with --set full, divided by m), scaled to a launch by the rows it processes.
-# Valid for n = 64 and the kernels as captured.
-MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.01e6 + 484.83e6) / 1048576,
-                                   "gram_tc": (537.01e6 + 3.06e6) / 1048576}
+# Valid for n = 64 and the kernels as captured; a kernel changed since its capture has no entry
+# (its traffic is reported as null until it is captured again).
+MEASURED_DRAM_BYTES_PER_ROW_N64 = {"gram_tc": (537.01e6 + 3.06e6) / 1048576}
 
 
 def kernel_roofline(kind, avg_ms, m, n):
@@ -69,7 +69,8 @@ def kernel_roofline(kind, avg_ms, m, n):
     traffic = MEASURED_DRAM_BYTES_PER_ROW_N64[kind] * m if (n == 64 and kind in MEASURED_DRAM_BYTES_PER_ROW_N64) else None
     return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "traffic_source": "ncu dram bytes per row at m=2^20, n=64, scaled by m" if traffic else None,
+            "traffic_source": ("ncu dram bytes per row at m=2^20, n=64, scaled by m" if traffic else
+                               "not captured since the kernel last changed"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
             "algorithmic": f"{per_row} bytes per row x {m} rows per launch"}
 
