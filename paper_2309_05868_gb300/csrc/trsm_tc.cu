@@ -33,7 +33,8 @@
 //   warp 16 loads 32-row sub-tiles of X into a four-slot ring (slot q holds sub-tile q) with
 //     per-row bulk copies,
 //   warp 17 owns tensor memory and issues the MMAs,
-// handing tiles over through mbarriers.  B's digit slices are built once per CTA.  A's K-block
+// handing tiles over through mbarriers.  For n = 64 (and 16-byte aligned rows of Y) a full-width
+// instance runs without any per-value column check.  B's digit slices are built once per CTA.  A's K-block
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
 // completed.  In place (Y == X) is safe: a tile's rows are read before any are written.
 #include <cuda.h>
