@@ -48,7 +48,8 @@ def roofline_model(kind, n):
 # m = 2^20, n = 64 with --set full, divided by m), scaled to a launch by the rows it processes.
 # Valid for n = 64 and the kernels as captured; a kernel changed since its capture has no entry
 # (its traffic is reported as null until it is captured again).
-MEASURED_DRAM_BYTES_PER_ROW_N64 = {"gram_tc": (537.01e6 + 3.06e6) / 1048576}
+MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.01e6 + 484.83e6) / 1048576,
+                                   "gram_tc": (537.01e6 + 3.06e6) / 1048576}
 
 
 def kernel_roofline(kind, avg_ms, m, n):

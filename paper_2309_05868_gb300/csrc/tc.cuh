@@ -231,9 +231,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
 
-// Poll an mbarrier phase at most MAX_WAIT times, giving up early once *abort is set (looked at
-// every 32 polls: a poll loop is a few instructions, and waiting warps share the issue slots
-// of the working ones).
+// Poll an mbarrier phase at most MAX_WAIT times, giving up early once *abort is set.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int *abort) {
   for (int it = 0; it < MAX_WAIT; ++it) {
     uint32_t done;
@@ -244,7 +242,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parit
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 31) == 31 && *abort) return false;
+    if (*abort) return false;
   }
   return false;
 }

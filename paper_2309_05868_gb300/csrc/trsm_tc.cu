@@ -33,8 +33,7 @@
 //   warp 16 loads 32-row sub-tiles of X into a four-slot ring (slot q holds sub-tile q) with
 //     per-row bulk copies,
 //   warp 17 owns tensor memory and issues the MMAs,
-// handing tiles over through mbarriers.  For n = 64 (and 16-byte aligned rows of Y) a full-width
-// instance runs without any per-value column check.  B's digit slices are built once per CTA.  A's K-block
+// handing tiles over through mbarriers.  B's digit slices are built once per CTA.  A's K-block
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
 // completed.  In place (Y == X) is safe: a tile's rows are read before any are written.
 #include <cuda.h>
@@ -123,9 +122,6 @@ __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uin
 
 }  // namespace
 
-// FULLN: n == 64, so no column of a staged row lies past n (the per-value column checks go, and
-// rows past the CTA's range, whose products are never stored, are cut like the others).
-template <bool FULLN>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
     k_trsm_oz(const __grid_constant__ CUtensorMap xmap, const double *__restrict__ X, int64_t ldx, double *Y,
               int64_t ldy, int64_t m, int n, const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode,
@@ -224,7 +220,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const uint32_t fb = bar(BAR_FULL + q);
         if (cnt > 0 && load_mode == LOAD_TMA) {
           // boxes of the n columns (rows past m arrive as zeros)
-          const int nbox = FULLN ? 4 : (n + 15) >> 4;
+          const int nbox = (n + 15) >> 4;
           if (lane == 0) {
             mbar_expect_tx(fb, (uint32_t)nbox * STAGE_BOX);
             for (int b = 0; b < nbox; ++b) tma_load_box(smem_addr(dst + b * STAGE_BOX), &xmap, 16 * b, (int)r0, fb);
@@ -309,7 +305,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const int rr = 8 * sg + r;  // row within the sub-tile
       const bool live = rr < sub_rows(i, q);
       const uint8_t *src = stage + (size_t)q * STAGE_BYTES;
-      uint32_t mxh = 0;  // largest high word without its sign: its bits 20-30 are the exponent
+      int mx = 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int kg = 2 * c + kk;
@@ -317,17 +313,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         for (int u = 0; u < 4; ++u) {
           const ulonglong2 raw = *(const ulonglong2 *)(src + stage_off(rr, 8 * kg + 2 * u));
           const int c0 = 8 * kg + 2 * u;
-          if (FULLN) {
-            e[c][2 * u] = raw.x;
-            e[c][2 * u + 1] = raw.y;
-          } else {
-            e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
-            e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
-          }
-          mxh = max(mxh, max((uint32_t)(e[c][2 * u] >> 32) & 0x7fffffffu, (uint32_t)(e[c][2 * u + 1] >> 32) & 0x7fffffffu));
+          e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
+          e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
+          mx = max(mx, max((int)((e[c][2 * u] >> 52) & 0x7ff), (int)((e[c][2 * u + 1] >> 52) & 0x7ff)));
         }
       }
-      int mx = (int)(mxh >> 20);
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(bar(BAR_EMPTY + grp));
@@ -415,7 +405,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
               const double y1 = int_times_pow2_cvt(t1, er[rg][hr] + e1);
               if (grow < r_end) {
                 double *yp = Y + grow * ldy + k0;
-                if (FULLN || (vec_store && k0 + 1 < n)) {
+                if (vec_store && k0 + 1 < n) {
                   *(double2 *)yp = make_double2(y0, y1);
                 } else {
                   if (k0 < n) yp[0] = y0;
@@ -478,13 +468,10 @@ cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy,
       load_mode = LOAD_TMA;
   }
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0;
-  // the full-width form stores 16-byte pairs unconditionally: only with aligned rows
-  const bool full = n == TQ_NP && vec_store;
-  auto kern = full ? k_trsm_oz<true> : k_trsm_oz<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta, load_mode,
-                                                   vec_store, st);
+  k_trsm_oz<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta, load_mode,
+                                                         vec_store, st);
   return cudaGetLastError();
 }
 
