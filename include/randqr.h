@@ -219,7 +219,8 @@ randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t
  * stream has reached the end of the call's work (info != NULL waits for it).  Pageable host
  * memory works, with copies that block the host.  One call at a time per context (the
  * staging area is the context's); callers that overlap consecutive factorizations use one
- * context per stream. */
+ * context per stream.  Errors as randqr_factor (argument errors before any copy), plus
+ * RANDQR_ERR_NOMEM when the staging area cannot be allocated within the budget. */
 randqr_status randqr_factor_host(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                                  int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                                  const double *S2, randqr_precision prec, double *Q, int64_t ldq,
