@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -33,3 +35,30 @@ def test_reference_arm_line():
 def test_reference_arm_takes_the_sketch_sizes():
     d = _run("--impl", "reference", "--steps", "1", "--warmup", "1", "--n", "8", "--s1", "300", "--s2", "40")
     assert "s1=300 s2=40" in d["config"]["workload"]
+
+
+def test_roofline_fields_from_a_launch_time():
+    # the dominant kernel's roofline object: algorithmic bytes per launch over the launch time,
+    # against the measured copy peak, with the DRAM traffic scaled from the capture
+    import bench
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):
+        pytest.skip("no measured peaks on this machine")
+    peak = json.load(open(path))["hbm_gbs"]
+    m, n = 1 << 23, 64
+    r = bench.kernel_roofline("trsm_tc", 2.5, m, n)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak
+    assert abs(r["achieved"] - 16 * n * m / 2.5e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    assert r["traffic"] == bench.MEASURED_DRAM_BYTES_PER_ROW_N64["trsm_tc"] * m
+    assert bench.kernel_roofline("trsm_tc", 2.5, m, 32)["traffic"] is None  # captured at n = 64 only
+
+
+def test_workload_names_carry_the_sketch_sizes():
+    import argparse
+    import bench
+    a = argparse.Namespace(m=1 << 23, n=64, kappa=1e12, s1=0, s2=0)
+    assert bench.sketch_sizes(a) == (8320, 256)
+    assert bench.workload_name(a) == "rand_cholQR m=8388608 n=64 kappa=1e+12 s1=8320 s2=256"
+    a.s1, a.s2 = 34279, 776
+    assert bench.workload_name(a).endswith("s1=34279 s2=776")
