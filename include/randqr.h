@@ -56,6 +56,10 @@ typedef enum {
   RANDQR_ERR_TICKET = -9        /* serving: unknown ticket */
 } randqr_status;
 
+/* Arithmetic of rand_cholQR's three row passes.  With the tensor cores on (the default) and
+ * n <= 64 the row passes are exact split products whatever this says (their accuracy is
+ * that of FP64, see randqr_set_tensor_cores), so RANDQR_F32X2 changes nothing there; it
+ * selects the pair-arithmetic kernels with the tensor cores off or for 64 < n <= 128. */
 typedef enum {
   RANDQR_FP64 = 0,   /* every step in IEEE FP64 */
   RANDQR_F32X2 = 1   /* the three row passes (triangular solves and Gram) in double-float
@@ -63,11 +67,26 @@ typedef enum {
                         Householder QR, Cholesky and R = R_c R_s stay in FP64 */
 } randqr_precision;
 
+/* Details of a call's outcome.  `want_accuracy` is the one input: set it (nonzero) before
+ * passing the struct to randqr_factor, randqr_factor_host, randqr_cholqr2 or
+ * randqr_shifted_cholqr3 and the call also measures the result it returns, so that each
+ * result states its own orthogonality and residual: after the factorization it forms Q^T Q
+ * (the same split-product Gram as the method, or the FP64 Gram with the tensor cores off) and
+ * ||I - Q^T Q||_2 (largest |eigenvalue|, cyclic Jacobi on the host), and the residual
+ * ||V - Q R||_F / ||V||_F from one more pass over V and Q (Q R as a split product on the tensor
+ * cores for n <= 64, FP64 otherwise).  That costs about three more reads of an m x n matrix.
+ * The fields are -1 when not measured: want_accuracy == 0, a failed factorization, or (for
+ * resid_relF) Q aliasing V, whose input is then gone.  The measurement's own error is a few
+ * units of 2^-53 (relative to |Q| for the Gram, to |V| for the residual). */
 typedef struct {
-  int32_t info;       /* failing Cholesky pivot (1-based) or 0 */
-  int32_t stage;      /* which Cholesky failed: 1 = first, 2 = second, 3 = third; else 0 */
-  double rs_min_diag; /* smallest diagonal entry of R_s (rand_cholQR) or of the first R */
-  double rs_max_diag; /* largest diagonal entry of that factor */
+  int32_t info;         /* failing Cholesky pivot (1-based), or the failing wait's step, or 0 */
+  int32_t stage;        /* which Cholesky failed: 1 = first, 2 = second, 3 = third; else 0 */
+  double rs_min_diag;   /* smallest diagonal entry of R_s (rand_cholQR) or of the first R */
+  double rs_max_diag;   /* largest diagonal entry of that factor */
+  int32_t want_accuracy; /* in: nonzero asks for orth_err2 and resid_relF */
+  int32_t reserved;
+  double orth_err2;     /* out: ||I - Q^T Q||_2, or -1 */
+  double resid_relF;    /* out: ||V - Q R||_F / ||V||_F, or -1 */
 } randqr_info;
 
 typedef struct randqr_ctx randqr_ctx;
@@ -90,6 +109,18 @@ randqr_status randqr_get_status(randqr_ctx *ctx, void *stream, randqr_info *info
 
 /* Bytes of workspace the context holds now. */
 size_t randqr_workspace_bytes(const randqr_ctx *ctx);
+
+/* Failure detection: every wait inside this library's kernels (an mbarrier phase in the
+ * tensor-core kernels, a published reflector's flag in the multi-CTA Householder QR) polls a
+ * bounded number of times, then gives up, records RANDQR_ERR_TIMEOUT in the status word and
+ * drains (waits for its own copies and products in flight, frees its tensor memory) so that
+ * the context stays usable.  The default bound (2^24 polls for mbarriers, 2^22 for the
+ * Householder flags: seconds) is far above any legitimate wait.  polls >= 0 replaces it for
+ * this context's later launches (0: a wait gives up without polling, so any launch that has
+ * to wait at all fails with RANDQR_ERR_TIMEOUT -- a way to exercise the failure path on a
+ * healthy GPU); polls < 0 restores the default.  With ctx == NULL the bound applies to
+ * randqr_sketch_static instead (process-wide; set it while no such call is in flight). */
+randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls);
 
 /* Gram products on the tensor cores (default on): for n <= 128 the Gram G = W^T W of the
  * Cholesky passes is formed from exact integer slices of W (eight balanced 7-bit digits of a
@@ -174,8 +205,9 @@ randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t
                             int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                             const double *S2, double *Ws, void *stream);
 
-/* Ws = S2 S1 V exactly as randqr_sketch computes it, but without a context and without
- * allocating any device memory.  The paper has no counterpart: this entry point exists for
+/* Ws = S2 S1 V as randqr_sketch computes it on a context with the tensor cores on (the
+ * default): the split-product sketch GEMM for n <= 64 with its stated error bound, the FP64
+ * GEMM above -- but without a context and without allocating any device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc where they need the sketch (a framework that owns
  * every device allocation through its own pool, a host callback or latency-critical path
  * where an allocation's implicit synchronisation is not allowed, a library that must not
@@ -193,6 +225,13 @@ randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t
 randqr_status randqr_sketch_static(const double *V, int64_t m, int64_t n, int64_t ldv,
                                    int64_t s1, int64_t s2, uint64_t seed, const double *S2,
                                    double *Ws, void *stream);
+
+/* The device status of the last randqr_sketch_static call on the current device: waits for
+ * `stream` (the stream that call used), copies the fixed status word to the host (into
+ * *info when non-NULL; no allocation) and returns its code -- RANDQR_OK, or
+ * RANDQR_ERR_TIMEOUT when a bounded wait of the sketch kernels gave up (Ws is then
+ * incomplete).  The word belongs to the last call: the next randqr_sketch_static clears it. */
+randqr_status randqr_sketch_static_status(void *stream, randqr_info *info);
 
 /* ---- The factorizations -------------------------------------------------------------
  * All three return Q (m x n, ldq) with orthonormal columns and R (n x n upper, ldr,
@@ -356,6 +395,9 @@ typedef struct {
                           and a value >= 1e-12 rand_cholQR may run its row passes as
                           RANDQR_F32X2, whose results meet ||I - Q^T Q||_2 <= 1e-12 and
                           ||V - QR||_F/||V||_F <= 1e-13 in this library's tests; 0 = FP64 */
+  int32_t want_accuracy; /* nonzero: the request's randqr_info carries orth_err2 and
+                            resid_relF measured on the device (randqr_info) */
+  int32_t reserved;
 } randqr_request;
 
 typedef struct {

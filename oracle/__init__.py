@@ -53,7 +53,7 @@ def _load():
     lib.orc_rand_cholqr.argtypes = [_D, _I64, _I64, _I64, _I64, _I64, _U64, _D, _D, _D, _D, _D,
                                     _ct.POINTER(_ct.c_int32)]
     lib.orc_cholqr2.argtypes = [_D, _I64, _I64, _I64, _D, _D, _ct.POINTER(_ct.c_int32)]
-    lib.orc_scholqr3.argtypes = [_D, _I64, _I64, _I64, _D, _D, _ct.POINTER(_ct.c_int32)]
+    lib.orc_scholqr3.argtypes = [_D, _I64, _I64, _I64, _D, _D, _D, _ct.POINTER(_ct.c_int32)]
     lib.orc_sym_absmax_eig.restype = _ct.c_double
     lib.orc_sym_absmax_eig.argtypes = [_D, _I64]
     lib.orc_orth_err.argtypes = [_D, _I64, _I64, _I64, _D, _D]
@@ -238,8 +238,14 @@ def cholqr2(V):
     return _two_out(_load().orc_cholqr2, V)
 
 
-def scholqr3(V):
-    return _two_out(_load().orc_scholqr3, V)
+def scholqr3(V, return_r0=False):
+    """Shifted CholeskyQR3.  Returns (Q, R) or (Q, R, R0), R0 the shifted pass's factor."""
+    V = _f64(V)
+    m, n = V.shape
+    Q = _np.empty((m, n)); R = _np.empty((n, n)); R0 = _np.empty((n, n))
+    info = _ct.c_int32(0)
+    _check(_load().orc_scholqr3(_p(V), m, n, n, _p(Q), _p(R), _p(R0), _ct.byref(info)), info.value)
+    return (Q, R, R0) if return_r0 else (Q, R)
 
 
 # ---- error measures --------------------------------------------------------------

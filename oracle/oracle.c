@@ -385,9 +385,11 @@ int orc_cholqr2(const double *V, int64_t m, int64_t n, int64_t ldv, double *Q, d
 /* Shifted CholeskyQR3.  The paper cites but never states it; this follows the cited
  * method (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa, SISC 2020): shift
  * s = 11 (m n + n (n+1)) u ||V||_F^2 with u = 2^-53; G = V^T V + s I; R0 = chol(G);
- * Q0 = V R0^{-1}; [Q, R12] = cholQR2(Q0); R = R12 R0. */
+ * Q0 = V R0^{-1}; [Q, R12] = cholQR2(Q0); R = R12 R0.  R0_out (may be NULL) receives the
+ * shifted pass's factor, so that R0^T R0 - V^T V (= s I up to rounding) can be checked
+ * against the cited shift. */
 int orc_scholqr3(const double *V, int64_t m, int64_t n, int64_t ldv, double *Q, double *R,
-                 int32_t *info) {
+                 double *R0_out, int32_t *info) {
   double *G = (double *)malloc(sizeof(double) * (size_t)(n * n));
   double *R0 = (double *)malloc(sizeof(double) * (size_t)(n * n));
   double *R12 = (double *)malloc(sizeof(double) * (size_t)(n * n));
@@ -406,6 +408,7 @@ int orc_scholqr3(const double *V, int64_t m, int64_t n, int64_t ldv, double *Q, 
     st = orc_cholqr2(Q0, m, n, n, Q, R12, info);
   }
   if (st == ORC_OK) orc_trmm(R12, R0, n, R);
+  if (R0_out) memcpy(R0_out, R0, sizeof(double) * (size_t)(n * n));
   free(G); free(R0); free(R12); free(Q0);
   return st;
 }

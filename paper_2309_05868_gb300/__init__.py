@@ -16,6 +16,7 @@ __all__ = ["RandQRError", "Context", "randqr_cs_hash", "randqr_gauss_sketch", "r
            "SKETCH_GAUSSIAN_ONLY",
            "randqr_factor", "randqr_factor_host", "randqr_randqr", "randqr_cholqr2", "randqr_shifted_cholqr3",
            "randqr_shard_sketch", "randqr_sketch_r", "randqr_shard_gram", "randqr_shard_finish",
+           "randqr_sketch_static", "randqr_sketch_static_status",
            "default_sketch_sizes", "library_path", "FP64", "F32X2"]
 
 FP64, F32X2 = 0, 1
@@ -44,7 +45,16 @@ class RandQRError(RuntimeError):
 
 class Info(_ct.Structure):
     _fields_ = [("info", _ct.c_int32), ("stage", _ct.c_int32),
-                ("rs_min_diag", _ct.c_double), ("rs_max_diag", _ct.c_double)]
+                ("rs_min_diag", _ct.c_double), ("rs_max_diag", _ct.c_double),
+                ("want_accuracy", _ct.c_int32), ("reserved", _ct.c_int32),
+                ("orth_err2", _ct.c_double), ("resid_relF", _ct.c_double)]
+
+
+def _info(accuracy=False):
+    i = Info()
+    i.want_accuracy = 1 if accuracy else 0
+    i.orth_err2 = i.resid_relF = -1.0
+    return i
 
 
 def library_path():
@@ -70,6 +80,8 @@ def _load():
         "randqr_set_sketch_kind": [vp, i32],
         "randqr_sketch": [vp, vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
         "randqr_sketch_static": [vp, i64, i64, i64, i64, i64, u64, vp, vp, vp],
+        "randqr_sketch_static_status": [vp, _ct.POINTER(Info)],
+        "randqr_set_wait_limit": [vp, i32],
         "randqr_factor": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
                           _ct.POINTER(Info), vp],
         "randqr_factor_host": [vp, vp, i64, i64, i64, i64, i64, u64, vp, _ct.c_int, vp, i64, vp, i64,
@@ -148,6 +160,10 @@ class Context:
         L.randqr_set_tensor_cores.argtypes = [_ct.c_void_p, _ct.c_int]
         L.randqr_set_tensor_cores.restype = _ct.c_int32
         self._check(L.randqr_set_tensor_cores(self._h, int(bool(enable))))
+
+    def set_wait_limit(self, polls):
+        """Poll bound of the kernels' bounded waits (< 0: the defaults); see randqr.h."""
+        self._check(_load().randqr_set_wait_limit(self._h, int(polls)))
 
     def set_sketch_kind(self, kind):
         """The sketch of Algorithm 1 step 1: SKETCH_GAUSSIAN or SKETCH_RADEMACHER multisketch
@@ -261,6 +277,25 @@ def randqr_sketch_static(V, s1, s2, S2, Ws, seed=0, stream=None):
     return Ws
 
 
+def randqr_set_wait_limit(ctx, polls):
+    """Poll bound of the kernels' bounded waits on this context (< 0: the defaults); with
+    ctx None, the bound of randqr_sketch_static."""
+    if ctx is None:
+        st = _load().randqr_set_wait_limit(None, int(polls))
+        if st != 0:
+            raise RandQRError(st)
+    else:
+        ctx.set_wait_limit(polls)
+
+
+def randqr_sketch_static_status(stream=None):
+    """(status, Info) of the last randqr_sketch_static call on the current device: waits for
+    `stream` and reads the fixed status word (no allocation)."""
+    info = _info()
+    st = _load().randqr_sketch_static_status(_stream(stream), _ct.byref(info))
+    return st, info
+
+
 def _alloc_qr(V, Q, R):
     import torch
     m, n = V.shape
@@ -272,9 +307,10 @@ def _alloc_qr(V, Q, R):
 
 
 def randqr_factor(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=None, ctx=None,
-                  stream=None, sync=True):
+                  stream=None, sync=True, accuracy=False):
     """rand_cholQR (Algorithm 3): returns (Q, R, info).  With sync=False the call only
-    enqueues work and info is None (read it later with Context.status)."""
+    enqueues work and info is None (read it later with Context.status).  accuracy=True
+    (with sync) also measures info.orth_err2 and info.resid_relF on the device."""
     ldv = _check_mat(V, "V")
     m, n = V.shape
     d1, d2 = default_sketch_sizes(n)
@@ -284,7 +320,7 @@ def randqr_factor(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=Non
         _check_mat(S2, "S2")
     Q, R, ldq, ldr = _alloc_qr(V, Q, R)
     c = _ctx(ctx, V)
-    info = Info() if sync else None
+    info = _info(accuracy) if sync else None
     st = _load().randqr_factor(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), int(prec),
                                _ptr(Q), ldq, _ptr(R), ldr,
                                _ct.byref(info) if sync else None, _stream(stream))
@@ -300,7 +336,7 @@ def _check_host_mat(t, name):
 
 
 def randqr_factor_host(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, R=None, ctx=None,
-                       device=0, stream=None, sync=True):
+                       device=0, stream=None, sync=True, accuracy=False):
     """rand_cholQR of a host matrix (pinned for asynchronous copies): V is uploaded into the
     context's staging area, factored there in place, and Q and R come back into host
     tensors (allocated pinned when not given).  Returns (Q, R, info); with sync=False only
@@ -319,7 +355,7 @@ def randqr_factor_host(V, s1=None, s2=None, seed=0, S2=None, prec=FP64, Q=None, 
         R = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     ldq, ldr = _check_host_mat(Q, "Q"), _check_host_mat(R, "R")
     c = ctx if ctx is not None else _ctx(None, torch.empty(0, device=f"cuda:{device}"))
-    info = Info() if sync else None
+    info = _info(accuracy) if sync else None
     st = _load().randqr_factor_host(c.handle, _ptr(V), m, n, ldv, s1, s2, seed, _ptr(S2), int(prec),
                                     _ptr(Q), ldq, _ptr(R), ldr,
                                     _ct.byref(info) if sync else None, _stream(stream))
@@ -343,26 +379,26 @@ def randqr_randqr(V, s1=None, s2=None, seed=0, S2=None, Q=None, R=None, ctx=None
     return Q, R, info
 
 
-def _baseline(fn, V, Q, R, ctx, stream, sync):
+def _baseline(fn, V, Q, R, ctx, stream, sync, accuracy=False):
     ldv = _check_mat(V, "V")
     m, n = V.shape
     Q, R, ldq, ldr = _alloc_qr(V, Q, R)
     c = _ctx(ctx, V)
-    info = Info() if sync else None
+    info = _info(accuracy) if sync else None
     st = fn(c.handle, _ptr(V), m, n, ldv, _ptr(Q), ldq, _ptr(R), ldr,
             _ct.byref(info) if sync else None, _stream(stream))
     c._check(st, info)
     return Q, R, info
 
 
-def randqr_cholqr2(V, Q=None, R=None, ctx=None, stream=None, sync=True):
+def randqr_cholqr2(V, Q=None, R=None, ctx=None, stream=None, sync=True, accuracy=False):
     """CholeskyQR2 (Algorithm 4): returns (Q, R, info)."""
-    return _baseline(_load().randqr_cholqr2, V, Q, R, ctx, stream, sync)
+    return _baseline(_load().randqr_cholqr2, V, Q, R, ctx, stream, sync, accuracy)
 
 
-def randqr_shifted_cholqr3(V, Q=None, R=None, ctx=None, stream=None, sync=True):
+def randqr_shifted_cholqr3(V, Q=None, R=None, ctx=None, stream=None, sync=True, accuracy=False):
     """Shifted CholeskyQR3: returns (Q, R, info)."""
-    return _baseline(_load().randqr_shifted_cholqr3, V, Q, R, ctx, stream, sync)
+    return _baseline(_load().randqr_shifted_cholqr3, V, Q, R, ctx, stream, sync, accuracy)
 
 
 # ---------------------------------------------------------------------------------------
@@ -452,7 +488,8 @@ class Request(_ct.Structure):
                 ("m", _ct.c_int64), ("n", _ct.c_int64), ("ldv", _ct.c_int64),
                 ("s1", _ct.c_int64), ("s2", _ct.c_int64), ("seed", _ct.c_uint64),
                 ("Q", _ct.c_void_p), ("ldq", _ct.c_int64), ("R", _ct.c_void_p),
-                ("ldr", _ct.c_int64), ("max_orth_err", _ct.c_double)]
+                ("ldr", _ct.c_int64), ("max_orth_err", _ct.c_double),
+                ("want_accuracy", _ct.c_int32), ("reserved", _ct.c_int32)]
 
 
 class ServeStats(_ct.Structure):
@@ -485,13 +522,13 @@ _inflight = {}  # (context handle, ticket) -> tensors kept alive until the ticke
 
 
 def make_request(V, Q=None, R=None, algo=ALGO_RAND_CHOLQR, prec=FP64, s1=0, s2=0, seed=0,
-                 max_orth_err=0.0):
+                 max_orth_err=0.0, accuracy=False):
     """A randqr_request over torch tensors (Q, R allocated if not given)."""
     ldv = _check_mat(V, "V")
     Q, R, ldq, ldr = _alloc_qr(V, Q, R)
     m, n = V.shape
     r = Request(algo, prec, V.data_ptr(), m, n, ldv, s1, s2, seed, Q.data_ptr(), ldq,
-                R.data_ptr(), ldr, max_orth_err)
+                R.data_ptr(), ldr, max_orth_err, 1 if accuracy else 0, 0)
     return r, (V, Q, R)
 
 

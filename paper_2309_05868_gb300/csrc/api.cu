@@ -60,6 +60,7 @@ struct Workspace {
   double *W1, *Ws, *Rs, *G, *Rc, *Rt, *Rt2;
   float2 *Rdf, *rinv;  // pair form of the current triangular factor (RANDQR_F32X2)
   double *hq;          // multi-CTA Householder scratch (published reflectors, flags)
+  double *acc;         // accuracy measurement: Q^T Q (packed), then the two residual sums
 };
 
 size_t packed(int64_t n) { return (size_t)(n * (n + 1) / 2); }
@@ -98,15 +99,18 @@ randqr_status ensure_host_stage(randqr_ctx *ctx, size_t bytes) {
   return RANDQR_OK;
 }
 
+size_t acc_doubles(int64_t n) { return packed(n) + 2; }
+
 randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspace *w) {
-  const size_t sz[10] = {align_up(sizeof(double) * (size_t)(s1 * n)),
+  const size_t sz[11] = {align_up(sizeof(double) * (size_t)(s1 * n)),
                          align_up(sizeof(double) * (size_t)(s2 * n)),
                          align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
                          align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
                          align_up(sizeof(double) * packed(n)),
                          align_up(sizeof(float2) * rq::pack_df_elems(n)),
                          align_up(sizeof(float2) * rq::pack_df_rinv_elems(n)),
-                         align_up(sizeof(double) * rq::hhqr_scratch_doubles(s2, n))};
+                         align_up(sizeof(double) * rq::hhqr_scratch_doubles(s2, n)),
+                         align_up(sizeof(double) * acc_doubles(n))};
   size_t total = 0;
   for (size_t b : sz) total += b;
   randqr_status st = ensure_ws(ctx, total);
@@ -122,6 +126,8 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
   w->rinv = (float2 *)p;
   p += sz[8];
   w->hq = (double *)p;
+  p += sz[9];
+  w->acc = (double *)p;
   return RANDQR_OK;
 }
 
@@ -194,13 +200,98 @@ bool bad_sketch_kind(const randqr_ctx *ctx, int64_t m, int64_t s1, int64_t s2, i
 
 randqr_status begin_call(randqr_ctx *ctx, cudaStream_t s) {
   RQ_CUDA(cudaSetDevice(ctx->device));
-  RQ_CUDA(cudaMemsetAsync(ctx->status_dev, 0, sizeof(DevStatus), s));
+  RQ_CUDA(rq::launch_status_reset(ctx->status_dev, ctx->wait_limit < 0 ? 0 : ctx->wait_limit + 1, s));
   return RANDQR_OK;
 }
 
 randqr_status finish_call(randqr_ctx *ctx, cudaStream_t s, randqr_info *info) {
   if (!info) return RANDQR_OK;
   return randqr_get_status(ctx, s, info);
+}
+
+}  // namespace
+
+// ---- Accuracy of a result (randqr_info.want_accuracy) -------------------------------------
+// Enqueued after a factorization on its stream: Q^T Q into w.acc (packed) with the library's
+// Gram (split products on the tensor cores where the method uses them, FP64 otherwise), and,
+// when V is still intact, the residual sums ||V - Q R||_F^2, ||V||_F^2 after it; then the block
+// is copied to the context's pinned host buffer.  Kernels skip themselves if the factorization
+// failed (status word).  rq_accuracy_finish() turns the copy into the two numbers.
+bool rq_accuracy_has_resid(const double *V, const double *Q);
+
+randqr_status rq_accuracy_enqueue(randqr_ctx *ctx, const double *V, int64_t ldv, const double *Q, int64_t ldq,
+                                  const double *R, int64_t ldr, int64_t m, int64_t n, cudaStream_t s) {
+  if (!ctx->acc_host) {
+    if (cudaMallocHost(&ctx->acc_host, sizeof(double) * acc_doubles(kMaxN)) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->acc_host = nullptr;
+      return RANDQR_ERR_NOMEM;
+    }
+  }
+  Workspace w;
+  randqr_status st = carve(ctx, n, 1, 1, &w);
+  if (st != RANDQR_OK) return st;
+  double *G = w.acc, *sums = w.acc + packed(n);
+  RQ_CUDA(cudaMemsetAsync(w.acc, 0, sizeof(double) * acc_doubles(n), s));
+  if (ctx->use_tc && rq::gram_oz_supported(n)) {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
+      if (rq::gram_split_supported(n))
+        return rq::launch_gram_split(Q, false, ldq, m, n, G, ctx->num_sms, ctx->status_dev, s);
+      return rq::launch_gram_oz(Q, false, ldq, m, n, G, true, ctx->num_sms, ctx->status_dev, s);
+    }));
+  } else {
+    RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+      return rq::launch_gram(Q, ldq, m, n, G, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
+    }));
+  }
+  if (rq_accuracy_has_resid(V, Q)) {
+    RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_pack_upper(R, ldr, n, w.Rt, ctx->status_dev, s); }));
+    if (ctx->use_tc && rq::trsm_oz_supported(n)) {
+      RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+        return rq::launch_trsm_oz_resid(Q, ldq, V, ldv, m, n, w.Rt, sums, ctx->num_sms, ctx->status_dev, s);
+      }));
+    } else {
+      RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
+        return rq::launch_resid_f64(V, ldv, Q, ldq, m, n, w.Rt, sums, ctx->num_sms, ctx->status_dev, s);
+      }));
+    }
+  }
+  RQ_CUDA(cudaMemcpyAsync(ctx->acc_host, w.acc, sizeof(double) * acc_doubles(n), cudaMemcpyDeviceToHost, s));
+  return RANDQR_OK;
+}
+
+bool rq_accuracy_has_resid(const double *V, const double *Q) { return V && (const void *)V != (const void *)Q; }
+
+// After the stream has passed the copy: fill the accuracy fields of *info (the residual only
+// when V was intact, rq_accuracy_has_resid).
+void rq_accuracy_finish(randqr_ctx *ctx, int64_t n, bool have_resid, randqr_info *info) {
+  const double *h = ctx->acc_host;
+  info->orth_err2 = rq::sym_identity_gap2(h, (int)n);
+  const double r2 = h[packed(n)], v2 = h[packed(n) + 1];
+  info->resid_relF = (!have_resid || !(v2 > 0.0)) ? -1.0 : sqrt(r2 / v2);
+}
+
+namespace {
+
+void clear_accuracy(randqr_info *info) {
+  if (!info) return;
+  info->orth_err2 = -1.0;
+  info->resid_relF = -1.0;
+}
+
+// finish_call for the factorizations: with info->want_accuracy, measure the result first.
+randqr_status finish_factor(randqr_ctx *ctx, cudaStream_t s, randqr_info *info, const double *V, int64_t ldv,
+                            const double *Q, int64_t ldq, const double *R, int64_t ldr, int64_t m, int64_t n) {
+  if (!info) return RANDQR_OK;
+  clear_accuracy(info);
+  const bool want = info->want_accuracy != 0;
+  if (want) {
+    randqr_status st = rq_accuracy_enqueue(ctx, V, ldv, Q, ldq, R, ldr, m, n, s);
+    if (st != RANDQR_OK) return st;
+  }
+  randqr_status st = randqr_get_status(ctx, s, info);
+  if (st == RANDQR_OK && want) rq_accuracy_finish(ctx, n, rq_accuracy_has_resid(V, Q), info);
+  return st;
 }
 
 // Algorithm 1 steps 1-2 into w.Rs (packed); V read once by the scatter.
@@ -347,6 +438,7 @@ randqr_status randqr_destroy(randqr_ctx *ctx) {
   if (ctx->s2_buf) cudaFree(ctx->s2_buf);
   if (ctx->status_dev) cudaFree(ctx->status_dev);
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
+  if (ctx->acc_host) cudaFreeHost(ctx->acc_host);
   for (auto &r : ctx->prof_recs) {
     cudaEventDestroy(r.beg);
     cudaEventDestroy(r.end);
@@ -360,6 +452,15 @@ randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable) {
   if (!ctx) return RANDQR_ERR_ARG;
   if (ctx->use_tc != (enable != 0) && ctx->batcher) rq_batcher_destroy(ctx);  // graphs hold the old kernels
   ctx->use_tc = enable != 0;
+  return RANDQR_OK;
+}
+
+randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls) {
+  if (!ctx) {
+    rq_static_set_wait_limit(polls);
+    return RANDQR_OK;
+  }
+  ctx->wait_limit = polls < 0 ? -1 : std::min<int32_t>(polls, (1 << 30) - 1);
   return RANDQR_OK;
 }
 
@@ -556,22 +657,26 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
     if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
                           /*well_conditioned=*/true)) != RANDQR_OK)
       return st;
-    return finish_call(ctx, s, info);
+    return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
   }
-  if (prec == RANDQR_F32X2 && second_pass) return factor_df(ctx, V, m, n, ldv, Q, ldq, R, ldr, w, s, info);
+  if (prec == RANDQR_F32X2 && second_pass) {
+    if ((st = factor_df(ctx, V, m, n, ldv, Q, ldq, R, ldr, w, s, nullptr)) != RANDQR_OK) return st;
+    return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
+  }
   // W = V R_s^{-1}, written into Q.
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
     return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
   }));
   if (!second_pass) {
     RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack(w.Rs, n, R, ldr, ctx->status_dev, s); }));
+    clear_accuracy(info);
     return finish_call(ctx, s, info);
   }
   // cholQR of W, in place on Q; R = R_c R_s written dense.
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
                         /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
-  return finish_call(ctx, s, info);
+  return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }
 
 randqr_status randqr_factor(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
@@ -603,9 +708,18 @@ randqr_status randqr_factor_host(randqr_ctx *ctx, const double *V, int64_t m, in
   RQ_CUDA(cudaMemcpy2DAsync(Vd, row, V, sizeof(double) * (size_t)ldv, row, (size_t)m, cudaMemcpyHostToDevice, s));
   st = factor_impl(ctx, Vd, m, n, n, s1, s2, seed, S2, prec, Vd, n, Rd, n, nullptr, stream, true);
   if (st != RANDQR_OK) return st;
+  if (info && info->want_accuracy) {
+    // the factorization ran in place on the staged V: only the orthogonality can be measured
+    if ((st = rq_accuracy_enqueue(ctx, nullptr, 0, Vd, n, Rd, n, m, n, s)) != RANDQR_OK) return st;
+  }
   RQ_CUDA(cudaMemcpy2DAsync(Q, sizeof(double) * (size_t)ldq, Vd, row, row, (size_t)m, cudaMemcpyDeviceToHost, s));
   RQ_CUDA(cudaMemcpy2DAsync(R, sizeof(double) * (size_t)ldr, Rd, row, row, (size_t)n, cudaMemcpyDeviceToHost, s));
-  return finish_call(ctx, s, info);
+  if (!info) return RANDQR_OK;
+  const bool want = info->want_accuracy != 0;
+  clear_accuracy(info);
+  st = randqr_get_status(ctx, s, info);
+  if (st == RANDQR_OK && want) rq_accuracy_finish(ctx, n, false, info);
+  return st;
 }
 
 randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
@@ -635,7 +749,7 @@ randqr_status randqr_cholqr2(randqr_ctx *ctx, const double *V, int64_t m, int64_
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, nullptr, R, ldr, 2, RANDQR_FP64,
                         w, s, /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
-  return finish_call(ctx, s, info);
+  return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }
 
 randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
@@ -662,7 +776,7 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt2, nullptr, R, ldr, 3, RANDQR_FP64,
                         w, s, /*well_conditioned=*/true)) != RANDQR_OK)
     return st;
-  return finish_call(ctx, s, info);
+  return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }
 
 // ---- Row-sharded rand_cholQR (Sec. 4.1): the stages between the two reductions ----------

@@ -23,15 +23,21 @@ namespace rq {
 // returns at once if it is set, so a failed factorization drains without faulting.
 // ---------------------------------------------------------------------------------------
 struct DevStatus {
-  int32_t code;   // randqr_status (0 = ok)
-  int32_t info;   // 1-based failing pivot
-  int32_t stage;  // which factorization stage failed
-  int32_t pad;
-  double dmin, dmax;  // min / max diagonal of the first triangular factor
+  int32_t code;        // randqr_status (0 = ok)
+  int32_t info;        // 1-based failing pivot
+  int32_t stage;       // which factorization stage failed
+  int32_t wait_limit;  // 0: each wait's default bound; k + 1: k polls (randqr_set_wait_limit)
+  double dmin, dmax;   // min / max diagonal of the first triangular factor
 };
 
 __device__ __forceinline__ bool status_failed(const DevStatus *st) {
   return *(volatile const int32_t *)&st->code != 0;
+}
+
+// The poll bound of a kernel's waits: its default unless the context set one.
+__device__ __forceinline__ int wait_bound(const DevStatus *st, int dflt) {
+  const int v = st->wait_limit;
+  return v > 0 ? v - 1 : dflt;
 }
 
 __device__ __forceinline__ void status_fail(DevStatus *st, int32_t code, int32_t info,
@@ -118,6 +124,11 @@ struct randqr_ctx {
   char last_err[256] = {0};
   // Gram on the tensor cores (split products) when n <= 128
   bool use_tc = true;
+  // poll bound of the kernels' waits (randqr_set_wait_limit): < 0 = defaults
+  int32_t wait_limit = -1;
+  // accuracy measurement (randqr_info.want_accuracy): pinned host copy of Q^T Q (packed) and
+  // the two residual sums
+  double *acc_host = nullptr;
   // per-kernel timing (randqr_set_profiling)
   bool prof = false;
   struct ProfRec {
@@ -134,6 +145,14 @@ struct randqr_ctx {
 
 // Tear down a context's request server (waits for its streams).
 void rq_server_destroy(randqr_ctx *ctx);
+// Wait bound of randqr_sketch_static's kernels (randqr_set_wait_limit with no context).
+void rq_static_set_wait_limit(int32_t polls);
+// Accuracy of a result (api.cu): enqueue the measurement of Q (and of V - Q R when V is intact,
+// rq_accuracy_has_resid) on `s`; after the stream has passed it, rq_accuracy_finish fills *info.
+randqr_status rq_accuracy_enqueue(randqr_ctx *ctx, const double *V, int64_t ldv, const double *Q, int64_t ldq,
+                                  const double *R, int64_t ldr, int64_t m, int64_t n, cudaStream_t s);
+bool rq_accuracy_has_resid(const double *V, const double *Q);
+void rq_accuracy_finish(randqr_ctx *ctx, int64_t n, bool have_resid, randqr_info *info);
 // Tear down a context's batched plans and their lanes.
 void rq_batcher_destroy(randqr_ctx *ctx);
 
@@ -146,6 +165,18 @@ enum KernelKind {
 }  // namespace rq
 
 namespace rq {
+// Status word reset at the start of a call: zero, with the context's wait bound
+// (wait_limit_field: 0 = defaults, k + 1 = k polls).
+cudaError_t launch_status_reset(DevStatus *st, int32_t wait_limit_field, cudaStream_t s);
+// Accuracy of a result (accuracy.cu): sums[0] += ||V - Q R||_F^2 and sums[1] += ||V||_F^2 for R
+// upper triangular (packed), FP64 on the CUDA cores.
+cudaError_t launch_resid_f64(const double *V, int64_t ldv, const double *Q, int64_t ldq, int64_t m, int64_t n,
+                             const double *Rpacked, double *sums, int num_sms, const DevStatus *st, cudaStream_t s);
+// The same sums with Q R formed as a split product on the tensor cores (trsm_tc.cu), n <= 64.
+cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,
+                                 const double *Rpacked, double *sums, int num_sms, DevStatus *st, cudaStream_t s);
+// Largest |eigenvalue| of the symmetric n x n matrix I - G, G given packed upper (host, Jacobi).
+double sym_identity_gap2(const double *Gpacked, int n);
 // Kernel launchers (defined in the .cu files; all enqueue on `s`).
 cudaError_t launch_cs_hash(uint64_t seed, int64_t m, int64_t s1, int32_t *bucket, int8_t *sign,
                            cudaStream_t s);

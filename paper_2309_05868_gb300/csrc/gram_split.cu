@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     k_gram_split(const void *Win, int64_t ldw, int64_t m, int n, double *Gp, int64_t rows_per_cta,
                  int load_mode, DevStatus *st) {
   if (status_failed(st)) return;
+  const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t gs_smem[];
   uint8_t *slices = gs_smem + GOFF_SL;
   uint8_t *stage = gs_smem + GOFF_STAGE;
@@ -215,14 +216,14 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       };
       for (int g = 0; g < ngroups && ok; ++g) {
         const int b = g & 1;  // slice buffer
-        if (!mbar_wait_or_abort(slf0 + 8 * b, (g >> 1) & 1, abort_flag)) {
+        if (!mbar_wait_or_abort(slf0 + 8 * b, (g >> 1) & 1, abort_flag, lim)) {
           ok = false;
           break;
         }
         const bool merge = evt[g % 3] != 0;
         if (!merge) {
           if (pending_g >= 0) close_event();
-          if (!mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {  // previous event read back
+          if (!mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag, lim)) {  // previous event read back
             ok = false;
             break;
           }
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         umma_commit(sle0 + 8 * b);
       }
       if (ok && pending_g >= 0) close_event();
-      if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag)) {
+      if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag, lim)) {
         evt[8 + (ev & 3)] = -1;  // no more events
         mbar_arrive(ev_bar);
       } else if (!*abort_flag) {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1, q = 2 * b + h;  // slice buffer, this lane's staged sub-tile
       bool ok = true;
-      for (int qq = 0; qq < 2 && ok; ++qq) ok = mbar_wait_or_abort(full0 + 8 * (2 * b + qq), (g >> 1) & 1, abort_flag);
+      for (int qq = 0; qq < 2 && ok; ++qq) ok = mbar_wait_or_abort(full0 + 8 * (2 * b + qq), (g >> 1) & 1, abort_flag, lim);
       if (!ok) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           if (lane == 0 && over) atomicMax((int *)&evt[3 + g % 3], g + 1);
           __syncwarp();
           if (lane == 0) mbar_arrive(scale_bar);
-          if (!mbar_wait_or_abort(scale_bar, (uint32_t)(n_scale_syncs & 1), abort_flag)) {
+          if (!mbar_wait_or_abort(scale_bar, (uint32_t)(n_scale_syncs & 1), abort_flag, lim)) {
             ok = false;
             break;
           }
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     for (int c = 0; c < 32; ++c) S[c] = 0.0;
     const bool active = 32 * kh + 31 >= jlo;  // some k >= j in this warp's block
     for (int ev = 0;; ++ev) {
-      if (!mbar_wait_or_abort(ev_bar, ev & 1, abort_flag)) {
+      if (!mbar_wait_or_abort(ev_bar, ev & 1, abort_flag, lim)) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
           status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       }
       const int g = evt[8 + (ev & 3)];
       if (g < 0) break;
-      if (!mbar_wait_or_abort(t_full, ev & 1, abort_flag)) {
+      if (!mbar_wait_or_abort(t_full, ev & 1, abort_flag, lim)) {
         if (lane == 0 && !*abort_flag) {
           *abort_flag = 1;
           status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);

@@ -69,9 +69,9 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t 
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = OZ_MAX_WAIT) {
   uint32_t done = 0;
-  for (int it = 0; it < OZ_MAX_WAIT && !done; ++it)
+  for (int it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---- the chunk in shared memory
     if (tid < np) colexp[tid] = 0;
     if (bulk) {
-      if (!__syncthreads_and(mbar_wait(copy_bar, parity))) {
+      if (!__syncthreads_and(mbar_wait(copy_bar, parity, wait_bound(st, OZ_MAX_WAIT)))) {
         ok = false;
         if (tid == 0) status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
         mbar_wait(copy_bar, parity);  // second bounded wait for the copy in flight
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           mma_bar));
     }
-    if (!__syncthreads_and(mbar_wait(mma_bar, parity))) {
+    if (!__syncthreads_and(mbar_wait(mma_bar, parity, wait_bound(st, OZ_MAX_WAIT)))) {
       ok = false;
       if (tid == 0) status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
       mbar_wait(mma_bar, parity);  // second bounded wait for the work in flight

@@ -169,6 +169,9 @@ randqr_status start(randqr_ctx *ctx, randqr_server *sv, uint64_t t, int i) {
                                 sl.stream);
   }
   if (st != RANDQR_OK) return st;
+  if (r.want_accuracy &&
+      (st = rq_accuracy_enqueue(sl.sub, r.V, r.ldv, r.Q, r.ldq, r.R, r.ldr, r.m, r.n, sl.stream)) != RANDQR_OK)
+    return st;
   if (cudaMemcpyAsync(sl.sub->status_host, sl.sub->status_dev, sizeof(rq::DevStatus),
                       cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
       cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
@@ -200,6 +203,11 @@ randqr_status pump(randqr_ctx *ctx, randqr_server *sv) {
       q.info.stage = h.stage;
       q.info.rs_min_diag = h.dmin;
       q.info.rs_max_diag = h.dmax;
+      q.info.want_accuracy = q.r.want_accuracy;
+      q.info.orth_err2 = -1.0;
+      q.info.resid_relF = -1.0;
+      if (q.status == RANDQR_OK && q.r.want_accuracy)
+        rq_accuracy_finish(sl.sub, q.r.n, rq_accuracy_has_resid(q.r.V, q.r.Q), &q.info);
     }
     q.state = DONE;
     q.slot = -1;

@@ -10,6 +10,7 @@
 // creation allocates) and performs no allocation: the CountSketch accumulator W1 and the
 // device status word live in the file-scope arrays below, which every GPU that loads the
 // library holds until the process exits (8 MiB + 64 bytes per device).
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -31,6 +32,8 @@ struct StaticSlot {
 
 StaticSlot g_slots[kMaxDevices];
 std::mutex g_slots_mu;
+// wait bound written into the status word by each call (randqr_set_wait_limit(NULL, polls))
+std::atomic<int32_t> g_static_wait_field{0};
 
 // Once per device, with that device current: the device addresses of the static arrays.
 // (In host code the array names are host-side stand-ins, not device addresses.)
@@ -73,8 +76,9 @@ extern "C" randqr_status randqr_sketch_static(const double *V, int64_t m, int64_
   }
   cudaStream_t s = (cudaStream_t)stream;
   // W1 and Ws accumulate with atomics and the status word gates the kernels: all three
-  // must start at zero on every call (the array keeps the previous call's contents).
-  if (cudaMemsetAsync(slot.status, 0, sizeof(rq::DevStatus), s) != cudaSuccess ||
+  // must start at zero on every call (the array keeps the previous call's contents); the
+  // status word also carries the wait bound.
+  if (rq::launch_status_reset(slot.status, g_static_wait_field.load(), s) != cudaSuccess ||
       cudaMemsetAsync(slot.w1, 0, sizeof(double) * (size_t)(s1 * n), s) != cudaSuccess ||
       cudaMemsetAsync(Ws, 0, sizeof(double) * (size_t)(s2 * n), s) != cudaSuccess ||
       rq::launch_cs_scatter(V, m, n, ldv, s1, seed, 0, slot.w1, slot.num_sms, slot.status, s) !=
@@ -85,4 +89,40 @@ extern "C" randqr_status randqr_sketch_static(const double *V, int64_t m, int64_
     return RANDQR_ERR_CUDA;
   }
   return RANDQR_OK;
+}
+
+extern "C" randqr_status randqr_sketch_static_status(void *stream, randqr_info *info) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  StaticSlot slot;
+  if (static_slot(dev, &slot) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  // a plain host variable as the destination: the copy is synchronous for pageable memory,
+  // and nothing is allocated
+  rq::DevStatus h;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpyAsync(&h, slot.status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return RANDQR_ERR_CUDA;
+  }
+  if (info) {
+    info->info = h.info;
+    info->stage = h.stage;
+    info->rs_min_diag = h.dmin;
+    info->rs_max_diag = h.dmax;
+    info->orth_err2 = -1.0;
+    info->resid_relF = -1.0;
+  }
+  return (randqr_status)h.code;
+}
+
+void rq_static_set_wait_limit(int32_t polls) {
+  g_static_wait_field.store(polls < 0 ? 0 : std::min<int32_t>(polls, (1 << 30) - 1) + 1);
 }

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
 #pragma unroll 1
       for (int c = 0; c < 4; ++c) sk_issue_kstep(tmem, ad, bd, c);
       umma_commit(bar);
-      if (!mbar_wait(bar, (uint32_t)par)) *failed = 1;
+      if (!mbar_wait(bar, (uint32_t)par, wait_bound(st, MAX_WAIT))) *failed = 1;
     }
     __syncthreads();
     if (*failed) break;

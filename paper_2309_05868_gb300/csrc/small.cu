@@ -165,6 +165,7 @@ __device__ __forceinline__ void hq_reflect(double *col, int rows, int j, double 
 __global__ void __launch_bounds__(HQ_THREADS) k_hhqr_coop(const double *Ag, int rows, int n, double *pub,
                                                           int *flags, double *Rp, DevStatus *st) {
   if (status_failed(st)) return;
+  const int lim = wait_bound(st, HQ_MAX_WAIT);
   extern __shared__ double hq_sm[];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncl = (n - b + HQ_CTAS - 1) / HQ_CTAS;  // local columns: k = b + HQ_CTAS * c
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(HQ_THREADS) k_hhqr_coop(const double *Ag, int 
     // wait for reflector j
     if (tid == 0) {
       int ok = 0;
-      for (int it = 0; it < HQ_MAX_WAIT && !ok; ++it) ok = *(volatile int *)&flags[j];
+      for (int it = 0; it < lim && !ok; ++it) ok = *(volatile int *)&flags[j];
       if (!ok) {
         s_fail = 1;
         status_fail(st, RANDQR_ERR_TIMEOUT, j + 1, 0);
@@ -373,6 +374,20 @@ cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_pa
   }
   k_potrf<<<1, SMALL_THREADS, dyn, s>>>(G, (int)n, shift_coeff, Rc_packed, Rprev_packed,
                                         Rout_packed, Rout, ldr, stage, st);
+  return cudaGetLastError();
+}
+
+__global__ void k_status_reset(DevStatus *st, int32_t wait_limit_field) {
+  st->code = 0;
+  st->info = 0;
+  st->stage = 0;
+  st->wait_limit = wait_limit_field;
+  st->dmin = 0.0;
+  st->dmax = 0.0;
+}
+
+cudaError_t launch_status_reset(DevStatus *st, int32_t wait_limit_field, cudaStream_t s) {
+  k_status_reset<<<1, 1, 0, s>>>(st, wait_limit_field);
   return cudaGetLastError();
 }
 

@@ -58,10 +58,10 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
 }
 
-// Poll an mbarrier phase, at most MAX_WAIT times; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Poll an mbarrier phase, at most `limit` times; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = MAX_WAIT) {
   uint32_t done = 0;
-  for (int it = 0; it < MAX_WAIT && !done; ++it)
+  for (int it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
@@ -231,9 +231,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
 
-// Poll an mbarrier phase at most MAX_WAIT times, giving up early once *abort is set.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int *abort) {
-  for (int it = 0; it < MAX_WAIT; ++it) {
+// Poll an mbarrier phase at most `limit` times, giving up early once *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int *abort,
+                                                   int limit = MAX_WAIT) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

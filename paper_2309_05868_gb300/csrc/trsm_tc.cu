@@ -122,11 +122,15 @@ __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uin
 
 }  // namespace
 
+// RESID: instead of storing Y, accumulate sums[0] += sum (Vref - Y)^2 and sums[1] += sum Vref^2
+// over the rows (the residual of a factorization V = Q R, with X = Q and B = R).
+template <bool RESID>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
     k_trsm_oz(const __grid_constant__ CUtensorMap xmap, const double *__restrict__ X, int64_t ldx, double *Y,
               int64_t ldy, int64_t m, int n, const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode,
-              bool vec_store, DevStatus *st) {
+              bool vec_store, const double *__restrict__ Vref, int64_t ldvr, double *sums, DevStatus *st) {
   if (status_failed(st)) return;
+  const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t tq_smem[];
   uint8_t *Bs = tq_smem + OFF_B;
   uint8_t *As = tq_smem + OFF_A;
@@ -249,9 +253,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       for (int i = 0; i < ntiles; ++i) {
         const uint32_t ph = (uint32_t)(i & 1);
         // half 0: K-steps 0 and 1 (A's K-blocks 0, 1), once the previous tile's half 0 is read
-        if (!mbar_wait_or_abort(bar(BAR_TEMPTY + 0), ph ^ 1, abort_flag) ||
-            !mbar_wait_or_abort(bar(BAR_AFULL + 0), ph, abort_flag) ||
-            !mbar_wait_or_abort(bar(BAR_AFULL + 1), ph, abort_flag)) {
+        if (!mbar_wait_or_abort(bar(BAR_TEMPTY + 0), ph ^ 1, abort_flag, lim) ||
+            !mbar_wait_or_abort(bar(BAR_AFULL + 0), ph, abort_flag, lim) ||
+            !mbar_wait_or_abort(bar(BAR_AFULL + 1), ph, abort_flag, lim)) {
           if (!*abort_flag) set_abort(abort_flag, st);
           break;
         }
@@ -263,9 +267,9 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         issue_half_kstep<0, 1>(tmem, ad, bd);
         umma_commit(bar(BAR_HDONE + 0));
         // half 1: all four K-steps; after K-step c no MMA of this tile reads A's K-block c
-        if (!mbar_wait_or_abort(bar(BAR_TEMPTY + 1), ph ^ 1, abort_flag) ||
-            !mbar_wait_or_abort(bar(BAR_AFULL + 2), ph, abort_flag) ||
-            !mbar_wait_or_abort(bar(BAR_AFULL + 3), ph, abort_flag)) {
+        if (!mbar_wait_or_abort(bar(BAR_TEMPTY + 1), ph ^ 1, abort_flag, lim) ||
+            !mbar_wait_or_abort(bar(BAR_AFULL + 2), ph, abort_flag, lim) ||
+            !mbar_wait_or_abort(bar(BAR_AFULL + 3), ph, abort_flag, lim)) {
           if (!*abort_flag) set_abort(abort_flag, st);
           break;
         }
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     for (int i = 0; i < ntiles && ok; ++i) {
       unsigned long long e[4][8];
       for (int u = 0; u < 2; ++u)
-        if (!mbar_wait_or_abort(bar(BAR_FULL + grp + 2 * u), (uint32_t)(i & 1), abort_flag)) ok = false;
+        if (!mbar_wait_or_abort(bar(BAR_FULL + grp + 2 * u), (uint32_t)(i & 1), abort_flag, lim)) ok = false;
       if (!ok) break;
       const int rr = 8 * sg + r;  // row within the sub-tile
       const bool live = rr < sub_rows(i, q);
@@ -356,13 +360,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     // store one row's 64-byte segment.  One 16-row group (16 columns, all eight regions) per wait.
     const int f = warp - W_FLUSH0, quad = f & 3, cq = f >> 2;  // warp % 4 == quad: lanes 32 quad ..
     const int tr = lane >> 2, tc2 = 2 * (lane & 3);
+    double res2 = 0.0, ref2 = 0.0;  // RESID sums of this thread
     bool ok = true;
     for (int i = 0; i < ntiles && ok; ++i) {
       const int64_t row0 = r_begin + (int64_t)i * TQ_ROWS + 32 * quad;
       int er[2][2];
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
-        if (!mbar_wait_or_abort(bar(BAR_HDONE + h), (uint32_t)(i & 1), abort_flag)) {
+        if (!mbar_wait_or_abort(bar(BAR_HDONE + h), (uint32_t)(i & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
@@ -404,12 +409,26 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
               const double y0 = int_times_pow2_cvt(t0, er[rg][hr] + e0);
               const double y1 = int_times_pow2_cvt(t1, er[rg][hr] + e1);
               if (grow < r_end) {
-                double *yp = Y + grow * ldy + k0;
-                if (vec_store && k0 + 1 < n) {
-                  *(double2 *)yp = make_double2(y0, y1);
+                if (RESID) {
+                  const double *vp = Vref + grow * ldvr + k0;
+                  if (k0 < n) {
+                    const double v = vp[0], d = v - y0;
+                    res2 = fma(d, d, res2);
+                    ref2 = fma(v, v, ref2);
+                  }
+                  if (k0 + 1 < n) {
+                    const double v = vp[1], d = v - y1;
+                    res2 = fma(d, d, res2);
+                    ref2 = fma(v, v, ref2);
+                  }
                 } else {
-                  if (k0 < n) yp[0] = y0;
-                  if (k0 + 1 < n) yp[1] = y1;
+                  double *yp = Y + grow * ldy + k0;
+                  if (vec_store && k0 + 1 < n) {
+                    *(double2 *)yp = make_double2(y0, y1);
+                  } else {
+                    if (k0 < n) yp[0] = y0;
+                    if (k0 + 1 < n) yp[1] = y1;
+                  }
                 }
               }
             }
@@ -418,6 +437,17 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       }
     }
     if (!ok && lane == 0 && !*abort_flag) set_abort(abort_flag, st);
+    if (RESID) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        res2 += __shfl_xor_sync(0xffffffffu, res2, o);
+        ref2 += __shfl_xor_sync(0xffffffffu, ref2, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&sums[0], res2);
+        atomicAdd(&sums[1], ref2);
+      }
+    }
   }
 
   __syncthreads();
@@ -448,8 +478,10 @@ EncodeTiledFn encode_tiled() {
 }
 }  // namespace
 
-cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
-                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s) {
+template <bool RESID>
+cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
+                             const double *Bpacked, const double *Vref, int64_t ldvr, double *sums, int num_sms,
+                             DevStatus *st, cudaStream_t s) {
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
@@ -468,11 +500,21 @@ cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy,
       load_mode = LOAD_TMA;
   }
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0;
-  cudaError_t e = cudaFuncSetAttribute(k_trsm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_oz<RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  k_trsm_oz<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta, load_mode,
-                                                         vec_store, st);
+  k_trsm_oz<RESID><<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta,
+                                                                load_mode, vec_store, Vref, ldvr, sums, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
+                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s) {
+  return launch_trsm_oz_t<false>(X, ldx, Y, ldy, m, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+}
+
+cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,
+                                 const double *Rpacked, double *sums, int num_sms, DevStatus *st, cudaStream_t s) {
+  return launch_trsm_oz_t<true>(Q, ldq, nullptr, 0, m, n, Rpacked, V, ldv, sums, num_sms, st, s);
 }
 
 }  // namespace rq

@@ -62,6 +62,12 @@ def test_batched_matches_single_calls(rq, prec):
         Qs1, Rs1, _ = rq.randqr_factor(Vs[i], seed=i, prec=prec)
         assert np.abs(Q - Qs1.cpu().numpy()).max() <= scale * tq
         assert np.abs(R - Rs1.cpu().numpy()).max() / np.abs(R).max() <= scale * tr
+        # and against the oracle itself (its own S2 for seed + 1: the device's Gaussian
+        # entries agree with the host's to a few ulp, and Q, R are the unique QR factors of
+        # V whatever the sketch, within the parity tolerance)
+        Qo, Ro = oracle.rand_cholqr(Vh[i], s1, s2, seed=i)
+        assert np.abs(Q - Qo).max() <= scale * tq
+        assert np.abs(R - Ro).max() / np.abs(Ro).max() <= scale * tr
     ctx.close()
 
 

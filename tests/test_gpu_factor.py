@@ -38,7 +38,7 @@ def _run(rq, V, s1, s2, seed, S2, ld_pad=0, inplace=False, prec=0):
 CASES = [  # m, n, kappa
     (20000, 16, 1e10),     # the small benchmarked configuration
     (3001, 1, 1.0), (2999, 2, 1e3), (5003, 3, 1e6), (4097, 5, 1e12), (6000, 7, 1e14),
-    (10000, 32, 1e0), (10000, 32, 1e4), (12001, 33, 1e8), (20000, 64, 1e12),
+    (10000, 32, 1e0), (10000, 32, 1e4), (12001, 33, 1e8), (30000, 64, 1e8), (20000, 64, 1e12),
     (20000, 64, 1e14), (16385, 100, 1e8), (20000, 128, 1e4), (20000, 128, 1e14),
 ]
 
@@ -204,6 +204,43 @@ def test_full_size_sampled(rq):
     b, sg = rq.randqr_cs_hash(0, m, s1)
     bo, so = oracle.cs_hash(0, m, s1)
     assert np.array_equal(b.cpu().numpy(), bo) and np.array_equal(sg.cpu().numpy(), so)
+
+
+def test_full_size_elementwise_against_oracle(rq):
+    """The benchmarked configuration (m = 2^23, n = 64, kappa = 1e12, s1 = 8320, s2 = 256, S2
+    passed in) in the launch configuration the bench times: every element of Q and R against
+    the oracle on the same V and S2, at the parity tolerance max(1e-10, 10 x the oracle's own
+    two-sketch spread) measured on this V.  The three oracle runs (about two minutes each)
+    go in parallel threads (the ctypes calls release the interpreter lock)."""
+    import threading
+    m, n, kappa = 2**23, 64, 1e12
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    Vd = synthetic.make_v_torch(m, n, kappa, seed=0)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, _ = rq.randqr_factor(Vd, s1, s2, seed=0, S2=torch.from_numpy(S2).cuda())
+    Vh, Qh, Rh = Vd.cpu().numpy(), Q.cpu().numpy(), R.cpu().numpy()
+    del Q, R, Vd
+    torch.cuda.empty_cache()
+    out = {}
+
+    def run(key, seed, S):
+        out[key] = oracle.rand_cholqr(Vh, s1, s2, seed=seed, S2=S)
+
+    jobs = [threading.Thread(target=run, args=("o", 0, S2)),
+            threading.Thread(target=run, args=("a", 0, None)),
+            threading.Thread(target=run, args=("b", 1, None))]
+    for j in jobs:
+        j.start()
+    for j in jobs:
+        j.join()
+    Qo, Ro = out["o"]
+    dq = np.abs(out["a"][0] - out["b"][0]).max()
+    dr = np.abs(out["a"][1] - out["b"][1]).max() / np.abs(out["a"][1]).max()
+    tq, tr = max(1e-10, 10 * dq), max(1e-10, 10 * dr)
+    eq = np.abs(Qh - Qo).max()
+    er = np.abs(Rh - Ro).max() / np.abs(Ro).max()
+    assert eq <= tq, (eq, tq)
+    assert er <= tr, (er, tr)
 
 
 DF_CASES = [(20000, 16, 1e10), (3001, 1, 1.0), (5003, 3, 1e6), (6000, 7, 1e14), (10000, 32, 1e4),

@@ -441,3 +441,41 @@ def test_paper_printed_constants():
     assert abs(c["assumption_ratio"]["bound_sq"] - 625 / 9) < 1e-12
     # the multisketch in the paper's experiment satisfies Assumptions 5.1's eps condition
     assert eL < 616 / 625 - 9 / 625 * eH
+
+
+def test_scholqr3_shift_is_the_cited_shift():
+    """The shifted pass of sCholQR3 factors V^T V + s I with the cited method's shift
+    s = 11 (m n + n (n+1)) u ||V||_F^2, u = 2^-53 (Fukaya et al., SISC 2020).  On V = c U
+    with orthonormal U (||V||_F^2 = n c^2 to rounding), R0^T R0 - V^T V must be s I to
+    within the Cholesky's O(u) backward error: a coefficient of 1 instead of 11, u = 2^-52,
+    or the shift on ||V||_2 instead of ||V||_F^2 all miss by a factor of 2 or more."""
+    m, n = 2000, 8
+    U = np.linalg.qr(synthetic.rng(5).standard_normal((m, n)))[0]
+    for c in (1.0, 2.0 ** -3, 2.0 ** 5):
+        V = c * U
+        _, _, R0 = oracle.scholqr3(V, return_r0=True)
+        D = R0.T @ R0 - V.T @ V
+        s = 11.0 * (m * n + n * (n + 1)) * 2.0 ** -53 * (n * c * c)
+        assert np.abs(np.diag(D) / s - 1.0).max() < 1e-3
+        assert np.abs(D - np.diag(np.diag(D))).max() < 1e-3 * s
+
+
+def test_scholqr3_kappa_sweep():
+    """sCholQR3 past CholeskyQR2's limit: with the shift, the shifted pass succeeds at any
+    kappa and Q0 = V R0^{-1} has kappa(Q0) ~ sqrt(s) kappa(V), so CholeskyQR2 of Q0 holds
+    O(u) orthogonality while that stays below ~u^{-1/2} (here up to 1e13) and breaks down
+    past it (1e14, 1e15) -- the failure point Sec. 6.3 reports near 1e12-1e15.  Without the
+    shift the first Cholesky would already fail at 1e12 (kappa(V^T V) = 1e24 > 1/u)."""
+    m, n = 3000, 16
+    for kappa in (1e12, 1e13):
+        V = synthetic.make_v(m, n, kappa, seed=1)
+        Q, R = oracle.scholqr3(V)
+        assert oracle.orth_err(Q)[0] < 1e-13 and oracle.resid(V, Q, R) < 1e-14
+        with pytest.raises(oracle.OracleError) as e:  # no shift: plain CholeskyQR2 fails
+            oracle.cholqr2(V)
+        assert e.value.status == -2
+    for kappa in (1e14, 1e15):
+        V = synthetic.make_v(m, n, kappa, seed=1)
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.scholqr3(V)
+        assert e.value.status == -2

@@ -68,3 +68,47 @@ def test_static_sketch_rejects_oversize_and_missing_s2(rq):
     st = L.randqr_sketch_static(ctypes.c_void_p(V.data_ptr()), 1000, 8, n, 144, 32, 0, None,
                                 ctypes.c_void_p(Ws.data_ptr()), None)
     assert st == -1
+
+
+def test_static_sketch_allocates_nothing(rq):
+    # after a first call (which looks up the array's device address once), further calls
+    # leave the device's free memory exactly as it was
+    m, n = 20_000, 32
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = torch.from_numpy(synthetic.make_v(m, n, 1e4, seed=8)).cuda()
+    S2 = torch.from_numpy(oracle.gauss_sketch(2, s2, s1)).cuda()
+    Ws = torch.empty((s2, n), dtype=torch.float64, device="cuda")
+    rq.randqr_sketch_static(V, s1, s2, S2, Ws, seed=1)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rq.randqr_sketch_static(V, s1, s2, S2, Ws, seed=1)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_static_sketch_reports_its_status(rq):
+    # the status word of the fixed scratch comes back through randqr_sketch_static_status:
+    # OK normally, RANDQR_ERR_TIMEOUT when the sketch kernel's bounded wait gives up (a wait
+    # bound of 0 polls makes it give up at once); the next call clears it
+    m, n = 20_000, 64
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = torch.from_numpy(synthetic.make_v(m, n, 1e4, seed=9)).cuda()
+    S2 = torch.from_numpy(oracle.gauss_sketch(3, s2, s1)).cuda()
+    ref = rq.randqr_sketch(V, s1, s2, seed=4, S2=S2)
+    Ws = torch.empty((s2, n), dtype=torch.float64, device="cuda")
+    rq.randqr_sketch_static(V, s1, s2, S2, Ws, seed=4)
+    st, _ = rq.randqr_sketch_static_status()
+    assert st == 0
+    try:
+        rq.randqr_set_wait_limit(None, 0)
+        rq.randqr_sketch_static(V, s1, s2, S2, Ws, seed=4)
+        st, _ = rq.randqr_sketch_static_status()
+        assert st == -7
+    finally:
+        rq.randqr_set_wait_limit(None, -1)
+    rq.randqr_sketch_static(V, s1, s2, S2, Ws, seed=4)
+    st, _ = rq.randqr_sketch_static_status()
+    assert st == 0
+    assert torch.allclose(Ws, ref, rtol=0, atol=1e-12 * ref.abs().max().item())
