@@ -177,6 +177,63 @@ def cpu_baseline(n, kappa, rows, s1, s2):
                       f"same s1/s2), single-threaded FP64 C oracle, {dt:.1f} s"}
 
 
+def cpu_baseline_parallel(n, kappa, rows, s1, s2):
+    """The oracle's own routines, unchanged, on every host core: the row-block decomposition
+    of Sec. 4.1 (per-block CountSketch with the global row index, trsm and Gram), one thread per
+    block (the routines release the interpreter lock), the small steps on one core, the two
+    block sums in fixed order.  The same algorithm as the oracle, parallel over row blocks."""
+    import threading
+
+    import numpy as np
+
+    import oracle
+    import synthetic
+    cores = os.cpu_count() or 1
+    V = synthetic.make_v(rows, n, kappa, seed=0)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    cuts = [rows * k // cores for k in range(cores + 1)]
+    blocks = [(cuts[k], cuts[k + 1]) for k in range(cores) if cuts[k + 1] > cuts[k]]
+    out = [None] * len(blocks)
+
+    def par(fn):
+        ts = [threading.Thread(target=fn, args=(k, a, b)) for k, (a, b) in enumerate(blocks)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+
+    t0 = time.perf_counter()
+
+    def sk(k, a, b):
+        out[k] = oracle.countsketch_rows(V[a:b], s1, 0, a)
+    par(sk)
+    W1 = out[0].copy()
+    for w in out[1:]:
+        W1 += w
+    Rs = oracle.hhqr_r(oracle.gemm(S2, W1))
+    Ws_blocks = [None] * len(blocks)
+
+    def wg(k, a, b):
+        W = oracle.trsm(V[a:b], Rs)
+        Ws_blocks[k] = W
+        out[k] = oracle.gram(W)
+    par(wg)
+    G = out[0].copy()
+    for g in out[1:]:
+        G += g
+    Rc = oracle.chol(G)
+
+    def fin(k, a, b):
+        out[k] = oracle.trsm(Ws_blocks[k], Rc)
+    par(fin)
+    oracle.trmm(Rc, Rs)
+    dt = time.perf_counter() - t0
+    return {"value": 32.0 * rows * n / dt / 1e9, "unit": "GB/s", "cores": len(blocks), "kind": "oracle",
+            "sample": f"rand_cholQR of the first {rows} rows (n={n}, kappa={kappa:g}, same s1/s2): the "
+                      f"oracle's routines over {len(blocks)} row blocks in {len(blocks)} threads "
+                      f"(Sec. 4.1 decomposition), {dt:.2f} s"}
+
+
 def run_reference(a):
     """--impl reference: the oracle, timed on the host cores, on a bounded sample per step."""
     rank, _, world = dist_env()
@@ -386,6 +443,76 @@ def batch_bench(rq, synthetic, torch, dev, count=512, seed=11):
         ctx.close()
     del pools, Vs, Qs, Rs
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# The other single-matrix configurations: small-matrix latency, and the large matrix at the
+# other column counts and precisions, each with its accuracy against the FP64 targets.
+# ---------------------------------------------------------------------------------------
+def small_latency(rq, synthetic, torch, dev, reps=200):
+    """m = 20000, n = 16, kappa = 1e10 (s1 = 544, s2 = 64): the matrix is 2.56 MB, L2-resident,
+    so the call is latency-bound.  Reports the device time per call (back-to-back on one
+    stream, CUDA events) and the host wall time of a call that waits for its status."""
+    m, n, kappa = 20000, 16, 1e10
+    s1, s2 = 2 * (n * n + n), 4 * n
+    V = synthetic.make_v_torch(m, n, kappa, seed=0, device=dev)
+    Q = torch.empty_like(V)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx = rq.Context(dev.index or 0)
+    stream = torch.cuda.current_stream()
+    for _ in range(10):
+        rq.randqr_factor(V, s1, s2, seed=0, Q=Q, R=R, ctx=ctx, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        rq.randqr_factor(V, s1, s2, seed=0, Q=Q, R=R, ctx=ctx, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dev_us = e0.elapsed_time(e1) / reps * 1e3
+    walls = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        rq.randqr_factor(V, s1, s2, seed=0, Q=Q, R=R, ctx=ctx)  # waits for the status
+        walls.append((time.perf_counter() - t0) * 1e6)
+    _, _, info = rq.randqr_factor(V, s1, s2, seed=0, Q=Q, R=R, ctx=ctx, accuracy=True)
+    ctx.close()
+    return {"workload": f"rand_cholQR m={m} n={n} kappa={kappa:g} s1={s1} s2={s2}",
+            "device_us_per_call": dev_us, "wall_us_p50": statistics.median(walls),
+            "wall_us_min": min(walls), "orth_err_2": info.orth_err2, "resid_rel_F": info.resid_relF}
+
+
+def large_config(rq, synthetic, torch, dev, m, n, kappa, prec, steps=3):
+    """One large single-matrix configuration: ms per step, effective GB/s (32 m n bytes per
+    step) and the accuracy the call states about its result."""
+    s1, s2 = 2 * (n * n + n), 4 * n
+    V = synthetic.make_v_torch(m, n, kappa, seed=1, device=dev)
+    Q = torch.empty_like(V)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx = rq.Context(dev.index or 0)
+    stream = torch.cuda.current_stream()
+    rq.randqr_factor(V, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+    torch.cuda.synchronize()
+    ctx.kernel_times()
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rq.randqr_factor(V, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    kt = ctx.kernel_times()
+    ms = e0.elapsed_time(e1) / steps
+    st, _ = rq.get_status(ctx)
+    _, _, info = rq.randqr_factor(V, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, accuracy=True)
+    ctx.close()
+    del V, Q
+    torch.cuda.empty_cache()
+    return {"m": m, "n": n, "kappa": kappa, "precision": "fp64" if prec == rq.FP64 else "f32x2",
+            "ms_per_step": ms, "value": 32.0 * m * n / (ms / 1e3) / 1e9, "unit": "GB/s", "status": st,
+            "orth_err_2": info.orth_err2, "resid_rel_F": info.resid_relF,
+            "kernels_ms_per_step": {k: v[0] / steps for k, v in kt.items()}}
 
 
 # ---------------------------------------------------------------------------------------
@@ -682,6 +809,13 @@ def main():
                                 "rand_cholqr_over_cholqr2": times["rand_cholqr"] / times["cholqr2"],
                                 "rand_cholqr_over_shifted_cholqr3": times["rand_cholqr"] / times["shifted_cholqr3"]}
         del Vb
+        if world == 1:
+            line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
+            line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
+            for kap in (1e2, 1e6, 1e10, 1e12):
+                for pr in (rq.FP64, rq.F32X2):
+                    line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
+                                                              steps=1))
         if not a.no_serve:
             del Q
             torch.cuda.empty_cache()
@@ -690,6 +824,7 @@ def main():
             line["batched"] = batch_bench(rq, synthetic, torch, dev)
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18, s1, s2)
+            line["cpu_baseline_parallel"] = cpu_baseline_parallel(n, a.kappa, 1 << 20, s1, s2)
 
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -310,7 +310,9 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
     return RANDQR_OK;
   }
   const double *S2p = S2;
-  if (!S2p) {
+  // a Rademacher S2 on the tensor-core path is generated inside the sketch GEMM: no buffer
+  const bool rad_fly = !S2p && ctx->s2_kind == RANDQR_SKETCH_RADEMACHER && ctx->use_tc && rq::sketch_oz_supported(n);
+  if (!S2p && !rad_fly) {
     randqr_status st = ensure_s2(ctx, seed + 1, s1, s2, s, &S2p);
     if (st != RANDQR_OK) return st;
   }
@@ -336,6 +338,7 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
     return rq::launch_cs_scatter(V, m, n, ldv, s1, seed, row0, w.W1, ctx->num_sms, ctx->status_dev, s);
   }));
   RQ_CUDA(timed(ctx, s, rq::K_SKETCH_GEMM, [&] {
+    if (rad_fly) return rq::launch_sketch_oz_rademacher(seed + 1, w.W1, n, s2, s1, n, w.Ws, ctx->num_sms, ctx->status_dev, s);
     return rq::launch_sketch_gemm(S2p, w.W1, s2, s1, n, w.Ws, ctx->use_tc, ctx->num_sms, ctx->status_dev, s);
   }));
   if (do_hhqr)

@@ -194,6 +194,10 @@ cudaError_t launch_sketch_gemm(const double *S2, const double *W1, int64_t s2, i
 bool sketch_oz_supported(int64_t n);
 cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
                              int64_t n, double *C, int num_sms, DevStatus *st, cudaStream_t s);
+// C += S2 B with S2 (M x K) the Rademacher sketch of `seed` generated inside the kernel (no buffer),
+// entries +-1/sqrt(M) exactly as launch_rad_gen writes them; n <= 64
+cudaError_t launch_sketch_oz_rademacher(uint64_t seed, const double *B, int64_t ldb, int64_t M, int64_t K, int64_t n,
+                                        double *C, int num_sms, DevStatus *st, cudaStream_t s);
 // Householder R of the rows x n sketch; with scratch (hhqr_scratch_doubles) and n >= 32 it runs
 // on several co-resident CTAs, otherwise on one.
 size_t hhqr_scratch_doubles(int64_t rows, int64_t n);

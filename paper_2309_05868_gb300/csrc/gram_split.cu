@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       bool ok = true;
       for (int qq = 0; qq < 2; ++qq) {
         const int q = 2 * (g & 1) + qq;
-        if (!mbar_wait_or_abort(empty0 + 8 * q, ((g >> 1) & 1) ^ 1, abort_flag)) {
+        if (!mbar_wait_or_abort(empty0 + 8 * q, ((g >> 1) & 1) ^ 1, abort_flag, lim)) {
           if (lane == 0 && !*abort_flag) {
             *abort_flag = 1;
             status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
         E = scale_exp(mx) + 1;
       }
-      if (!mbar_wait_or_abort(sle0 + 8 * b, ((g >> 1) & 1) ^ 1, abort_flag)) {
+      if (!mbar_wait_or_abort(sle0 + 8 * b, ((g >> 1) & 1) ^ 1, abort_flag, lim)) {
         ok = false;
       } else {
         uint8_t *buf = slices + (size_t)b * GS_BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;

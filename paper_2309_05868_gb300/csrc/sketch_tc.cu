@@ -74,9 +74,15 @@ __device__ __forceinline__ void sk_issue_kstep(uint32_t tmem, uint64_t ad, uint6
 
 }  // namespace
 
+// RAD: A is the Rademacher sketch, generated here instead of read: entry (r, k) is -rad_scale
+// when bit k mod 64 of splitmix64(rad_seed ^ splitmix64(r ceil(K / 64) + floor(k / 64))) is set,
+// else +rad_scale (the same values a materialised Rademacher S2 holds, so the same products).
+// A 64-long chunk of a row shares one 64-bit word: one generator call per row and chunk.
+template <bool RAD>
 __global__ void __launch_bounds__(SK_THREADS, 1)
     k_sketch_oz(const double *__restrict__ A, int64_t lda, const double *__restrict__ B, int64_t ldb, int M,
-                int64_t K, int n, double *C, int64_t chunks_per_cta, int ctas_per_tile, DevStatus *st) {
+                int64_t K, int n, double *C, int64_t chunks_per_cta, int ctas_per_tile, uint64_t rad_seed,
+                double rad_scale, DevStatus *st) {
   // one decision for the whole CTA (its threads meet at block barriers below)
   if (__syncthreads_or(threadIdx.x == 0 && status_failed(st))) return;
   extern __shared__ __align__(1024) uint8_t sk_smem[];
@@ -128,12 +134,19 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
     for (int hh = 0; hh < 2; ++hh) {
       const int row = row0 + 16 * warp + 8 * hh + r;
       const double *ap = A + (int64_t)row * lda;
+      uint64_t word = 0;
+      if (RAD) word = splitmix64(rad_seed ^ splitmix64((uint64_t)row * (uint64_t)nchunks + (uint64_t)ci));
+      const unsigned long long pos = (unsigned long long)__double_as_longlong(rad_scale);
 #pragma unroll
       for (int kg = 0; kg < 8; ++kg)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int64_t k = k0 + 8 * kg + 2 * pi + e;
-          a[hh][kg][e] = (row < M && k < K) ? (unsigned long long)__double_as_longlong(__ldg(ap + k)) : 0ULL;
+          const int kk = 8 * kg + 2 * pi + e;
+          const int64_t k = k0 + kk;
+          if (RAD)
+            a[hh][kg][e] = (row < M && k < K) ? (pos | (((word >> kk) & 1ULL) << 63)) : 0ULL;
+          else
+            a[hh][kg][e] = (row < M && k < K) ? (unsigned long long)__double_as_longlong(__ldg(ap + k)) : 0ULL;
         }
     }
     // ---- B: column 8 warp + r, K pairs 8 kg + 2 pi (+1)
@@ -255,8 +268,11 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
 
 bool sketch_oz_supported(int64_t n) { return n >= 1 && n <= SK_NP; }
 
-cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
-                             int64_t n, double *C, int num_sms, DevStatus *st, cudaStream_t s) {
+namespace {
+template <bool RAD>
+cudaError_t launch_sketch_oz_t(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
+                               int64_t n, double *C, uint64_t rad_seed, double rad_scale, int num_sms, DevStatus *st,
+                               cudaStream_t s) {
   if (M <= 0 || K <= 0) return cudaSuccess;
   const int64_t tiles = ceil_div(M, SK_ROWS);
   const int64_t nchunks = ceil_div(K, SK_K);
@@ -265,11 +281,22 @@ cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int6
   const int64_t ctas_per_tile = ceil_div(nchunks, chunks_per_cta);
   const int64_t grid = tiles * ctas_per_tile;
   if (grid >= ((int64_t)1 << 31) || M >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_sketch_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_oz<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM);
   if (e != cudaSuccess) return e;
-  k_sketch_oz<<<(unsigned)grid, SK_THREADS, SK_SMEM, s>>>(A, lda, B, ldb, (int)M, K, (int)n, C, chunks_per_cta,
-                                                          (int)ctas_per_tile, st);
+  k_sketch_oz<RAD><<<(unsigned)grid, SK_THREADS, SK_SMEM, s>>>(A, lda, B, ldb, (int)M, K, (int)n, C, chunks_per_cta,
+                                                               (int)ctas_per_tile, rad_seed, rad_scale, st);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
+                             int64_t n, double *C, int num_sms, DevStatus *st, cudaStream_t s) {
+  return launch_sketch_oz_t<false>(A, lda, B, ldb, M, K, n, C, 0, 0.0, num_sms, st, s);
+}
+
+cudaError_t launch_sketch_oz_rademacher(uint64_t seed, const double *B, int64_t ldb, int64_t M, int64_t K, int64_t n,
+                                        double *C, int num_sms, DevStatus *st, cudaStream_t s) {
+  return launch_sketch_oz_t<true>(nullptr, 0, B, ldb, M, K, n, C, seed, 1.0 / sqrt((double)M), num_sms, st, s);
 }
 
 }  // namespace rq

@@ -31,13 +31,12 @@
 //   warps 8-15 read tensor memory back (TMEM lanes 32 (w & 3) .., 16 columns of each half),
 //     recombine and store 64-byte row segments of Y,
 //   warp 16 loads 32-row sub-tiles of X into a four-slot ring (slot q holds sub-tile q) with
-//     per-row bulk copies,
+//     per-row bulk copies (one lane per row; rows padded to 528 bytes in shared memory, so the
+//     slicers' reads of eight rows at one column fall into eight different bank groups),
 //   warp 17 owns tensor memory and issues the MMAs,
 // handing tiles over through mbarriers.  B's digit slices are built once per CTA.  A's K-block
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
 // completed.  In place (Y == X) is safe: a tile's rows are read before any are written.
-#include <cuda.h>
-
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -63,11 +62,11 @@ __host__ __device__ constexpr uint32_t b_block(int h, int c) {
   return h == 0 ? (c == 0 ? 0u : 8u * B_TSLICE) : (15u + (c == 0 ? 0u : 8u + 7u * (uint32_t)(c - 1))) * B_TSLICE;
 }
 constexpr uint32_t B_BYTES = b_block(1, 3) + 7 * B_TSLICE;
-// A staged 32-row sub-tile is four boxes of 16 columns (4 KB each, 128-byte rows) in the
-// tensor-map copy's 128-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ (r & 7),
-// so the slicers' reads of eight rows at one column fall into eight different bank groups.
-constexpr uint32_t STAGE_BOX = TQ_SUB * 128;
-constexpr uint32_t STAGE_BYTES = 4 * STAGE_BOX;
+// A staged 32-row sub-tile holds its rows at a pitch of 528 bytes (64 FP64 values and 16
+// bytes of padding): row r starts in bank group r mod 8, so eight rows read at one column
+// touch eight different bank groups.
+constexpr uint32_t STAGE_PITCH = TQ_NP * 8 + 16;
+constexpr uint32_t STAGE_BYTES = TQ_SUB * STAGE_PITCH;
 constexpr size_t OFF_B = 0;
 constexpr size_t OFF_A = OFF_B + B_BYTES;
 constexpr size_t OFF_STAGE = OFF_A + (size_t)NDIG8 * A_SLICE;
@@ -82,21 +81,11 @@ constexpr size_t TQ_SMEM = OFF_MISC + 16;
 static_assert(OFF_A % 1024 == 0 && OFF_STAGE % 1024 == 0 && B_BYTES == 45056, "layout");
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
-enum LoadMode { LOAD_TMA = 0, LOAD_PLAIN = 1 };
+// LOAD_BULK: one bulk copy per row (rows 16-byte aligned, n even); LOAD_PLAIN: element loads.
+enum LoadMode { LOAD_BULK = 0, LOAD_PLAIN = 1 };
 
 // Byte offset of element (row r, column col) of a staged sub-tile.
-__device__ __forceinline__ uint32_t stage_off(int r, int col) {
-  return (uint32_t)(col >> 4) * STAGE_BOX + (uint32_t)r * 128u + ((((uint32_t)col >> 1) & 7u) ^ ((uint32_t)r & 7u)) * 16u +
-         ((uint32_t)col & 1u) * 8u;
-}
-
-// Tensor-map copy of a box (16 columns x 32 rows of FP64) at column x, row y into shared memory.
-__device__ __forceinline__ void tma_load_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
+__device__ __forceinline__ uint32_t stage_off(int r, int col) { return (uint32_t)r * STAGE_PITCH + (uint32_t)col * 8u; }
 
 __device__ __forceinline__ void set_abort(volatile int *abort_flag, DevStatus *st) {
   *abort_flag = 1;
@@ -122,11 +111,13 @@ __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uin
 
 }  // namespace
 
+// FULLN: n == 64 with 16-byte aligned rows of Y: no per-value column checks, and rows of a
+// partly filled sub-tile are cut whatever their slot holds (their products are never stored).
 // RESID: instead of storing Y, accumulate sums[0] += sum (Vref - Y)^2 and sums[1] += sum Vref^2
 // over the rows (the residual of a factorization V = Q R, with X = Q and B = R).
-template <bool RESID>
+template <bool FULLN, bool RESID>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
-    k_trsm_oz(const __grid_constant__ CUtensorMap xmap, const double *__restrict__ X, int64_t ldx, double *Y,
+    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y,
               int64_t ldy, int64_t m, int n, const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode,
               bool vec_store, const double *__restrict__ Vref, int64_t ldvr, double *sums, DevStatus *st) {
   if (status_failed(st)) return;
@@ -212,8 +203,15 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     for (int q = 0; q < TQ_NSTAGE; ++q) last_i[q] = -1;
     for (int i = 0; i < ntiles && !*abort_flag; ++i) {
       bool ok = true;
+      // the next tile's rows towards L2 while this tile's slots free up (contiguous rows only)
+      if (lane == 0 && load_mode == LOAD_BULK && ldx == n && i + 1 < ntiles) {
+        const int64_t p0 = r_begin + (int64_t)(i + 1) * TQ_ROWS;
+        const int64_t prow = imin64(TQ_ROWS, r_end - p0);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(X + p0 * ldx),
+                     "r"((uint32_t)(prow * n * 8)) : "memory");
+      }
       for (int q = 0; q < TQ_NSTAGE; ++q) {
-        if (!mbar_wait_or_abort(bar(BAR_EMPTY + q), (uint32_t)((i & 1) ^ 1), abort_flag)) {
+        if (!mbar_wait_or_abort(bar(BAR_EMPTY + q), (uint32_t)((i & 1) ^ 1), abort_flag, lim)) {
           if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
           ok = false;
           break;
@@ -222,13 +220,12 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int cnt = sub_rows(i, q);
         uint8_t *dst = stage + (size_t)q * STAGE_BYTES;
         const uint32_t fb = bar(BAR_FULL + q);
-        if (cnt > 0 && load_mode == LOAD_TMA) {
-          // boxes of the n columns (rows past m arrive as zeros)
-          const int nbox = (n + 15) >> 4;
-          if (lane == 0) {
-            mbar_expect_tx(fb, (uint32_t)nbox * STAGE_BOX);
-            for (int b = 0; b < nbox; ++b) tma_load_box(smem_addr(dst + b * STAGE_BOX), &xmap, 16 * b, (int)r0, fb);
-          }
+        if (cnt > 0 && load_mode == LOAD_BULK) {
+          // the cnt rows of the sub-tile, one bulk copy per lane (rows past cnt keep what the slot
+          // held; the slicers mask them)
+          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
+          __syncwarp();
+          if (lane < cnt) bulk_load(smem_addr(dst + (size_t)lane * STAGE_PITCH), X + (r0 + lane) * ldx, (uint32_t)n * 8u, fb);
         } else {
           for (int e = lane; e < cnt * n; e += 32) {
             const int r = e / n, cc = e - r * n;
@@ -309,7 +306,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const int rr = 8 * sg + r;  // row within the sub-tile
       const bool live = rr < sub_rows(i, q);
       const uint8_t *src = stage + (size_t)q * STAGE_BYTES;
-      int mx = 0;
+      uint32_t mxh = 0;  // largest high word without its sign: bits 20-30 are the exponent field
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int kg = 2 * c + kk;
@@ -317,11 +314,17 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         for (int u = 0; u < 4; ++u) {
           const ulonglong2 raw = *(const ulonglong2 *)(src + stage_off(rr, 8 * kg + 2 * u));
           const int c0 = 8 * kg + 2 * u;
-          e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
-          e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
-          mx = max(mx, max((int)((e[c][2 * u] >> 52) & 0x7ff), (int)((e[c][2 * u + 1] >> 52) & 0x7ff)));
+          if (FULLN) {
+            e[c][2 * u] = raw.x;
+            e[c][2 * u + 1] = raw.y;
+          } else {
+            e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
+            e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
+          }
+          mxh = max(mxh, max((uint32_t)(e[c][2 * u] >> 32) & 0x7fffffffu, (uint32_t)(e[c][2 * u + 1] >> 32) & 0x7fffffffu));
         }
       }
+      int mx = (int)(mxh >> 20);
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(bar(BAR_EMPTY + grp));
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const int E = scale_exp(mx);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (i > 0 && !mbar_wait_or_abort(bar(BAR_KFREE + c), (uint32_t)((i - 1) & 1), abort_flag)) {
+        if (i > 0 && !mbar_wait_or_abort(bar(BAR_KFREE + c), (uint32_t)((i - 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
                   }
                 } else {
                   double *yp = Y + grow * ldy + k0;
-                  if (vec_store && k0 + 1 < n) {
+                  if (FULLN || (vec_store && k0 + 1 < n)) {
                     *(double2 *)yp = make_double2(y0, y1);
                   } else {
                     if (k0 < n) yp[0] = y0;
@@ -457,27 +460,6 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 
-namespace {
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, looked up once (NULL if the driver does not provide it).
-EncodeTiledFn encode_tiled() {
-  static const EncodeTiledFn fn = [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    return (EncodeTiledFn)p;
-  }();
-  return fn;
-}
-}  // namespace
-
 template <bool RESID>
 cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
                              const double *Bpacked, const double *Vref, int64_t ldvr, double *sums, int num_sms,
@@ -485,24 +467,16 @@ cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ld
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
-  // X as a 2-D tensor (n columns, m rows, row pitch 8 ldx bytes) for the box copies; row
-  // coordinates are 32-bit, the base and pitch must be 16-byte multiples
-  alignas(64) CUtensorMap xmap;
-  memset(&xmap, 0, sizeof xmap);
-  int load_mode = LOAD_PLAIN;
-  const EncodeTiledFn enc = encode_tiled();
-  if (enc && ((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && m + TQ_ROWS < ((int64_t)1 << 31)) {
-    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
-    const cuuint64_t strides[1] = {(cuuint64_t)ldx * 8};
-    const cuuint32_t box[2] = {16, (cuuint32_t)TQ_SUB}, estride[2] = {1, 1};
-    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)X, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-      load_mode = LOAD_TMA;
-  }
+  // bulk copies need 16-byte aligned rows of a multiple of 16 bytes
+  const int load_mode =
+      (((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && (n * 8) % 16 == 0) ? LOAD_BULK : LOAD_PLAIN;
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0;
-  cudaError_t e = cudaFuncSetAttribute(k_trsm_oz<RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
+  // the full-width form stores 16-byte pairs unconditionally: only with aligned rows of Y
+  const bool full = n == TQ_NP && vec_store && !RESID;
+  auto kern = full ? k_trsm_oz<true, RESID> : k_trsm_oz<false, RESID>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  k_trsm_oz<RESID><<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(xmap, X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta,
+  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta,
                                                                 load_mode, vec_store, Vref, ldvr, sums, st);
   return cudaGetLastError();
 }

@@ -191,3 +191,33 @@ def test_sketch_at_paper_sizes_within_product_bound(rq, n):
     np.add.at(absW1, b, np.abs(V))
     bound = _split_product_bound(S2, W1) + 2 * (s1 + m / s1 + 8) * 2.0 ** -53 * (np.abs(S2) @ absW1)
     assert (np.abs(Ws - Wo) <= bound).all()
+
+
+def test_rademacher_generated_inside_the_sketch_gemm(rq):
+    """With the Rademacher kind and no S2 passed, the tensor-core sketch GEMM draws the signs
+    itself (Sec. 7's dense alternative, generated on the fly): no S2 buffer is held, and Ws is
+    what the materialised Rademacher S2 gives -- bit for bit on integer V with s2 = 64 (entries
+    +-1/8, every product exact), within the FP64 atomics' reordering otherwise."""
+    m, n = 50000, 16
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    Vi = torch.from_numpy(synthetic.integer_matrix(m, n, seed=4)).cuda()
+    ctx = rq.Context(0)
+    ctx.set_sketch_kind(rq.SKETCH_RADEMACHER)
+    fly = rq.randqr_sketch(Vi, s1, s2, seed=5, ctx=ctx)
+    assert ctx.workspace_bytes() < 8 * s1 * s2  # the sketch matrix was never materialised
+    S2 = rq.randqr_rademacher_sketch(6, s2, s1)
+    mat = rq.randqr_sketch(Vi, s1, s2, seed=5, S2=S2, ctx=ctx)
+    assert torch.equal(fly, mat)
+    np.testing.assert_array_equal(fly.cpu().numpy(),
+                                  oracle.gemm(oracle.rademacher_sketch(6, s2, s1),
+                                              oracle.countsketch(Vi.cpu().numpy(), s1, 5)))
+    m, n = 40000, 64
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = torch.from_numpy(synthetic.make_v(m, n, 1e10, seed=6)).cuda()
+    fly = rq.randqr_sketch(V, s1, s2, seed=7, ctx=ctx)
+    mat = rq.randqr_sketch(V, s1, s2, seed=7, S2=rq.randqr_rademacher_sketch(8, s2, s1), ctx=ctx)
+    assert (fly - mat).abs().max().item() <= 1e-13 * mat.abs().max().item()
+    Q, R, _ = rq.randqr_factor(V, s1, s2, seed=7, ctx=ctx)
+    Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+    assert oracle.orth_err(Qh)[0] <= 1e-12 and oracle.resid(V.cpu().numpy(), Qh, Rh) <= 1e-13
+    ctx.close()
