@@ -90,7 +90,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, baselines, CPU baseline (quick runs)")
     p.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
-    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-requests", type=int, default=2000,
+                   help="requests of the served stream (the configuration's full stream is 20000)")
     p.add_argument("--gen", default="qr", choices=["qr", "gauss"],
                    help="qr: V = U diag(sigma) W^T; gauss: plain N(0,1/m) entries (kappa ~ 1, "
                         "no QR in the generator -- for profiler runs)")
@@ -267,14 +268,17 @@ def run_reference(a):
 # ---------------------------------------------------------------------------------------
 # Served stream: Poisson arrivals of requests through randqr_submit / randqr_poll
 # ---------------------------------------------------------------------------------------
-def serve_bench(rq, synthetic, torch, dev, n_req=200, load=0.8, seed=7):
-    """Requests with m log-uniform in [1e4, 4e6], n uniform in {4, 8, 16, 32, 64}, kappa
-    log-uniform in [1, 1e12] (one pre-built matrix per (n, kappa level), requests take its
-    first m rows).  Service capacity is first measured with sequential plain-FP64 solves;
-    arrivals are then Poisson at `load` x that capacity.  Reports p50/p99 latency and
-    throughput of the served path (FP64, and with max_orth_err = 1e-12, which lets rand_cholQR
-    run its row passes in pair arithmetic), next to sequential plain-FP64 solves of the same
-    stream (single FIFO server; latency from the same arrival times)."""
+def serve_bench(rq, synthetic, torch, dev, n_req=2000, loads=(0.5, 0.8, 0.95), seed=7):
+    """The served stream: requests with m log-uniform in [1e4, 4e6], n uniform in
+    {4, 8, 16, 32, 64}, kappa log-uniform in [1, 1e12] (one pre-built matrix per (n, kappa
+    level); a request takes its first m rows).  The sequential plain-FP64 service time of every
+    request is measured first; arrivals are then Poisson at each offered load x that capacity,
+    through randqr_submit / randqr_poll with 8 slots and a 64 GB budget, in FP64 and with
+    max_orth_err = 1e-12 (the caller accepts 1e-12: rand_cholQR may take its reduced-precision
+    row passes).  A saturation run (every request submitted at once) gives the served capacity.
+    Reports p50/p99 latency and throughput per load, next to a single FIFO server running the
+    measured sequential service times on the same arrivals, and the worst ||I - Q^T Q||_2 over a
+    sample of each run's results."""
     import numpy as np
     rng = np.random.default_rng(seed)
     ns = [4, 8, 16, 32, 64]
@@ -287,90 +291,94 @@ def serve_bench(rq, synthetic, torch, dev, n_req=200, load=0.8, seed=7):
         n = int(rng.choice(ns))
         k = klev[min(3, int(rng.uniform(0, 12) // 3))]
         reqs.append((m, n, k))
-    outs = {}
-    for (m, n, k) in reqs:
-        if (m, n) not in outs:
-            outs[(m, n)] = (torch.empty((m, n), dtype=torch.float64, device=dev),
-                            torch.empty((n, n), dtype=torch.float64, device=dev))
     ctx = rq.Context(dev.index or 0)
-    # sequential plain FP64: per-request service time (S2 cached first, untimed)
-    for (m, n, k) in reqs:
-        rq.randqr_factor(pools[(n, k)][:m], seed=0, ctx=ctx, Q=outs[(m, n)][0], R=outs[(m, n)][1])
+    qbuf = {}
+    for (m, n, k) in sorted(set(reqs), key=lambda r: -r[0] * r[1])[:16]:
+        qbuf[(m, n)] = (torch.empty((m, n), dtype=torch.float64, device=dev),
+                        torch.empty((n, n), dtype=torch.float64, device=dev))
+    for (m, n, k) in sorted(set(reqs), key=lambda r: -r[0] * r[1])[:16]:  # workspaces, sketches
+        rq.randqr_factor(pools[(n, k)][:m], seed=0, ctx=ctx, Q=qbuf[(m, n)][0], R=qbuf[(m, n)][1])
     svc = []
     for (m, n, k) in reqs:
-        Q, R = outs[(m, n)]
+        Q = torch.empty((m, n), dtype=torch.float64, device=dev)
+        R = torch.empty((n, n), dtype=torch.float64, device=dev)
         t0 = time.perf_counter()
         rq.randqr_factor(pools[(n, k)][:m], seed=0, ctx=ctx, Q=Q, R=R)  # waits for the status
         svc.append(time.perf_counter() - t0)
+    ctx.close()
     mean_svc = float(np.mean(svc))
-    rate = load / mean_svc
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    # sequential FIFO server latencies for the same arrivals
-    free_at, seq_lat = 0.0, []
-    for a, s in zip(arrivals, svc):
-        start = max(a, free_at)
-        free_at = start + s
-        seq_lat.append(free_at - a)
 
-    def run_served(max_orth):
+    def pct(x, p):
+        return float(np.percentile(np.asarray(x) * 1e3, p))
+
+    def run_served(max_orth, arrivals, max_outstanding=None):
+        """One pass of the stream; arrivals None: saturation (at most max_outstanding requests
+        submitted and not finished at any time, refilled as they finish)."""
         sctx = rq.Context(dev.index or 0)
         rq.randqr_serve_config(sctx, slots=8, hbm_budget_bytes=64 << 30)
-        # warm the slots' workspaces and the sketch cache with the largest shapes
         for (m, n, k) in sorted(set(reqs), key=lambda r: -r[0] * r[1])[:16]:
-            Q, R = outs[(m, n)]
+            Q, R = qbuf[(m, n)]
             t, _ = rq.randqr_submit(sctx, pools[(n, k)][:m], Q=Q, R=R, seed=0, max_orth_err=max_orth)
             rq.randqr_wait(sctx, t)
         torch.cuda.synchronize()
-        lat, pending, nxt = [], {}, 0
-        qbuf = [(torch.empty((m, n), dtype=torch.float64, device=dev),
-                 torch.empty((n, n), dtype=torch.float64, device=dev)) for (m, n, k) in reqs]
+        lat, pending, nxt, sample = [], {}, 0, {}
         t0 = time.perf_counter()
+        sub_t = {}
         while len(lat) < n_req:
             now = time.perf_counter() - t0
-            while nxt < n_req and arrivals[nxt] <= now:
+            while nxt < n_req and ((arrivals is None and len(pending) < max_outstanding) or
+                                   (arrivals is not None and arrivals[nxt] <= now)):
                 m, n, k = reqs[nxt]
-                Q, R = qbuf[nxt]
+                # every request in flight has buffers of its own (freed when it finishes)
+                Q = torch.empty((m, n), dtype=torch.float64, device=dev)
+                R = torch.empty((n, n), dtype=torch.float64, device=dev)
+                if nxt % 97 == 0:  # kept for the accuracy sample
+                    sample[nxt] = (Q, R)
                 t, _ = rq.randqr_submit(sctx, pools[(n, k)][:m], Q=Q, R=R, seed=0, max_orth_err=max_orth)
                 pending[t] = nxt
+                sub_t[t] = arrivals[nxt] if arrivals is not None else time.perf_counter() - t0
                 nxt += 1
             for t in list(pending):
                 st, _ = rq.randqr_poll(sctx, t)
                 if st != rq.PENDING:
                     if st != 0:
                         raise rq.RandQRError(st)
-                    lat.append(time.perf_counter() - t0 - arrivals[pending.pop(t)])
-            if not pending and nxt < n_req:
+                    pending.pop(t)
+                    lat.append(time.perf_counter() - t0 - sub_t.pop(t))
+            if arrivals is not None and not pending and nxt < n_req:
                 time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
-        makespan = time.perf_counter() - t0
+        span = time.perf_counter() - t0
         worst = 0.0
-        for i in range(0, n_req, max(1, n_req // 16)):
-            Q, R = qbuf[i]
+        for i, (Q, R) in sample.items():
             G = Q.T @ Q
-            worst = max(worst, torch.linalg.matrix_norm(G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
+            worst = max(worst, torch.linalg.matrix_norm(
+                G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
         sctx.close()
-        del qbuf
-        return lat, makespan, worst
+        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_req_s": n_req / span,
+                "eff_GBs": bytes_total / span / 1e9, "max_orth_err_2_sampled": worst}
 
-    def pct(x, p):
-        return float(np.percentile(np.asarray(x) * 1e3, p))
-
-    lat64, span64, orth64 = run_served(0.0)
-    latmx, spanmx, orthmx = run_served(1e-12)
     bytes_total = sum(32.0 * m * n for (m, n, k) in reqs)
-    res = {"requests": n_req, "offered_load": load, "rate_per_s": rate, "slots": 8,
-           "budget_bytes": 64 << 30,
+    res = {"requests": n_req, "slots": 8, "budget_bytes": 64 << 30,
            "workload": "m log-uniform [1e4, 4e6], n in {4,8,16,32,64}, kappa in {1,1e4,1e8,1e12}",
-           "sequential_fp64": {"p50_ms": pct(seq_lat, 50), "p99_ms": pct(seq_lat, 99),
-                               "mean_service_ms": mean_svc * 1e3,
-                               "throughput_req_s": 1.0 / mean_svc},
-           "served_fp64": {"p50_ms": pct(lat64, 50), "p99_ms": pct(lat64, 99),
-                           "throughput_req_s": n_req / span64,
-                           "eff_GBs": bytes_total / span64 / 1e9, "max_orth_err_2": orth64},
-           "served_mixed": {"p50_ms": pct(latmx, 50), "p99_ms": pct(latmx, 99),
-                            "throughput_req_s": n_req / spanmx,
-                            "eff_GBs": bytes_total / spanmx / 1e9, "max_orth_err_2": orthmx}}
-    ctx.close()
-    del pools, outs
+           "sequential_fp64": {"mean_service_ms": mean_svc * 1e3, "capacity_req_s": 1.0 / mean_svc},
+           "loads": {}}
+    for load in loads:
+        arr = np.cumsum(np.random.default_rng(seed + int(load * 100)).exponential(mean_svc / load, size=n_req))
+        free_at, seq_lat = 0.0, []
+        for a_t, sv in zip(arr, svc):
+            start = max(a_t, free_at)
+            free_at = start + sv
+            seq_lat.append(free_at - a_t)
+        res["loads"][str(load)] = {
+            "rate_per_s": load / mean_svc,
+            "sequential_fp64": {"p50_ms": pct(seq_lat, 50), "p99_ms": pct(seq_lat, 99)},
+            "served_fp64": run_served(0.0, arr), "served_mixed": run_served(1e-12, arr)}
+    res["saturation"] = {"max_outstanding": 32, "served_fp64": run_served(0.0, None, 32),
+                         "served_mixed": run_served(1e-12, None, 32)}
+    mid = res["loads"].get("0.8") or next(iter(res["loads"].values()))
+    res["served_fp64"] = dict(mid["served_fp64"], max_orth_err_2=mid["served_fp64"]["max_orth_err_2_sampled"])
+    res["served_mixed"] = dict(mid["served_mixed"], max_orth_err_2=mid["served_mixed"]["max_orth_err_2_sampled"])
+    del pools, qbuf
     return res
 
 

@@ -61,6 +61,7 @@ struct Workspace {
   float2 *Rdf, *rinv;  // pair form of the current triangular factor (RANDQR_F32X2)
   double *hq;          // multi-CTA Householder scratch (published reflectors, flags)
   double *acc;         // accuracy measurement: Q^T Q (packed), then the two residual sums
+  double *blk;         // blocked solves (64 < n <= 128): five packed 64 x 64 blocks
 };
 
 size_t packed(int64_t n) { return (size_t)(n * (n + 1) / 2); }
@@ -100,9 +101,10 @@ randqr_status ensure_host_stage(randqr_ctx *ctx, size_t bytes) {
 }
 
 size_t acc_doubles(int64_t n) { return packed(n) + 2; }
+constexpr size_t kBlkDoubles = 5 * 2080;  // five packed 64 x 64 upper blocks
 
 randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspace *w) {
-  const size_t sz[11] = {align_up(sizeof(double) * (size_t)(s1 * n)),
+  const size_t sz[12] = {align_up(sizeof(double) * (size_t)(s1 * n)),
                          align_up(sizeof(double) * (size_t)(s2 * n)),
                          align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
                          align_up(sizeof(double) * packed(n)), align_up(sizeof(double) * packed(n)),
@@ -110,7 +112,8 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
                          align_up(sizeof(float2) * rq::pack_df_elems(n)),
                          align_up(sizeof(float2) * rq::pack_df_rinv_elems(n)),
                          align_up(sizeof(double) * rq::hhqr_scratch_doubles(s2, n)),
-                         align_up(sizeof(double) * acc_doubles(n))};
+                         align_up(sizeof(double) * acc_doubles(n)),
+                         align_up(sizeof(double) * (n > 64 ? kBlkDoubles : 0))};
   size_t total = 0;
   for (size_t b : sz) total += b;
   randqr_status st = ensure_ws(ctx, total);
@@ -128,6 +131,8 @@ randqr_status carve(randqr_ctx *ctx, int64_t n, int64_t s1, int64_t s2, Workspac
   w->hq = (double *)p;
   p += sz[9];
   w->acc = (double *)p;
+  p += sz[10];
+  w->blk = (double *)p;
   return RANDQR_OK;
 }
 
@@ -352,9 +357,85 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
 // Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores: only where R_c is well
 // conditioned by construction (rand_cholQR's solves, the last pass of CholeskyQR2 and of
 // shifted CholeskyQR3); R_c^{-1} goes to w.Rt2 (after the Cholesky kernel has read it).
+// The split-product solves blocked for 64 < n <= 128 (n even, 16-byte aligned rows): columns split
+// at n1 = n - 64 into X = [X1 X2], B = [[B11, B12], [0, B22]] upper triangular; every block
+// product is one launch of the split-product kernel on at most 64 x 64 operands, and B12 = U + L
+// (its upper and strictly lower parts) runs as two upper-triangular products, L through the
+// column reversals (J L J is upper triangular).
+bool blocked_tc_ok(const randqr_ctx *ctx, int64_t n, const void *X, int64_t ldx, const void *Y, int64_t ldy) {
+  return ctx->use_tc && n > 64 && n <= 128 && n % 2 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0 &&
+         ldx % 2 == 0 && ldy % 2 == 0;
+}
+
+// Y = X Binv with Binv = R^{-1}, R well conditioned, by the explicit inverse (packed in Binv): all
+// blocks are O(1) products, so the block sums may round separately.  Order: Y2 first (reads X2,
+// X1), then Y1 (reads X1), so Y == X works in place.
+randqr_status blocked_product_tc(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m,
+                                 int64_t n, const double *Binv, const Workspace &w, cudaStream_t s) {
+  const int64_t n1 = n - 64;
+  double *B22 = w.blk, *U12 = w.blk + 2080, *L12 = w.blk + 2 * 2080;
+  RQ_CUDA(rq::launch_block_prep(Binv, n, 0, 1.0, B22, ctx->status_dev, s));
+  RQ_CUDA(rq::launch_block_prep(Binv, n, 1, 1.0, U12, ctx->status_dev, s));
+  RQ_CUDA(rq::launch_block_prep(Binv, n, 2, 1.0, L12, ctx->status_dev, s));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X + n1, ldx, Y + n1, ldy, m, 64, 64, B22, false, nullptr, 0, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X, ldx, Y + n1, ldy, m, n1, 64, U12, false, Y + n1, ldy, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X, ldx, Y + n1, ldy, m, n1, 64, L12, true, Y + n1, ldy, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X, ldx, Y, ldy, m, n1, n1, Binv, false, nullptr, 0, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  return RANDQR_OK;
+}
+
+// W = V R_s^{-1} blocked, for an R_s that may be as ill conditioned as V: the inverse is applied
+// only to the diagonal blocks, the off-diagonal block by substitution order,
+//   W1 = V1 R11^{-1},   T = V2 - W1 R12,   W2 = T R22^{-1},
+// each block product exact up to the split format and T formed as one rounded sum per term, a
+// backward error of the size of a triangular solve's (row-wise, relative to |V| + |W1| |R12|).
+randqr_status blocked_first_solve_tc(randqr_ctx *ctx, const double *V, int64_t ldv, double *Q, int64_t ldq, int64_t m,
+                                     int64_t n, const double *Rs, const Workspace &w, cudaStream_t s) {
+  const int64_t n1 = n - 64;
+  double *R22 = w.blk, *mU12 = w.blk + 2080, *mL12 = w.blk + 2 * 2080, *R11i = w.blk + 3 * 2080,
+         *R22i = w.blk + 4 * 2080;
+  RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(Rs, n1, R11i, ctx->status_dev, s); }));
+  RQ_CUDA(rq::launch_block_prep(Rs, n, 0, 1.0, R22, ctx->status_dev, s));
+  RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(R22, 64, R22i, ctx->status_dev, s); }));
+  RQ_CUDA(rq::launch_block_prep(Rs, n, 1, -1.0, mU12, ctx->status_dev, s));
+  RQ_CUDA(rq::launch_block_prep(Rs, n, 2, -1.0, mL12, ctx->status_dev, s));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(V, ldv, Q, ldq, m, n1, n1, R11i, false, nullptr, 0, ctx->num_sms, ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(Q, ldq, Q + n1, ldq, m, n1, 64, mU12, false, V + n1, ldv, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(Q, ldq, Q + n1, ldq, m, n1, 64, mL12, true, Q + n1, ldq, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(Q + n1, ldq, Q + n1, ldq, m, 64, 64, R22i, false, nullptr, 0, ctx->num_sms,
+                                    ctx->status_dev, s);
+  }));
+  return RANDQR_OK;
+}
+
 randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y,
                                   int64_t ldy, int64_t m, int64_t n, const Workspace &w,
                                   cudaStream_t s) {
+  if (n > 64) {
+    RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
+    return blocked_product_tc(ctx, X, ldx, Y, ldy, m, n, w.Rt2, w, s);
+  }
   RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
     return rq::launch_trsm_oz(X, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
@@ -391,7 +472,7 @@ randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double 
     return rq::launch_potrf(w.G, n, shift_coeff, w.Rc, Rprev, Rnext, Rdense, ldr, stage,
                             ctx->status_dev, s);
   }));
-  if (well_conditioned && use_tc_solve(ctx, n))
+  if (well_conditioned && (use_tc_solve(ctx, n) || blocked_tc_ok(ctx, n, X, ldx, Y, ldy)))
     return solve_by_inverse_tc(ctx, X, ldx, Y, ldy, m, n, w, s);
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
     return rq::launch_trsm(X, ldx, Y, ldy, m, n, w.Rc, prec, ctx->num_sms, ctx->status_dev, s);
@@ -650,6 +731,14 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
   if ((st = carve(ctx, n, s1, s2, &w)) != RANDQR_OK) return st;
   if ((st = sketch_and_hhqr(ctx, V, m, n, ldv, s1, s2, seed, S2, w, s, true)) != RANDQR_OK)
     return st;
+  if (second_pass && blocked_tc_ok(ctx, n, V, ldv, Q, ldq)) {
+    // 64 < n <= 128: both solves blocked into split products (either precision)
+    if ((st = blocked_first_solve_tc(ctx, V, ldv, Q, ldq, m, n, w.Rs, w, s)) != RANDQR_OK) return st;
+    if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
+                          /*well_conditioned=*/true)) != RANDQR_OK)
+      return st;
+    return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
+  }
   if (second_pass && use_tc_solve(ctx, n)) {
     // Both solves as tensor-core products with explicit inverses (either precision): W =
     // V (R_s^{-1}) into Q, then the Cholesky pass on W in place.

@@ -236,6 +236,20 @@ cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, co
 // Y = X B (B upper triangular, packed) from exact split products on the tensor cores
 // (trsm_tc.cu), n <= 64; Y may equal X (same ld)
 bool trsm_oz_supported(int64_t n);
+// One block product of a blocked solve (64 < n <= 128): Y = X B, or Y = Ref + X B when Ref is
+// given (Ref may be Y), for X with nk <= 64 columns, Y with nn <= 64, B packed upper
+// (dimension nn, entries with row >= nk ignored); reverse: X read as X J and Y (and Ref) as Y J
+// (J the column reversal; needs Ref, even nk and nn, 16-byte aligned rows)
+cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk,
+                                 int64_t nn, const double *Bpacked, bool reverse, const double *Ref, int64_t ldref,
+                                 int num_sms, DevStatus *st, cudaStream_t s);
+// The blocks of an upper-triangular R (packed, dimension n, 64 < n <= 128) split at n1 = n - 64:
+// mode 0: R22 (rows and columns n1 .. n-1); mode 1: sign * R12 restricted to its upper part
+// (entries (j, k) with j <= k, j < n1); mode 2: sign * J L12 J with L12 the strictly lower part of
+// R12 (entry (c, k) = sign * R(n1 - 1 - c, n1 + 63 - k) where that lies below R12's diagonal).
+// Output packed upper of dimension 64.
+cudaError_t launch_block_prep(const double *Rp, int64_t n, int mode, double sign, double *Bout, const DevStatus *st,
+                              cudaStream_t s);
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
                            const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s);
 // Gram from exact split products on the tensor cores, n <= 64 (gram_split.cu)

@@ -377,6 +377,33 @@ cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_pa
   return cudaGetLastError();
 }
 
+// Blocks of a packed upper-triangular R split at n1 = n - 64, as packed 64 x 64 upper matrices
+// (launch_block_prep in common.cuh describes the modes).
+__global__ void k_block_prep(const double *Rp, int n, int mode, double sign, double *Bout, const DevStatus *st) {
+  if (status_failed(st)) return;
+  const int n1 = n - 64;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 64; e += gridDim.x * blockDim.x) {
+    const int j = e >> 6, k = e & 63;  // row j, column k of the output (j <= k stored)
+    if (j > k) continue;
+    double v = 0.0;
+    if (mode == 0) {
+      v = Rp[tri_idx(n1 + j, n1 + k)];
+    } else if (mode == 1) {
+      if (j < n1) v = sign * Rp[tri_idx(j, n1 + k)];
+    } else {
+      const int rj = n1 - 1 - j, ck = 63 - k;  // R12 entry (rj, ck), in R12's strictly lower part
+      if (rj >= 0 && rj > ck) v = sign * Rp[tri_idx(rj, n1 + ck)];
+    }
+    Bout[tri_idx(j, k)] = v;
+  }
+}
+
+cudaError_t launch_block_prep(const double *Rp, int64_t n, int mode, double sign, double *Bout, const DevStatus *st,
+                              cudaStream_t s) {
+  k_block_prep<<<16, 256, 0, s>>>(Rp, (int)n, mode, sign, Bout, st);
+  return cudaGetLastError();
+}
+
 __global__ void k_status_reset(DevStatus *st, int32_t wait_limit_field) {
   st->code = 0;
   st->info = 0;

@@ -1,7 +1,11 @@
-// trsm_tc.cu -- Y = X B for an n x n upper-triangular B given by its packed FP64 entries
-// (n <= 64), from exact split products on the tensor cores.  rand_cholQR runs both of its
+// trsm_tc.cu -- Y = X B for an upper-triangular B given by its packed FP64 entries (at most
+// 64 x 64), from exact split products on the tensor cores.  rand_cholQR runs both of its
 // triangular solves (W = V R_s^{-1} and Q = W R_c^{-1}, Algorithm 3) this way, as products with
-// the explicit inverses.
+// the explicit inverses; for 64 < n <= 128 the solves are blocked into such products (api.cu):
+// X has nk <= 64 columns and Y nn <= 64 (B is nk x nn, entries j <= k), the columns of X and Y
+// may be taken in reverse order (so that a strictly lower block becomes upper triangular), and
+// the product may be added to a reference matrix instead of stored (Y = Ref + X B, formed as
+// one integer sum and rounded once).
 //
 // Number format.  Row i of X gets a scale 2^E_i > max_j |x_ij| and column k of B a scale
 // 2^F_k > max_j |b_jk|.  x_ij = 2^(E_i - 54) X_ij up to truncation, with the integer
@@ -81,8 +85,18 @@ constexpr size_t TQ_SMEM = OFF_MISC + 16;
 static_assert(OFF_A % 1024 == 0 && OFF_STAGE % 1024 == 0 && B_BYTES == 45056, "layout");
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
-// LOAD_BULK: one bulk copy per row (rows 16-byte aligned, n even); LOAD_PLAIN: element loads.
-enum LoadMode { LOAD_BULK = 0, LOAD_PLAIN = 1 };
+// LOAD_ASYNC: 16-byte asynchronous copies, one row per warp instruction (lane = 16-byte chunk);
+// LOAD_BULK: one bulk copy per row; both need 16-byte aligned rows and an even column count.
+// LOAD_PLAIN: element loads.  Every loader lane arrives on the slot's barrier once per fill.
+enum LoadMode { LOAD_ASYNC = 0, LOAD_BULK = 1, LOAD_PLAIN = 2 };
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+// arrives on mbar once this thread's earlier cp.async copies have landed (no extra pending count)
+__device__ __forceinline__ void cp_async_arrive(uint32_t mbar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
+}
 
 // Byte offset of element (row r, column col) of a staged sub-tile.
 __device__ __forceinline__ uint32_t stage_off(int r, int col) { return (uint32_t)r * STAGE_PITCH + (uint32_t)col * 8u; }
@@ -111,15 +125,37 @@ __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uin
 
 }  // namespace
 
-// FULLN: n == 64 with 16-byte aligned rows of Y: no per-value column checks, and rows of a
+// ref + t 2^u0 (t the recombined product, |t| < 2^62) as one 64-bit integer sum, rounded once:
+// the unit of the sum is 2^u0, or coarser when ref would not fit 2^61 units of it; ref is
+// truncated to that unit (below 2^-59 of |ref|, an FP64 subtraction's rounding).
+__device__ __forceinline__ double add_fixed(double ref, long long t, int u0) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(ref);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  const int u1 = max(u0, ef - 1023 - 60);
+  const int d = min(u1 - u0, 63);
+  const long long ts = t >> d;
+  const int sh = ef - 1075 - u1;  // ref = mant 2^(ef - 1075); at most 8 by the choice of u1
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
+  long long rf = sh >= 0 ? (mant << sh) : (-sh < 63 ? (mant >> -sh) : 0);
+  rf = ef == 0 ? 0 : rf;
+  rf = (b >> 63) ? -rf : rf;
+  return int_times_pow2_cvt(ts + rf, u1);
+}
+
+enum Epilogue { EPI_STORE = 0, EPI_ADDREF = 1, EPI_RESID = 2 };
+
+// FULLN: nk == nn == 64 with 16-byte aligned rows of Y: no per-value column checks, and rows of a
 // partly filled sub-tile are cut whatever their slot holds (their products are never stored).
-// RESID: instead of storing Y, accumulate sums[0] += sum (Vref - Y)^2 and sums[1] += sum Vref^2
+// REV: X's columns are read as X J and Y's written as Y J (J the reversal of nk, nn columns).
+// EPI_ADDREF: Y = Ref + X B (Ref may be Y itself, read in the same column order).
+// EPI_RESID: instead of storing Y, accumulate sums[0] += sum (Ref - Y)^2 and sums[1] += sum Ref^2
 // over the rows (the residual of a factorization V = Q R, with X = Q and B = R).
-template <bool FULLN, bool RESID>
+template <bool FULLN, bool REV, int EPI>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
-    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y,
-              int64_t ldy, int64_t m, int n, const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode,
-              bool vec_store, const double *__restrict__ Vref, int64_t ldvr, double *sums, DevStatus *st) {
+    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int nk, int nn,
+              const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode, bool vec_store,
+              const double *Vref, int64_t ldvr, double *sums, DevStatus *st) {
+  constexpr bool RESID = EPI == EPI_RESID;
   if (status_failed(st)) return;
   const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t tq_smem[];
@@ -137,7 +173,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 
   if (tid == 0) {
     for (int q = 0; q < TQ_NSTAGE; ++q) {
-      mbar_init_count(bar(BAR_FULL + q), 1);
+      mbar_init_count(bar(BAR_FULL + q), 32);
       mbar_init_count(bar(BAR_EMPTY + q), 4);
     }
     for (int c = 0; c < 4; ++c) {
@@ -159,7 +195,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   // ---- B's digit slices (all threads, once): column scales, then the blocks
   for (int e = tid; e < TQ_NP * TQ_NP; e += TQ_THREADS) {
     const int k = e >> 6, j = e & 63;
-    if (k < n && j <= k) atomicMax(&colexp[k], expfield<false>(Bp + tri_idx(j, k)));
+    if (k < nn && j <= k && j < nk) atomicMax(&colexp[k], expfield<false>(Bp + tri_idx(j, k)));
   }
   for (int e = tid; e < (int)(B_TSLICE / 4); e += TQ_THREADS) {  // the zero eighth slices
     *(uint32_t *)(Bs + b_block(0, 0) + 7 * B_TSLICE + 4 * e) = 0u;
@@ -172,8 +208,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     const int h = bb < 2 ? 0 : 1, c = bb < 2 ? bb : bb - 2;
     const int k = 32 * h + kp, j = 16 * c + 2 * jp;
     const int F = scale_exp(colexp[k]);
-    const long long za = (k < n && j <= k) ? fix54(Bp[tri_idx(j, k)], F) : 0;
-    const long long zb = (k < n && j + 1 <= k) ? fix54(Bp[tri_idx(j + 1, k)], F) : 0;
+    const long long za = (k < nn && j <= k && j < nk) ? fix54(Bp[tri_idx(j, k)], F) : 0;
+    const long long zb = (k < nn && j + 1 <= k && j + 1 < nk) ? fix54(Bp[tri_idx(j + 1, k)], F) : 0;
     uint32_t w[NDIG8];
     digits8(za, zb, w);
     const uint32_t off = b_block(h, c) + (uint32_t)(kp >> 3) * B_SBO + (uint32_t)(jp >> 2) * B_LBO +
@@ -204,11 +240,11 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     for (int i = 0; i < ntiles && !*abort_flag; ++i) {
       bool ok = true;
       // the next tile's rows towards L2 while this tile's slots free up (contiguous rows only)
-      if (lane == 0 && load_mode == LOAD_BULK && ldx == n && i + 1 < ntiles) {
+      if (lane == 0 && load_mode != LOAD_PLAIN && ldx == nk && i + 1 < ntiles) {
         const int64_t p0 = r_begin + (int64_t)(i + 1) * TQ_ROWS;
         const int64_t prow = imin64(TQ_ROWS, r_end - p0);
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(X + p0 * ldx),
-                     "r"((uint32_t)(prow * n * 8)) : "memory");
+                     "r"((uint32_t)(prow * nk * 8)) : "memory");
       }
       for (int q = 0; q < TQ_NSTAGE; ++q) {
         if (!mbar_wait_or_abort(bar(BAR_EMPTY + q), (uint32_t)((i & 1) ^ 1), abort_flag, lim)) {
@@ -220,19 +256,25 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int cnt = sub_rows(i, q);
         uint8_t *dst = stage + (size_t)q * STAGE_BYTES;
         const uint32_t fb = bar(BAR_FULL + q);
-        if (cnt > 0 && load_mode == LOAD_BULK) {
-          // the cnt rows of the sub-tile, one bulk copy per lane (rows past cnt keep what the slot
-          // held; the slicers mask them)
-          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
+        // the cnt rows of the sub-tile (rows past cnt keep what the slot held; the slicers mask them)
+        if (load_mode == LOAD_ASYNC) {
+          const int chunks = nk >> 1;  // 16-byte chunks per row
+          if (lane < chunks)
+            for (int r = 0; r < cnt; ++r)
+              cp_async16(smem_addr(dst + (size_t)r * STAGE_PITCH + 16u * lane), X + (r0 + r) * ldx + 2 * lane);
+          cp_async_arrive(fb);
+        } else if (cnt > 0 && load_mode == LOAD_BULK) {
+          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)nk * 8u);
           __syncwarp();
-          if (lane < cnt) bulk_load(smem_addr(dst + (size_t)lane * STAGE_PITCH), X + (r0 + lane) * ldx, (uint32_t)n * 8u, fb);
+          if (lane < cnt) bulk_load(smem_addr(dst + (size_t)lane * STAGE_PITCH), X + (r0 + lane) * ldx, (uint32_t)nk * 8u, fb);
+          if (lane != 0) mbar_arrive(fb);
         } else {
-          for (int e = lane; e < cnt * n; e += 32) {
-            const int r = e / n, cc = e - r * n;
+          for (int e = lane; e < cnt * nk; e += 32) {
+            const int r = e / nk, cc = e - r * nk;
             *(double *)(dst + stage_off(r, cc)) = X[(r0 + r) * ldx + cc];
           }
           __syncwarp();
-          if (lane == 0) mbar_arrive(fb);
+          mbar_arrive(fb);
         }
         last_i[q] = i;
       }
@@ -312,14 +354,17 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         const int kg = 2 * c + kk;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const ulonglong2 raw = *(const ulonglong2 *)(src + stage_off(rr, 8 * kg + 2 * u));
           const int c0 = 8 * kg + 2 * u;
+          // REV: K indices c0, c0 + 1 are columns nk - 1 - c0, nk - 2 - c0 (nk even: one aligned pair)
+          const int sc = REV ? max(nk - 2 - c0, 0) : c0;
+          const ulonglong2 raw = *(const ulonglong2 *)(src + stage_off(rr, sc));
+          const unsigned long long v0 = REV ? raw.y : raw.x, v1 = REV ? raw.x : raw.y;
           if (FULLN) {
-            e[c][2 * u] = raw.x;
-            e[c][2 * u + 1] = raw.y;
+            e[c][2 * u] = v0;
+            e[c][2 * u + 1] = v1;
           } else {
-            e[c][2 * u] = (live && c0 < n) ? raw.x : 0ULL;
-            e[c][2 * u + 1] = (live && c0 + 1 < n) ? raw.y : 0ULL;
+            e[c][2 * u] = (live && c0 < nk) ? v0 : 0ULL;
+            e[c][2 * u + 1] = (live && c0 + 1 < nk) ? v1 : 0ULL;
           }
           mxh = max(mxh, max((uint32_t)(e[c][2 * u] >> 32) & 0x7fffffffu, (uint32_t)(e[c][2 * u + 1] >> 32) & 0x7fffffffu));
         }
@@ -414,23 +459,42 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
               if (grow < r_end) {
                 if (RESID) {
                   const double *vp = Vref + grow * ldvr + k0;
-                  if (k0 < n) {
+                  if (k0 < nn) {
                     const double v = vp[0], d = v - y0;
                     res2 = fma(d, d, res2);
                     ref2 = fma(v, v, ref2);
                   }
-                  if (k0 + 1 < n) {
+                  if (k0 + 1 < nn) {
                     const double v = vp[1], d = v - y1;
                     res2 = fma(d, d, res2);
                     ref2 = fma(v, v, ref2);
                   }
+                } else if (REV) {
+                  // columns nn - 1 - k0 (y0) and nn - 2 - k0 (y1): one aligned pair (nn even)
+                  const int64_t cpos = (int64_t)nn - 2 - k0;
+                  if (k0 + 1 < nn) {
+                    double a1 = y1, a0 = y0;
+                    if (EPI == EPI_ADDREF) {
+                      const double2 rv = *(const double2 *)(Vref + grow * ldvr + cpos);
+                      a1 = add_fixed(rv.x, t1, er[rg][hr] + e1);
+                      a0 = add_fixed(rv.y, t0, er[rg][hr] + e0);
+                    }
+                    *(double2 *)(Y + grow * ldy + cpos) = make_double2(a1, a0);
+                  }
                 } else {
                   double *yp = Y + grow * ldy + k0;
-                  if (FULLN || (vec_store && k0 + 1 < n)) {
-                    *(double2 *)yp = make_double2(y0, y1);
+                  double a0 = y0, a1 = y1;
+                  if (FULLN || (vec_store && k0 + 1 < nn)) {
+                    if (EPI == EPI_ADDREF) {
+                      const double2 rv = *(const double2 *)(Vref + grow * ldvr + k0);
+                      a0 = add_fixed(rv.x, t0, er[rg][hr] + e0);
+                      a1 = add_fixed(rv.y, t1, er[rg][hr] + e1);
+                    }
+                    *(double2 *)yp = make_double2(a0, a1);
                   } else {
-                    if (k0 < n) yp[0] = y0;
-                    if (k0 + 1 < n) yp[1] = y1;
+                    const double *rp = Vref + grow * ldvr + k0;
+                    if (k0 < nn) yp[0] = EPI == EPI_ADDREF ? add_fixed(rp[0], t0, er[rg][hr] + e0) : a0;
+                    if (k0 + 1 < nn) yp[1] = EPI == EPI_ADDREF ? add_fixed(rp[1], t1, er[rg][hr] + e1) : a1;
                   }
                 }
               }
@@ -460,35 +524,53 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 
-template <bool RESID>
-cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
+// the loader's copy mechanism for aligned rows (LOAD_ASYNC or LOAD_BULK)
+int g_trsm_load_mode = LOAD_ASYNC;
+
+template <bool REV, int EPI>
+cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk, int64_t nn,
                              const double *Bpacked, const double *Vref, int64_t ldvr, double *sums, int num_sms,
                              DevStatus *st, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
   ctas = ceil_div(m, rows_per_cta);
   // bulk copies need 16-byte aligned rows of a multiple of 16 bytes
   const int load_mode =
-      (((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && (n * 8) % 16 == 0) ? LOAD_BULK : LOAD_PLAIN;
-  const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0;
+      (((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && (nk * 8) % 16 == 0) ? g_trsm_load_mode : LOAD_PLAIN;
+  const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0 &&
+                         (EPI != EPI_ADDREF || (((uintptr_t)Vref & 15) == 0 && (ldvr % 2) == 0));
+  if (REV && (!vec_store || (nk % 2) != 0 || (nn % 2) != 0)) return cudaErrorInvalidValue;
   // the full-width form stores 16-byte pairs unconditionally: only with aligned rows of Y
-  const bool full = n == TQ_NP && vec_store && !RESID;
-  auto kern = full ? k_trsm_oz<true, RESID> : k_trsm_oz<false, RESID>;
+  const bool full = nk == TQ_NP && nn == TQ_NP && vec_store && EPI != EPI_RESID;
+  auto kern = full ? k_trsm_oz<true, REV, EPI> : k_trsm_oz<false, REV, EPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)n, Bpacked, rows_per_cta,
-                                                                load_mode, vec_store, Vref, ldvr, sums, st);
+  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)nk, (int)nn, Bpacked, rows_per_cta,
+                                                   load_mode, vec_store, Vref, ldvr, sums, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
                            const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_trsm_oz_t<false>(X, ldx, Y, ldy, m, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_STORE>(X, ldx, Y, ldy, m, n, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+}
+
+cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk,
+                                 int64_t nn, const double *Bpacked, bool reverse, const double *Ref, int64_t ldref,
+                                 int num_sms, DevStatus *st, cudaStream_t s) {
+  if (!Ref) {
+    if (reverse) return cudaErrorInvalidValue;
+    return launch_trsm_oz_t<false, EPI_STORE>(X, ldx, Y, ldy, m, nk, nn, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+  }
+  if (reverse)
+    return launch_trsm_oz_t<true, EPI_ADDREF>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_ADDREF>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
 }
 
 cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,
                                  const double *Rpacked, double *sums, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_trsm_oz_t<true>(Q, ldq, nullptr, 0, m, n, Rpacked, V, ldv, sums, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_RESID>(Q, ldq, nullptr, 0, m, n, n, Rpacked, V, ldv, sums, num_sms, st, s);
 }
 
 }  // namespace rq

@@ -243,6 +243,39 @@ def test_full_size_elementwise_against_oracle(rq):
     assert er <= tr, (er, tr)
 
 
+@pytest.mark.parametrize("m,n,kappa,inplace", [(30000, 66, 1e12, False), (20000, 100, 1e14, False),
+                                                 (40001, 128, 1e8, False), (20000, 128, 1e15, True),
+                                                 (9999, 97, 1e10, False)])
+def test_blocked_solves_64_to_128(rq, m, n, kappa, inplace):
+    """64 < n <= 128 (even n): both solves blocked into split products at n1 = n - 64 (the
+    off-diagonal block by substitution order for the first solve, through the inverse for the
+    well-conditioned second); odd n keeps the substitution kernels.  Targets and parity as for
+    every other size."""
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=n)
+    S2 = oracle.gauss_sketch(1, s2, s1)
+    Q, R, _ = _run(rq, V, s1, s2, 0, S2, inplace=inplace)
+    e2, _ = oracle.orth_err(Q)
+    assert e2 <= 1e-12, e2
+    assert oracle.resid(V, Q, R) <= 1e-13
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    Qo, Ro = oracle.rand_cholqr(V, s1, s2, seed=0, S2=S2)
+    tq, tr = parity_tolerance(V, s1, s2)
+    assert np.abs(Q - Qo).max() <= tq
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= tr
+
+
+def test_blocked_cholqr2_last_pass(rq):
+    # CholeskyQR2's well-conditioned last pass at n = 128 runs the blocked product
+    m, n = 30000, 128
+    V = synthetic.make_v(m, n, 1e4, seed=3)
+    Q, R, _ = rq.randqr_cholqr2(torch.from_numpy(V).cuda())
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    assert oracle.orth_err(Q)[0] <= 1e-13 and oracle.resid(V, Q, R) <= 1e-14
+    Qo, Ro = oracle.cholqr2(V)
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-11
+
+
 DF_CASES = [(20000, 16, 1e10), (3001, 1, 1.0), (5003, 3, 1e6), (6000, 7, 1e14), (10000, 32, 1e4),
             (12001, 33, 1e8), (20000, 64, 1e12), (20000, 64, 1e14), (16385, 100, 1e8),
             (20000, 128, 1e14)]

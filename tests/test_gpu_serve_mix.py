@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 def test_bench_served_stream_completes():
     import bench
     import paper_2309_05868_gb300 as rq
-    r = bench.serve_bench(rq, synthetic, torch, torch.device("cuda", 0), n_req=200)
+    r = bench.serve_bench(rq, synthetic, torch, torch.device("cuda", 0), n_req=200, loads=(0.8,))
     for mode in ("served_fp64", "served_mixed"):
         assert r[mode]["max_orth_err_2"] <= 1e-12, (mode, r[mode])
     assert r["requests"] == 200
