@@ -37,6 +37,13 @@ FP64_ALU_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # FP64 CUDA-core passes are bound by the FP64 pipe (flops per row); the pair-arithmetic and
 # tensor-core passes, and the CountSketch scatter, by HBM (bytes per row: an 8-byte FP64
 # or (hi, lo) FP32 pair read per element, plus the write for the solves).
+
+def identity_gap2(G):
+    """||G - I||_2 of a small symmetric Gram, on the host (numpy's symmetric eigensolver)."""
+    import numpy as np
+    Gh = G.double().cpu().numpy()
+    return float(np.abs(np.linalg.eigvalsh(Gh - np.eye(Gh.shape[0]))).max())
+
 def roofline_model(kind, n):
     return {"trsm": ("alu", n * n), "gram": ("alu", n * (n + 1)),
             "cs_scatter": ("hbm", 8 * n), "trsm_df": ("hbm", 16 * n),
@@ -350,9 +357,7 @@ def serve_bench(rq, synthetic, torch, dev, n_req=2000, loads=(0.5, 0.8, 0.95), s
         span = time.perf_counter() - t0
         worst = 0.0
         for i, (Q, R) in sample.items():
-            G = Q.T @ Q
-            worst = max(worst, torch.linalg.matrix_norm(
-                G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
+            worst = max(worst, identity_gap2(Q.T @ Q))
         sctx.close()
         return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_req_s": n_req / span,
                 "eff_GBs": bytes_total / span / 1e9, "max_orth_err_2_sampled": worst}
@@ -440,9 +445,7 @@ def batch_bench(rq, synthetic, torch, dev, count=512, seed=11):
         rq.randqr_factor_batched(ctx, items, prec=prec)
         worst = 0.0
         for i in range(0, count, 32):
-            G = Qs[i].T @ Qs[i]
-            worst = max(worst, torch.linalg.matrix_norm(
-                G - torch.eye(G.shape[0], dtype=G.dtype, device=dev), ord=2).item())
+            worst = max(worst, identity_gap2(Qs[i].T @ Qs[i]))
         out[name] = {"ms_per_batch": ms, "eff_GBs": bytes_total / (ms / 1e3) / 1e9,
                      "lanes": lanes, "autotune_ms": tuned_ms, "plan_build_s": plan_s,
                      "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
@@ -521,6 +524,35 @@ def large_config(rq, synthetic, torch, dev, m, n, kappa, prec, steps=3):
             "ms_per_step": ms, "value": 32.0 * m * n / (ms / 1e3) / 1e9, "unit": "GB/s", "status": st,
             "orth_err_2": info.orth_err2, "resid_rel_F": info.resid_relF,
             "kernels_ms_per_step": {k: v[0] / steps for k, v in kt.items()}}
+
+
+def l2_resident_rowpass(rq, synthetic, torch, dev, m=1 << 17, n=64, steps=20):
+    """The row-pass kernels on a matrix that stays in L2 between steps (in-place factorization,
+    m x n FP64 = 64 MB at the defaults against 129 MB of L2): per-kernel time per million rows.
+    Set beside the same figure at the bench's HBM-resident size, it shows how much of a kernel's
+    time its HBM traffic accounts for (equal times: the kernel is bound by its own work)."""
+    V0 = synthetic.make_v_torch(m, n, 1e12, seed=3, device=dev)
+    V = V0.clone()
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx = rq.Context(dev.index or 0)
+    s1, s2 = 2 * (n * n + n), 4 * n
+    for _ in range(3):
+        V.copy_(V0)
+        rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
+    torch.cuda.synchronize()
+    ctx.kernel_times()
+    ctx.set_profiling(True)
+    for _ in range(steps):  # Q = V in place: the step's working set stays at m n 8 bytes
+        rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    kt = ctx.kernel_times()
+    st, _ = rq.get_status(ctx)
+    ctx.close()
+    del V, V0
+    torch.cuda.empty_cache()
+    return {"m": m, "n": n, "bytes_resident": 8 * m * n, "status": st,
+            "kernels_ms_per_Mrow": {k: v[0] / steps / (m / 1e6) for k, v in kt.items()}}
 
 
 # ---------------------------------------------------------------------------------------
@@ -616,7 +648,7 @@ def main():
         if world > 1:
             torch.distributed.all_reduce(G)
             torch.distributed.all_reduce(sq)
-        orth = torch.linalg.matrix_norm(G - torch.eye(n, dtype=G.dtype, device=dev), ord=2).item()
+        orth = identity_gap2(G)
         resid = (sq[0] / sq[1]).sqrt().item()
         return ms_, kt_, clk, {"orth_err_2": orth, "resid_rel_F": resid}
 
@@ -819,6 +851,9 @@ def main():
         del Vb
         if world == 1:
             line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
+            line["row_pass_l2_resident"] = l2_resident_rowpass(rq, synthetic, torch, dev)
+            line["row_pass_l2_resident"]["hbm_resident_kernels_ms_per_Mrow"] = {
+                k: v / (m / 1e6) for k, v in line["kernels_ms_per_step"].items()}
             line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
             for kap in (1e2, 1e6, 1e10, 1e12):
                 for pr in (rq.FP64, rq.F32X2):

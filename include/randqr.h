@@ -56,15 +56,17 @@ typedef enum {
   RANDQR_ERR_TICKET = -9        /* serving: unknown ticket */
 } randqr_status;
 
-/* Arithmetic of rand_cholQR's three row passes.  With the tensor cores on (the default) and
- * n <= 64 the row passes are exact split products whatever this says (their accuracy is
- * that of FP64, see randqr_set_tensor_cores), so RANDQR_F32X2 changes nothing there; it
- * selects the pair-arithmetic kernels with the tensor cores off or for 64 < n <= 128. */
+/* Arithmetic of rand_cholQR's two triangular solves (and, with the tensor cores off, of its Gram).
+ * With the tensor cores on (the default) and n <= 64 the solves are split products: RANDQR_FP64
+ * keeps seven byte digits of every row (products to 2^-56 of the row and column scales, FP64's
+ * accuracy), RANDQR_F32X2 six (2^-48, fewer products and digits: the faster mixed-precision form);
+ * for 64 < n <= 128 (even n) both take the seven-digit blocked products.  With the tensor cores
+ * off, RANDQR_F32X2 selects the pair-arithmetic kernels.  Householder QR, Cholesky and
+ * R = R_c R_s are FP64 in every case, and the Gram keeps its full split format. */
 typedef enum {
-  RANDQR_FP64 = 0,   /* every step in IEEE FP64 */
-  RANDQR_F32X2 = 1   /* the three row passes (triangular solves and Gram) in double-float
-                        (pairs of FP32, ~48-bit significand) on the FP32 pipes; sketch,
-                        Householder QR, Cholesky and R = R_c R_s stay in FP64 */
+  RANDQR_FP64 = 0,   /* FP64 accuracy throughout */
+  RANDQR_F32X2 = 1   /* ~48-bit row passes: six-digit split products on the tensor cores, or
+                        double-float (pairs of FP32) on the FP32 pipes with the tensor cores off */
 } randqr_precision;
 
 /* Details of a call's outcome.  `want_accuracy` is the one input: set it (nonzero) before
@@ -125,13 +127,15 @@ randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls);
 /* Gram products on the tensor cores (default on): for n <= 128 the Gram G = W^T W of the
  * Cholesky passes is formed from exact integer slices of W (eight balanced 7-bit digits of a
  * 54-bit fixed point per column and row group, each an exact f16) multiplied by tcgen05 MMAs
- * with exact FP32 accumulation, then recombined in 64-bit integers.  For n <= 64 the triangular solves whose
- * factor is well conditioned are formed the same way as products with the FP64 inverse: both
- * solves of rand_cholQR (Algorithm 3; R_s^{-1} is applied to V so that its truncation error is a
- * row-wise backward error in V, and kappa(R_c) = O(1) by the sketch's embedding property) and
- * the last pass of CholeskyQR2 and of shifted CholeskyQR3.  Their earlier passes, whose R may be
- * ill-conditioned, use substitution.  enable = 0 selects the CUDA-core kernels of the chosen
- * precision everywhere. */
+ * with exact FP32 accumulation, then recombined in 64-bit integers.  The triangular solves whose
+ * factor is well conditioned are formed the same way as products with the FP64 inverse (n <= 64,
+ * and even n <= 128 blocked at n - 64): both solves of rand_cholQR (Algorithm 3; R_s^{-1} is
+ * applied to V so that its truncation error is a row-wise backward error in V, and kappa(R_c) =
+ * O(1) by the sketch's embedding property; for n > 64 the first solve's off-diagonal block goes
+ * by substitution order, T = V2 - W1 R12, W2 = T R22^{-1}) and the last pass of CholeskyQR2 and
+ * of shifted CholeskyQR3.  Their earlier passes, whose R may be ill-conditioned, use
+ * substitution.  The sketch GEMM Ws = S2 W1 is a split product too for n <= 128.  enable = 0
+ * selects the CUDA-core kernels of the chosen precision everywhere. */
 randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable);
 
 /* ---- Per-kernel timing (tracing) ------------------------------------------------------
@@ -180,7 +184,9 @@ randqr_status randqr_rademacher_sketch(randqr_ctx *ctx, uint64_t seed, int64_t s
  *     s1 == m; S2 is s2 x m; not for randqr_shard_sketch).
  * The single-sketch kinds are the paper's comparison points (Sec. 6.2, sizes ceil(6.8 (n^2+n))
  * and ceil(36.01 ln n)); a call whose sizes do not fit the kind returns RANDQR_ERR_ARG.
- * Generated sketches are cached per (seed, s1, s2, kind).  Applies to randqr_sketch,
+ * Generated sketches are cached per (seed, s1, s2, kind); a Rademacher S2 on the tensor-core path
+ * (n <= 128) is not materialised at all: the sketch GEMM draws its signs itself, the same values
+ * randqr_rademacher_sketch would write.  Applies to randqr_sketch,
  * randqr_factor, randqr_randqr and randqr_shard_sketch on this context; the batched and
  * serving calls keep the Gaussian multisketch. */
 typedef enum {
@@ -196,7 +202,7 @@ randqr_status randqr_set_sketch_kind(randqr_ctx *ctx, int32_t kind);
  * with `seed`), then Ws = S2 W1.  S2 may be NULL: the context then uses (and caches) the
  * sketch randqr_gauss_sketch would give for seed + 1.  Requires 1 <= n <= s2 <= s1,
  * m >= 1, ldv >= n.
- * Accuracy of Ws = S2 W1: with the tensor cores on (the default) and n <= 64, the product is
+ * Accuracy of Ws = S2 W1: with the tensor cores on (the default) and n <= 128, the product is
  * formed from exact integer digit products over chunks of 64 along s1; each term carries an
  * error below 2^-53 of the chunk's largest |S2| entry in its row times the chunk's largest
  * |W1| entry in its column, and integer W1 with +-1 S2 gives the exact result.  Otherwise an
@@ -206,8 +212,8 @@ randqr_status randqr_sketch(randqr_ctx *ctx, const double *V, int64_t m, int64_t
                             const double *S2, double *Ws, void *stream);
 
 /* Ws = S2 S1 V as randqr_sketch computes it on a context with the tensor cores on (the
- * default): the split-product sketch GEMM for n <= 64 with its stated error bound, the FP64
- * GEMM above -- but without a context and without allocating any device memory.  The paper has no counterpart: this entry point exists for
+ * default): the split-product sketch GEMM (n <= 128) with its stated error bound -- but without a
+ * context and without allocating any device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc where they need the sketch (a framework that owns
  * every device allocation through its own pool, a host callback or latency-critical path
  * where an allocation's implicit synchronisation is not allowed, a library that must not
@@ -266,7 +272,9 @@ randqr_status randqr_factor_host(randqr_ctx *ctx, const double *V, int64_t m, in
                                  double *R, int64_t ldr, randqr_info *info, void *stream);
 
 /* randQR alone (Algorithm 1): Q0 = V R_s^{-1} (S2S1-orthogonal, kappa(Q0) = O(1)) and
- * R0 = R_s.  Same arguments as randqr_factor. */
+ * R0 = R_s.  Same arguments as randqr_factor.  With the tensor cores on (n <= 64, or even
+ * n <= 128 with 16-byte aligned rows) the solve is the split-product solve of randqr_factor's
+ * first pass; otherwise FP64 forward substitution. */
 randqr_status randqr_randqr(randqr_ctx *ctx, const double *V, int64_t m, int64_t n,
                             int64_t ldv, int64_t s1, int64_t s2, uint64_t seed,
                             const double *S2, double *Q0, int64_t ldq, double *R0,

@@ -155,7 +155,8 @@ class Context:
         self._check(_load().randqr_set_profiling(self._h, int(bool(enable))))
 
     def set_tensor_cores(self, enable=True):
-        """Gram from exact split products on the tensor cores (default) or on CUDA cores."""
+        """Sketch GEMM, solves and Gram as exact split products on the tensor cores (default), or
+        on CUDA cores (FP64 or FP32-pair substitution and Gram)."""
         L = _load()
         L.randqr_set_tensor_cores.argtypes = [_ct.c_void_p, _ct.c_int]
         L.randqr_set_tensor_cores.restype = _ct.c_int32

@@ -351,12 +351,6 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
   return RANDQR_OK;
 }
 
-// One cholQR pass (Algorithm 2) on X into Y: G = X^T X (+ shift) -> R_x -> Y = X R_x^{-1}.
-// With Rprev, writes Rnext = R_x Rprev (packed); with Rdense, writes that product (or R_x)
-// dense.
-// Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores: only where R_c is well
-// conditioned by construction (rand_cholQR's solves, the last pass of CholeskyQR2 and of
-// shifted CholeskyQR3); R_c^{-1} goes to w.Rt2 (after the Cholesky kernel has read it).
 // The split-product solves blocked for 64 < n <= 128 (n even, 16-byte aligned rows): columns split
 // at n1 = n - 64 into X = [X1 X2], B = [[B11, B12], [0, B22]] upper triangular; every block
 // product is one launch of the split-product kernel on at most 64 x 64 operands, and B12 = U + L
@@ -429,16 +423,20 @@ randqr_status blocked_first_solve_tc(randqr_ctx *ctx, const double *V, int64_t l
   return RANDQR_OK;
 }
 
+// Y = X R_c^{-1} as the product X (R_c^{-1}) on the tensor cores, R_c^{-1} computed by column
+// back substitution into w.Rt2 (after the Cholesky kernel has read R_c).  The computed inverse
+// perturbs Y on the right by I + F with ||F|| of order n u kappa(R_c): used for the Cholesky
+// passes (R_c well conditioned in rand_cholQR; kappa(R_c) <= about u^{-1/2} in the baselines).
 randqr_status solve_by_inverse_tc(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y,
                                   int64_t ldy, int64_t m, int64_t n, const Workspace &w,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int digits = 7) {
   if (n > 64) {
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
     return blocked_product_tc(ctx, X, ldx, Y, ldy, m, n, w.Rt2, w, s);
   }
   RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rc, n, w.Rt2, ctx->status_dev, s); }));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz(X, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+    return rq::launch_trsm_oz(X, ldx, Y, ldy, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s, digits);
   }));
   return RANDQR_OK;
 }
@@ -450,14 +448,23 @@ cudaError_t launch_gram_tc(const randqr_ctx *ctx, const void *X, bool x_df, int6
                            int64_t n, double *G, cudaStream_t s) {
   if (rq::gram_split_supported(n))
     return rq::launch_gram_split(X, x_df, ldx, m, n, G, ctx->num_sms, ctx->status_dev, s);
+  if (!x_df && n > 64 && n <= 128) {
+    // the first 64 columns' Gram, then the columns 64 .. n - 1 against all n (upper triangle)
+    cudaError_t e = rq::launch_gram_split(X, false, ldx, m, 64, G, ctx->num_sms, ctx->status_dev, s);
+    if (e != cudaSuccess) return e;
+    return rq::launch_gram_cross((const double *)X, ldx, m, n, G, ctx->num_sms, ctx->status_dev, s);
+  }
   return rq::launch_gram_oz(X, x_df, ldx, m, n, G, !x_df, ctx->num_sms, ctx->status_dev, s);
 }
 
+// One cholQR pass (Algorithm 2) on X into Y: G = X^T X (+ shift) -> R_x -> Y = X R_x^{-1}.
+// With Rprev, writes Rnext = R_x Rprev (packed); with Rdense, writes that product (or R_x)
+// dense.  inverse_ok: the solve may be the tensor-core product with R_x^{-1}.
 randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy,
                           int64_t m, int64_t n, double shift_coeff, const double *Rprev,
                           double *Rnext, double *Rdense, int64_t ldr, int stage,
                           randqr_precision prec, const Workspace &w, cudaStream_t s,
-                          bool well_conditioned = false) {
+                          bool inverse_ok = false, int digits = 7) {
   RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
   if (ctx->use_tc && rq::gram_oz_supported(n)) {
     RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
@@ -472,8 +479,8 @@ randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double 
     return rq::launch_potrf(w.G, n, shift_coeff, w.Rc, Rprev, Rnext, Rdense, ldr, stage,
                             ctx->status_dev, s);
   }));
-  if (well_conditioned && (use_tc_solve(ctx, n) || blocked_tc_ok(ctx, n, X, ldx, Y, ldy)))
-    return solve_by_inverse_tc(ctx, X, ldx, Y, ldy, m, n, w, s);
+  if (inverse_ok && (use_tc_solve(ctx, n) || blocked_tc_ok(ctx, n, X, ldx, Y, ldy)))
+    return solve_by_inverse_tc(ctx, X, ldx, Y, ldy, m, n, w, s, digits);
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
     return rq::launch_trsm(X, ldx, Y, ldy, m, n, w.Rc, prec, ctx->num_sms, ctx->status_dev, s);
   }));
@@ -735,25 +742,41 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
     // 64 < n <= 128: both solves blocked into split products (either precision)
     if ((st = blocked_first_solve_tc(ctx, V, ldv, Q, ldq, m, n, w.Rs, w, s)) != RANDQR_OK) return st;
     if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
-                          /*well_conditioned=*/true)) != RANDQR_OK)
+                          /*inverse_ok=*/true)) != RANDQR_OK)
       return st;
     return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
   }
   if (second_pass && use_tc_solve(ctx, n)) {
-    // Both solves as tensor-core products with explicit inverses (either precision): W =
-    // V (R_s^{-1}) into Q, then the Cholesky pass on W in place.
+    // Both solves as tensor-core products with explicit inverses: W = V (R_s^{-1}) into Q, then
+    // the Cholesky pass on W in place.  RANDQR_F32X2 keeps six digits of the rows (48-bit
+    // products, its stated precision) instead of seven.
+    const int dg = prec == RANDQR_F32X2 ? 6 : 7;
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
     RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-      return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+      return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s, dg);
     }));
     if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
-                          /*well_conditioned=*/true)) != RANDQR_OK)
+                          /*inverse_ok=*/true, dg)) != RANDQR_OK)
       return st;
     return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
   }
   if (prec == RANDQR_F32X2 && second_pass) {
     if ((st = factor_df(ctx, V, m, n, ldv, Q, ldq, R, ldr, w, s, nullptr)) != RANDQR_OK) return st;
     return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
+  }
+  if (!second_pass && (use_tc_solve(ctx, n) || blocked_tc_ok(ctx, n, V, ldv, Q, ldq))) {
+    // randQR alone: Q = V R_s^{-1} by the same tensor-core solve as rand_cholQR's first pass
+    if (n > 64) {
+      if ((st = blocked_first_solve_tc(ctx, V, ldv, Q, ldq, m, n, w.Rs, w, s)) != RANDQR_OK) return st;
+    } else {
+      RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
+      RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+        return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
+      }));
+    }
+    RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack(w.Rs, n, R, ldr, ctx->status_dev, s); }));
+    clear_accuracy(info);
+    return finish_call(ctx, s, info);
   }
   // W = V R_s^{-1}, written into Q.
   RQ_CUDA(timed(ctx, s, rq::K_TRSM, [&] {
@@ -766,7 +789,7 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
   }
   // cholQR of W, in place on Q; R = R_c R_s written dense.
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
-                        /*well_conditioned=*/true)) != RANDQR_OK)
+                        /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
   return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }
@@ -831,15 +854,18 @@ randqr_status randqr_cholqr2(randqr_ctx *ctx, const double *V, int64_t m, int64_
   if (st != RANDQR_OK) return st;
   Workspace w;
   if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
-  // pass 1: Q0 = V R0^{-1} into Q; keep R0 in w.Rt
+  // pass 1: Q0 = V R0^{-1} into Q; keep R0 in w.Rt.  R0 is as ill conditioned as V (at most
+  // about u^{-1/2} when the Cholesky factorization succeeds); a product with its computed
+  // inverse X (R0 X = I + F, |F| <= gamma_n |R0| |X|) gives Q0 (I + F) with ||F|| of order
+  // n u kappa(R0), far below pass 1's own loss of orthogonality (u kappa(V)^2), which pass 2
+  // removes.  So both passes take the tensor-core products where they exist.
   if ((st = cholqr_pass(ctx, V, ldv, Q, ldq, m, n, 0.0, nullptr, nullptr, nullptr, 0, 1,
-                        RANDQR_FP64, w, s)) != RANDQR_OK)
+                        RANDQR_FP64, w, s, /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
   RQ_CUDA(cudaMemcpyAsync(w.Rt, w.Rc, sizeof(double) * packed(n), cudaMemcpyDeviceToDevice, s));
-  // pass 2 in place; R = R1 R0.  Q0 is orthonormal to O(u kappa(V)^2) when pass 1 succeeded,
-  // so R1 is well conditioned and its solve may run as a product with the inverse.
+  // pass 2 in place; R = R1 R0
   if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, nullptr, R, ldr, 2, RANDQR_FP64,
-                        w, s, /*well_conditioned=*/true)) != RANDQR_OK)
+                        w, s, /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
   return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }
@@ -855,18 +881,19 @@ randqr_status randqr_shifted_cholqr3(randqr_ctx *ctx, const double *V, int64_t m
   if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
   const double u = 1.1102230246251565404e-16;  // 2^-53
   const double coeff = 11.0 * ((double)m * (double)n + (double)n * (double)(n + 1)) * u;
-  // shifted pass: R0 -> w.Rt
+  // shifted pass: R0 -> w.Rt.  The shift keeps kappa(R0) below about u^{-1/2}, so the solves
+  // may run as products with computed inverses as in randqr_cholqr2.
   if ((st = cholqr_pass(ctx, V, ldv, Q, ldq, m, n, coeff, nullptr, nullptr, nullptr, 0, 1,
-                        RANDQR_FP64, w, s)) != RANDQR_OK)
+                        RANDQR_FP64, w, s, /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
   RQ_CUDA(cudaMemcpyAsync(w.Rt, w.Rc, sizeof(double) * packed(n), cudaMemcpyDeviceToDevice, s));
-  // cholQR2 of Q0: R1 R0 -> w.Rt2, then R2 (R1 R0) dense
-  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, w.Rt2, nullptr, 0, 2, RANDQR_FP64,
-                        w, s)) != RANDQR_OK)
+  // cholQR2 of Q0: R1 R0 -> w.Rs (not used by this method otherwise; w.Rt2 holds the inverses
+  // of the tensor-core solves), then R2 (R1 R0) dense
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt, w.Rs, nullptr, 0, 2, RANDQR_FP64,
+                        w, s, /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
-  // (the last pass factors a nearly orthonormal Q1: well conditioned)
-  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rt2, nullptr, R, ldr, 3, RANDQR_FP64,
-                        w, s, /*well_conditioned=*/true)) != RANDQR_OK)
+  if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 3, RANDQR_FP64,
+                        w, s, /*inverse_ok=*/true)) != RANDQR_OK)
     return st;
   return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
 }

@@ -250,12 +250,17 @@ cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_
 // Output packed upper of dimension 64.
 cudaError_t launch_block_prep(const double *Rp, int64_t n, int mode, double sign, double *Bout, const DevStatus *st,
                               cudaStream_t s);
+// digits: 7 (products to 2^-56 of the row x column scales, the FP64 path) or 6 (2^-48: RANDQR_F32X2)
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
-                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s);
+                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s, int digits = 7);
 // Gram from exact split products on the tensor cores, n <= 64 (gram_split.cu)
 bool gram_split_supported(int64_t n);
 cudaError_t launch_gram_split(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
                               int num_sms, DevStatus *st, cudaStream_t s);
+// G[:, 64:n] (upper triangle) = W^T W[:, 64:n] for 64 < n <= 128 from exact split products
+// (gram_cross.cu); with launch_gram_split on the first 64 columns, the whole Gram
+cudaError_t launch_gram_cross(const double *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked, int num_sms,
+                              DevStatus *st, cudaStream_t s);
 // Gram from exact split products on the tensor cores, n <= 128 (gram_tc.cu)
 bool gram_oz_supported(int64_t n);
 cudaError_t launch_gram_oz(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n,

@@ -3,33 +3,37 @@
 //
 // Rows are taken in groups of 64.  Column j of a group gets a scale 2^E_j > max_r |w_rj| and
 // w_rj = 2^(E_j - 54) X_rj up to truncation, with X_rj = trunc(w_rj 2^(54 - E_j)) written in
-// eight balanced 7-bit digits d_p (tc.cuh; slice s = 7 - p).  Slices s = 2a and 2a + 1 of all
-// 64 columns stack into the 128 rows of A-tile a (TMEM lane 64 * (s & 1) + j); slices t of the
-// same buffer are the B operand, several stacked along N, so one MMA covers up to four
-// regions.  Region g' (64 columns of tensor memory) gathers the pairs (a, t) with 2a + t = g':
-// lanes 0-63 then hold D_g for g = g', lanes 64-127 hold g = g' + 1 (odd s).
+// eight balanced 7-bit digits d_p (tc.cuh; slice s = 7 - p).  The kernel comes in three widths
+// NP = 64, 32, 16 (n padded to NP): a slice holds NP columns, and SPA = 128 / NP consecutive
+// slices stack into the 128 rows of an A-tile (TMEM lane L <-> slice SPA a + L / NP, column
+// L % NP).  Slices t of the same buffer are the B operand, up to 256 / NP of them stacked along
+// N per MMA.  A-tile a times slice t lands in region c = SPA a + t (NP tensor-memory columns),
+// so region c of lane L gathers the pairs (s, t) with s + t = c + L / NP: lanes with p = L / NP
+// hold D_g for g = c + p.  A-tile a needs the slices t <= 7 - SPA a; NP = 64 issues 24 MMAs per
+// 64-row group (N from 128 to 256), NP = 32 eight, NP = 16 four.
 //
 // Groups form events: the first group of an event takes its column maxima plus one bit of
 // headroom as scales, and the following groups keep those scales unless one of their columns
 // outgrew them, up to 16 groups.  An event's groups accumulate in the same regions (at most 1024
 // rows), so every D is a sum of at most 4 x 1024 digit products of at most 2^12, |D| <= 2^24,
-// exact in FP32.  With
-//   T_p(j, k) = sum_g' 2^(7 (7 - g')) D_g'(64p + j, k),
+// exact in FP32 (NP = 32: two pairs per region, NP = 16: one).  With
+//   T_p(j, k) = sum_c 2^(7 (7 - c)) D_c(SPA-row p, j, k),
 // the event's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
 // are dropped, below 2^-54 of 2^(E_j + E_k) per row.  T_p / 256 is formed in 64-bit integers
 // (tc::recombine_g7w), converted on the FP64 pipe and added to per-thread FP64 sums; one FP64
-// atomic per entry (j <= k) and parity at the end.  Longer events mean fewer read-backs, and the
-// next event's products wait for a read-back to finish (tensor memory holds one event).
+// atomic per entry (j <= k) and lane row p at the end.  Longer events mean fewer read-backs, and
+// the next event's products wait for a read-back to finish (tensor memory holds one event).
 //
 // One CTA per SM, persistent over its row range; warps specialise:
 //   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
-//     group into digit slices (second pass; two 64 KB slice buffers, alternating groups),
-//   warps 4-11 read the regions back (warp w: TMEM lanes 32 (w & 3) .., columns k in
-//     [32 h, 32 h + 32) with h = (w - 4) / 4) and keep the FP64 sums,
-//   warp 12 loads 32-row sub-tiles into a four-slot ring with bulk copies (two groups in
-//     flight, so a group's rows arrive while the previous one is cut),
-//   warp 13 owns tensor memory and issues the MMAs (24 per group), closing an event
-//     (commit to the recombination warps) when the next group starts a new one.
+//     group into digit slices (second pass; two slice buffers, alternating groups); a warp owns
+//     NP / 4 columns, and the lanes of one column split the group's 64 rows,
+//   warps 4-11 read the regions back (warp w: TMEM lanes 32 (w & 3) .., columns k in the half
+//     (w - 4) / 4 of the NP) and keep the FP64 sums,
+//   warp 12 loads 32-row sub-tiles into a ring with bulk copies (64 / NP * 2 groups in flight,
+//     so a group's rows arrive while earlier ones are cut),
+//   warp 13 owns tensor memory and issues the MMAs, closing an event (commit to the
+//     recombination warps) when the next group starts a new one.
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -38,26 +42,43 @@ namespace rq {
 namespace {
 using namespace tc;
 
-constexpr int GS_SUB = 32, GS_NP = 64, GS_GROUP = 64;
+constexpr int GS_SUB = 32, GS_GROUP = 64;
 // Groups per tensor-memory accumulation: 1024 rows keep every region within 4 x 1024 digit
 // products of at most 2^12, |D| <= 2^24, exact in FP32.
 constexpr int GS_EV_GROUPS = 16;
 constexpr int GS_THREADS = 448;
 constexpr int GW_LOAD = 12, GW_MMA = 13;
-constexpr uint32_t GS_TMEM_COLS = 512;
-constexpr uint32_t GS_SLICE = 8192;                 // 64 columns x 64 rows of f16 digits
-constexpr uint32_t GS_BUF = NDIG * GS_SLICE;        // one 64-row tile's slices
-constexpr uint32_t GS_STAGE = GS_SUB * GS_NP * 8;   // 16 KB sub-tile
-constexpr size_t GOFF_SL = 0;
-constexpr size_t GOFF_STAGE = GOFF_SL + 2 * (size_t)GS_BUF;
-constexpr size_t GOFF_COLE = GOFF_STAGE + 4 * (size_t)GS_STAGE;
-constexpr size_t GOFF_EVT = GOFF_COLE + 4 * GS_NP * sizeof(int);  // merge[3], grow[3], ev_grp[4]
-constexpr size_t GOFF_BARS = GOFF_EVT + 16 * sizeof(int);
-constexpr int GS_NBARS = 17;  // full[4], empty[4], sl_full[2], sl_empty[2], t_full, t_empty, drain,
-                              // scale_bar, ev_bar
-constexpr size_t GOFF_MISC = GOFF_BARS + GS_NBARS * 8;
-constexpr size_t GS_SMEM = GOFF_MISC + 16;
-static_assert(GS_SMEM <= 232448, "shared memory budget");
+constexpr int GS_NBARS_MAX = 2 * 16 + 9;  // full[NQ], empty[NQ], sl_full[2], sl_empty[2], t_full,
+                                          // t_empty, drain, scale_bar, ev_bar
+
+// Shared-memory plan of the width-NP instance.
+template <int NP>
+struct GsCfg {
+  static constexpr int SPA = 128 / NP;                 // slices per A-tile
+  static constexpr int SPB = 256 / NP;                 // slices per MMA's B (N <= 256)
+  static constexpr int NAT = 8 / SPA;                  // A-tiles
+  static constexpr int NGF = 128 / NP;                 // groups in flight in the stage ring
+  static constexpr int NQ = 2 * NGF;                   // stage slots (32-row sub-tiles)
+  static constexpr int CPW = NP / 4;                   // columns per slicer warp
+  static constexpr int RP = 32 / CPW;                  // lanes per column
+  static constexpr int RPT = GS_GROUP / RP;            // rows of a group per slicer lane
+  static constexpr uint32_t SLICE = NP * GS_GROUP * 2; // one slice of one group (f16 digits)
+  static constexpr uint32_t BUF = NDIG * SLICE;
+  static constexpr uint32_t PITCH = NP * 8;            // staged row
+  static constexpr uint32_t STAGE = GS_SUB * PITCH;    // one 32-row sub-tile
+  static constexpr uint32_t TMEM_COLS = 8 * NP;
+  static constexpr size_t OFF_SL = 0;
+  static constexpr size_t OFF_STAGE = OFF_SL + 2 * (size_t)BUF;
+  static constexpr size_t OFF_COLE = OFF_STAGE + (size_t)NQ * STAGE;
+  static constexpr size_t OFF_EVT = OFF_COLE + 4 * NP * sizeof(int);  // merge[3], grow[3], ev_grp[4]
+  static constexpr size_t OFF_BARS = OFF_EVT + 16 * sizeof(int);
+  static constexpr int NBARS = 2 * NQ + 9;
+  static constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;
+  static constexpr size_t SMEM = OFF_MISC + 16;
+  static_assert(SMEM <= 232448, "shared memory budget");
+  static_assert(RPT % 8 == 0 && RPT <= GS_SUB, "a slicer lane cuts whole K-groups of one sub-tile");
+  static_assert(NBARS <= GS_NBARS_MAX, "barrier count");
+};
 
 enum GLoadMode { GLOAD_BLOCK = 0, GLOAD_ROWS = 1, GLOAD_PLAIN = 2 };
 
@@ -77,50 +98,62 @@ __device__ __forceinline__ long long g_fix(unsigned long long bits, int E) {
   return fix54(__longlong_as_double((long long)bits), E);
 }
 
-// One 64-row tile's MMAs (K = 64 in four steps): A-tile a = slices 2a, 2a + 1; B = slices t0 ..
-// t0 + nt - 1 stacked along N; D = regions 2a + t0 ...
+// One 64-row group's MMAs (K = 64 in four steps of 16): A-tile a (slices SPA a ..) times the
+// slices t = 0 .. 7 - SPA a, SPB of them stacked per MMA, into regions SPA a + t.  The first
+// A-tile's products at K-step 0 of an event's first group open every region.
+template <int NP>
 __device__ __forceinline__ void gram_issue_tile(uint32_t tmem, uint64_t d0, bool first) {
+  using C = GsCfg<NP>;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const uint64_t kc = (uint64_t)(256 * c) >> 4;
-#define GS_MMA(a, t0, nt)                                                                              \
-  umma_bf16(tmem + (uint32_t)((2 * (a) + (t0)) * 64), d0 + kc + ((uint64_t)(2 * (a)) * GS_SLICE >> 4), \
-            d0 + kc + ((uint64_t)(t0) * GS_SLICE >> 4), umma_idesc_f16(128, 64 * (nt)),                 \
-            (first && c == 0 && (a) == 0) ? 0u : 1u)
-    GS_MMA(0, 0, 4);
-    GS_MMA(0, 4, 4);
-    GS_MMA(1, 0, 4);
-    GS_MMA(1, 4, 2);
-    GS_MMA(2, 0, 4);
-    GS_MMA(3, 0, 2);
-#undef GS_MMA
+#pragma unroll
+    for (int a = 0; a < C::NAT; ++a) {
+      const int tmax = 8 - C::SPA * a;  // slices t = 0 .. tmax - 1
+#pragma unroll
+      for (int t0 = 0; t0 < tmax; t0 += C::SPB) {
+        const int nt = (tmax - t0) < C::SPB ? (tmax - t0) : C::SPB;
+        umma_bf16(tmem + (uint32_t)((C::SPA * a + t0) * NP),
+                  d0 + kc + (((uint64_t)(C::SPA * a) * C::SLICE) >> 4),
+                  d0 + kc + (((uint64_t)t0 * C::SLICE) >> 4), umma_idesc_f16(128, NP * nt),
+                  (first && c == 0 && a == 0) ? 0u : 1u);
+      }
+    }
   }
 }
 
 }  // namespace
 
-template <bool IN_DF>
+template <int NP, bool IN_DF>
 __global__ void __launch_bounds__(GS_THREADS, 1)
     k_gram_split(const void *Win, int64_t ldw, int64_t m, int n, double *Gp, int64_t rows_per_cta,
                  int load_mode, DevStatus *st) {
+  using C = GsCfg<NP>;
   if (status_failed(st)) return;
   const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t gs_smem[];
-  uint8_t *slices = gs_smem + GOFF_SL;
-  uint8_t *stage = gs_smem + GOFF_STAGE;
-  int *colE = (int *)(gs_smem + GOFF_COLE);
-  volatile int *evt = (volatile int *)(gs_smem + GOFF_EVT);
-  uint64_t *bars = (uint64_t *)(gs_smem + GOFF_BARS);
-  uint32_t *tmem_slot = (uint32_t *)(gs_smem + GOFF_MISC);
-  volatile int *abort_flag = (volatile int *)(gs_smem + GOFF_MISC + 4);
+  uint8_t *slices = gs_smem + C::OFF_SL;
+  uint8_t *stage = gs_smem + C::OFF_STAGE;
+  int *colE = (int *)(gs_smem + C::OFF_COLE);
+  volatile int *evt = (volatile int *)(gs_smem + C::OFF_EVT);
+  uint64_t *bars = (uint64_t *)(gs_smem + C::OFF_BARS);
+  uint32_t *tmem_slot = (uint32_t *)(gs_smem + C::OFF_MISC);
+  volatile int *abort_flag = (volatile int *)(gs_smem + C::OFF_MISC + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[4]);
-  const uint32_t slf0 = smem_addr(&bars[8]), sle0 = smem_addr(&bars[10]);
-  const uint32_t t_full = smem_addr(&bars[12]), t_empty = smem_addr(&bars[13]), drain = smem_addr(&bars[14]);
-  const uint32_t scale_bar = smem_addr(&bars[15]), ev_bar = smem_addr(&bars[16]);
+  const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[C::NQ]);
+  const uint32_t slf0 = smem_addr(&bars[2 * C::NQ]), sle0 = smem_addr(&bars[2 * C::NQ + 2]);
+  const uint32_t t_full = smem_addr(&bars[2 * C::NQ + 4]), t_empty = smem_addr(&bars[2 * C::NQ + 5]);
+  const uint32_t drain = smem_addr(&bars[2 * C::NQ + 6]);
+  const uint32_t scale_bar = smem_addr(&bars[2 * C::NQ + 7]), ev_bar = smem_addr(&bars[2 * C::NQ + 8]);
+  auto fail = [&]() {
+    if (!*abort_flag) {
+      *abort_flag = 1;
+      status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
+    }
+  };
 
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < C::NQ; ++q) {
       mbar_init_count(full0 + 8 * q, 1);
       mbar_init_count(empty0 + 8 * q, 4);
     }
@@ -137,7 +170,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     for (int e = 0; e < 16; ++e) evt[e] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == GW_MMA) tmem_alloc(tmem_slot, GS_TMEM_COLS);
+  if (warp == GW_MMA) tmem_alloc(tmem_slot, C::TMEM_COLS);
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
@@ -152,56 +185,56 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
 
   if (warp == GW_LOAD) {
     // ------------------------------------------------------------------ loader
-    // group g uses slots 2 (g & 1) and 2 (g & 1) + 1: two groups in flight
-    int last_g[4] = {-1, -1, -1, -1};
+    // group g uses slots 2 (g % NGF) and 2 (g % NGF) + 1, on their (g / NGF)-th use
+    int last_use[C::NQ];
+#pragma unroll
+    for (int q = 0; q < C::NQ; ++q) last_use[q] = -1;
     for (int g = 0; g < ngroups && !*abort_flag; ++g) {
       bool ok = true;
+      const int use = g / C::NGF;
       for (int qq = 0; qq < 2; ++qq) {
-        const int q = 2 * (g & 1) + qq;
-        if (!mbar_wait_or_abort(empty0 + 8 * q, ((g >> 1) & 1) ^ 1, abort_flag, lim)) {
-          if (lane == 0 && !*abort_flag) {
-            *abort_flag = 1;
-            status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-          }
+        const int q = 2 * (g % C::NGF) + qq;
+        if (!mbar_wait_or_abort(empty0 + 8 * q, (uint32_t)((use & 1) ^ 1), abort_flag, lim)) {
+          if (lane == 0) fail();
           ok = false;
           break;
         }
         const int64_t r0 = r_begin + (int64_t)g * GS_GROUP + GS_SUB * qq;
         const int cnt = sub_rows(g, qq);
-        uint8_t *dst = stage + (size_t)q * GS_STAGE;
+        uint8_t *dst = stage + (size_t)q * C::STAGE;
         const uint32_t fb = full0 + 8 * q;
         if (cnt > 0 && load_mode == GLOAD_BLOCK) {
           if (lane == 0) {
-            mbar_expect_tx(fb, (uint32_t)cnt * 512u);
-            bulk_load(smem_addr(dst), (const uint8_t *)Win + (size_t)r0 * 512, (uint32_t)cnt * 512u, fb);
+            mbar_expect_tx(fb, (uint32_t)cnt * C::PITCH);
+            bulk_load(smem_addr(dst), (const uint8_t *)Win + (size_t)r0 * C::PITCH, (uint32_t)cnt * C::PITCH, fb);
           }
         } else if (cnt > 0 && load_mode == GLOAD_ROWS) {
           if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)n * 8u);
           __syncwarp();
           for (int r = lane; r < cnt; r += 32)
-            bulk_load(smem_addr(dst + r * 512), (const uint8_t *)Win + (size_t)(r0 + r) * (size_t)ldw * 8,
+            bulk_load(smem_addr(dst + r * C::PITCH), (const uint8_t *)Win + (size_t)(r0 + r) * (size_t)ldw * 8,
                       (uint32_t)n * 8u, fb);
         } else {
           const unsigned long long *src = (const unsigned long long *)Win;
           for (int e = lane; e < cnt * n; e += 32) {
             const int r = e / n, cc = e - r * n;
-            ((unsigned long long *)dst)[r * GS_NP + cc] = src[(r0 + r) * ldw + cc];
+            ((unsigned long long *)dst)[r * NP + cc] = src[(r0 + r) * ldw + cc];
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(fb);
         }
-        last_g[q] = g;
+        last_use[q] = use;
       }
       if (!ok) break;
     }
     if (lane == 0)
-      for (int q = 0; q < 4; ++q)
-        if (last_g[q] >= 0) mbar_wait(full0 + 8 * q, (last_g[q] >> 1) & 1);
+      for (int q = 0; q < C::NQ; ++q)
+        if (last_use[q] >= 0) mbar_wait(full0 + 8 * q, (uint32_t)(last_use[q] & 1));
   } else if (warp == GW_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
       const uint64_t dA = umma_desc(smem_addr(slices), 128, 1024);
-      const uint64_t dB = umma_desc(smem_addr(slices + GS_BUF), 128, 1024);
+      const uint64_t dB = umma_desc(smem_addr(slices + C::BUF), 128, 1024);
       // Events: one tensor-memory accumulation = one group, or up to GS_EV_GROUPS consecutive
       // groups with common scales.  evt[8 + (ev & 3)] names the event's last group (whose scale
       // slot the recombination reads).
@@ -216,14 +249,14 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       };
       for (int g = 0; g < ngroups && ok; ++g) {
         const int b = g & 1;  // slice buffer
-        if (!mbar_wait_or_abort(slf0 + 8 * b, (g >> 1) & 1, abort_flag, lim)) {
+        if (!mbar_wait_or_abort(slf0 + 8 * b, (uint32_t)((g >> 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
         const bool merge = evt[g % 3] != 0;
         if (!merge) {
           if (pending_g >= 0) close_event();
-          if (!mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag, lim)) {  // previous event read back
+          if (!mbar_wait_or_abort(t_empty, (uint32_t)((ev & 1) ^ 1), abort_flag, lim)) {  // previous event read back
             ok = false;
             break;
           }
@@ -232,17 +265,16 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         fence_after_sync();
         uint64_t d = b ? dB : dA;
         asm volatile("" : "+l"(d));
-        gram_issue_tile(tmem, d, !merge);
+        gram_issue_tile<NP>(tmem, d, !merge);
         last_g = g;
         umma_commit(sle0 + 8 * b);
       }
       if (ok && pending_g >= 0) close_event();
-      if (ok && mbar_wait_or_abort(t_empty, (ev & 1) ^ 1, abort_flag, lim)) {
+      if (ok && mbar_wait_or_abort(t_empty, (uint32_t)((ev & 1) ^ 1), abort_flag, lim)) {
         evt[8 + (ev & 3)] = -1;  // no more events
         mbar_arrive(ev_bar);
-      } else if (!*abort_flag) {
-        *abort_flag = 1;
-        status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
+      } else {
+        fail();
       }
       umma_commit(drain);
       mbar_wait(drain, 0);
@@ -250,66 +282,69 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     __syncwarp();
   } else if (warp < 4) {
     // ------------------------------------------------------------------ scales and slices
-    const int j = 16 * warp + (lane & 15), h = lane >> 4;
+    // Lane: column j = CPW warp + (lane % CPW); rows rp RPT .. rp RPT + RPT - 1 of the group
+    // (rp = lane / CPW), which lie in sub-tile hq of the group.
+    const int j = C::CPW * warp + (lane % C::CPW), rp = lane / C::CPW;
+    const int row0 = rp * C::RPT, hq = row0 / GS_SUB, rin = row0 % GS_SUB;
     const bool cj = j < n;
     int ev_len = 0, n_scale_syncs = 0;  // the same in every slicer thread
     for (int g = 0; g < ngroups; ++g) {
-      const int b = g & 1, q = 2 * b + h;  // slice buffer, this lane's staged sub-tile
+      const int b = g & 1, use = g / C::NGF;
+      const int q = 2 * (g % C::NGF) + hq;  // this lane's staged sub-tile
       bool ok = true;
-      for (int qq = 0; qq < 2 && ok; ++qq) ok = mbar_wait_or_abort(full0 + 8 * (2 * b + qq), (g >> 1) & 1, abort_flag, lim);
+      for (int qq = 0; qq < 2 && ok; ++qq)
+        ok = mbar_wait_or_abort(full0 + 8 * (2 * (g % C::NGF) + qq), (uint32_t)(use & 1), abort_flag, lim);
       if (!ok) {
-        if (lane == 0 && !*abort_flag) {
-          *abort_flag = 1;
-          status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        }
+        if (lane == 0) fail();
         break;
       }
       // Scales.  The first group of an event takes its column maxima (a first pass over the staged
       // rows) plus one bit of headroom; a later group is cut with the event's scales straight
       // away and keeps them unless one of its values reached 2^E, in which case it is cut
       // again with its own maxima and starts a new event (up to GS_EV_GROUPS groups per event).
-      const int cnt = sub_rows(g, h);
-      const uint8_t *src = stage + (size_t)q * GS_STAGE + 8 * j;
+      const int cnt = sub_rows(g, hq) - rin;  // rows of this lane's range that exist
+      const uint8_t *src = stage + (size_t)q * C::STAGE + (size_t)rin * C::PITCH + 8 * j;
       const bool spec = g > 0 && ev_len < GS_EV_GROUPS;
       int E;
       if (spec) {
-        E = colE[((g - 1) & 3) * GS_NP + j];
+        E = colE[((g - 1) & 3) * NP + j];
       } else {
         int mx = 0;
 #pragma unroll 8
-        for (int r = 0; r < GS_SUB; ++r) {
-          const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(src + r * 512) : 0ULL;
+        for (int r = 0; r < C::RPT; ++r) {
+          const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(src + r * C::PITCH) : 0ULL;
           mx = max(mx, g_expfield<IN_DF>(bits));
         }
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+#pragma unroll
+        for (int o = C::CPW; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         E = scale_exp(mx) + 1;
       }
-      if (!mbar_wait_or_abort(sle0 + 8 * b, ((g >> 1) & 1) ^ 1, abort_flag, lim)) {
+      if (!mbar_wait_or_abort(sle0 + 8 * b, (uint32_t)(((g >> 1) & 1) ^ 1), abort_flag, lim)) {
         ok = false;
       } else {
-        uint8_t *buf = slices + (size_t)b * GS_BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
+        uint8_t *buf = slices + (size_t)b * C::BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
         bool merge = false;
         for (int attempt = 0; attempt < 2; ++attempt) {
-          // pass 2: the group's 64 rows into slice buffer b (and this lane's largest exponent)
+          // pass 2: this lane's rows into slice buffer b (and its largest exponent)
           int mxe = 0;
 #pragma unroll 1
-          for (int r0 = 0; r0 < GS_SUB; r0 += 8) {
+          for (int r0 = 0; r0 < C::RPT; r0 += 8) {
             uint32_t w[4][NDIG];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int ra = r0 + 2 * u, rb = ra + 1;
-              const unsigned long long ba = (cj && ra < cnt) ? *(const unsigned long long *)(src + ra * 512) : 0ULL;
-              const unsigned long long bb = (cj && rb < cnt) ? *(const unsigned long long *)(src + rb * 512) : 0ULL;
+              const unsigned long long ba = (cj && ra < cnt) ? *(const unsigned long long *)(src + ra * C::PITCH) : 0ULL;
+              const unsigned long long bb = (cj && rb < cnt) ? *(const unsigned long long *)(src + rb * C::PITCH) : 0ULL;
               mxe = max(mxe, max(g_expfield<IN_DF>(ba), g_expfield<IN_DF>(bb)));
               if (IN_DF)
                 digits2(g_fix<IN_DF>(ba, E), g_fix<IN_DF>(bb, E), w[u]);
               else
                 digits2_biased(fix54_biased<DIG_BIAS>(ba, E), fix54_biased<DIG_BIAS>(bb, E), w[u]);
             }
-            const int kg = (GS_SUB * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the tile
+            const int kg = (row0 + r0) >> 3;  // K-group of rows row0 + r0 .. + 7 within the group
 #pragma unroll
             for (int p = 0; p < NDIG; ++p)
-              *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * GS_SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
+              *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * C::SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
           }
           if (!spec || attempt == 1) break;
           // did any value of the group reach the event's scale?  (the four slicer warps meet)
@@ -324,19 +359,20 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           ++n_scale_syncs;
           merge = evt[3 + g % 3] != g + 1;
           if (merge) break;
-          mxe = max(mxe, __shfl_xor_sync(0xffffffffu, mxe, 16));
+#pragma unroll
+          for (int o = C::CPW; o < 32; o <<= 1) mxe = max(mxe, __shfl_xor_sync(0xffffffffu, mxe, o));
           E = scale_exp(mxe) + 1;  // cut again with the group's own scales
         }
         if (ok) {
           ev_len = merge ? ev_len + 1 : 1;
           // four scale slots: an event's read-back uses the slot of its last group, and the
           // slicers cannot get further than three groups past that group before it is done
-          if (h == 0) colE[(g & 3) * GS_NP + j] = E;
+          if (rp == 0) colE[(g & 3) * NP + j] = E;
           if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
           __syncwarp();
           if (lane == 0) {
-            mbar_arrive(empty0 + 8 * (2 * b));
-            mbar_arrive(empty0 + 8 * (2 * b + 1));
+            mbar_arrive(empty0 + 8 * (2 * (g % C::NGF)));
+            mbar_arrive(empty0 + 8 * (2 * (g % C::NGF) + 1));
           }
           fence_async_smem();
           __syncwarp();
@@ -344,51 +380,45 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
         }
       }
       if (!ok) {
-        if (lane == 0 && !*abort_flag) {
-          *abort_flag = 1;
-          status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        }
+        if (lane == 0) fail();
         break;
       }
     }
   } else {
     // ------------------------------------------------------------------ recombination and sums
+    // Warp: TMEM lanes 32 quad .. 32 quad + 31 (lane L: slice row p = L / NP of the A-tiles,
+    // column j = L % NP), columns k in [KH kh, KH kh + KH).
+    constexpr int KH = NP / 2;
     const int quad = warp & 3, kh = (warp - 4) >> 2;
-    const int L = 32 * quad + lane, par = L >> 6, j = L & 63;
-    const int jlo = 32 * (quad & 1);  // smallest j of this warp
+    const int L = 32 * quad + lane, par = L / NP, j = L % NP;
+    const int jlo = (32 * quad) % NP;  // smallest j of this warp
     const uint32_t tq = tmem + ((uint32_t)(32 * quad) << 16);
-    double S[32];
+    double S[KH];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) S[c] = 0.0;
-    const bool active = 32 * kh + 31 >= jlo;  // some k >= j in this warp's block
+    for (int c = 0; c < KH; ++c) S[c] = 0.0;
+    const bool active = KH * kh + KH - 1 >= jlo;  // some k >= j in this warp's block
     for (int ev = 0;; ++ev) {
-      if (!mbar_wait_or_abort(ev_bar, ev & 1, abort_flag, lim)) {
-        if (lane == 0 && !*abort_flag) {
-          *abort_flag = 1;
-          status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        }
+      if (!mbar_wait_or_abort(ev_bar, (uint32_t)(ev & 1), abort_flag, lim)) {
+        if (lane == 0) fail();
         break;
       }
       const int g = evt[8 + (ev & 3)];
       if (g < 0) break;
-      if (!mbar_wait_or_abort(t_full, ev & 1, abort_flag, lim)) {
-        if (lane == 0 && !*abort_flag) {
-          *abort_flag = 1;
-          status_fail(st, RANDQR_ERR_TIMEOUT, 0, 0);
-        }
+      if (!mbar_wait_or_abort(t_full, (uint32_t)(ev & 1), abort_flag, lim)) {
+        if (lane == 0) fail();
         break;
       }
       fence_after_sync();
       if (active) {
-        const int *ce = colE + (g & 3) * GS_NP;
+        const int *ce = colE + (g & 3) * NP;
         const int ebase = ce[j] - 51 - 7 * par;
 #pragma unroll
-        for (int h4 = 0; h4 < 8; ++h4) {
-          const int k0 = 32 * kh + 4 * h4;
+        for (int h4 = 0; h4 < KH / 4; ++h4) {
+          const int k0 = KH * kh + 4 * h4;
           if (k0 + 3 < jlo) continue;  // the whole 4-column group lies below this warp's diagonal
           uint32_t v[NDIG][4];
 #pragma unroll
-          for (int gg = 0; gg < NDIG; ++gg) tmem_ld4(tq + (uint32_t)(gg * 64 + k0), v[gg]);
+          for (int gg = 0; gg < NDIG; ++gg) tmem_ld4(tq + (uint32_t)(gg * NP + k0), v[gg]);
           tmem_wait_ld();
           tmem_regs_ready(v);
 #pragma unroll
@@ -405,8 +435,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     }
     if (active && j < n) {
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int k = 32 * kh + c;
+      for (int c = 0; c < KH; ++c) {
+        const int k = KH * kh + c;
         if (k >= j && k < n) atomicAdd(&Gp[tri_idx(j, k)], S[c]);
       }
     }
@@ -414,33 +444,45 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
 
   __syncthreads();
   fence_after_sync();
-  if (warp == GW_MMA) tmem_free(tmem, GS_TMEM_COLS);
+  if (warp == GW_MMA) tmem_free(tmem, C::TMEM_COLS);
 }
 
-bool gram_split_supported(int64_t n) { return n >= 1 && n <= GS_NP; }
+bool gram_split_supported(int64_t n) { return n >= 1 && n <= 64; }
 
-cudaError_t launch_gram_split(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
-                              int num_sms, DevStatus *st, cudaStream_t s) {
+namespace {
+template <int NP, bool IN_DF>
+cudaError_t launch_gram_split_t(const void *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked, int num_sms,
+                                DevStatus *st, cudaStream_t s) {
+  using C = GsCfg<NP>;
   int64_t ctas = std::min<int64_t>(ceil_div(m, GS_GROUP), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), GS_GROUP) * GS_GROUP;
   ctas = ceil_div(m, rows_per_cta);
   const bool aligned = ((uintptr_t)W & 15) == 0;
-  const int load_mode = (aligned && n == GS_NP && ldw == GS_NP) ? GLOAD_BLOCK
+  const int load_mode = (aligned && n == NP && ldw == NP) ? GLOAD_BLOCK
                         : (aligned && (n * 8) % 16 == 0 && (ldw * 8) % 16 == 0) ? GLOAD_ROWS
                                                                                  : GLOAD_PLAIN;
-  cudaError_t e;
-  if (in_df) {
-    e = cudaFuncSetAttribute(k_gram_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
-    if (e != cudaSuccess) return e;
-    k_gram_split<true><<<(unsigned)ctas, GS_THREADS, GS_SMEM, s>>>(W, ldw, m, (int)n, Gpacked, rows_per_cta,
-                                                                   load_mode, st);
-  } else {
-    e = cudaFuncSetAttribute(k_gram_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
-    if (e != cudaSuccess) return e;
-    k_gram_split<false><<<(unsigned)ctas, GS_THREADS, GS_SMEM, s>>>(W, ldw, m, (int)n, Gpacked, rows_per_cta,
-                                                                    load_mode, st);
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_gram_split<NP, IN_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  k_gram_split<NP, IN_DF><<<(unsigned)ctas, GS_THREADS, C::SMEM, s>>>(W, ldw, m, (int)n, Gpacked, rows_per_cta,
+                                                                      load_mode, st);
   return cudaGetLastError();
+}
+
+template <bool IN_DF>
+cudaError_t launch_gram_split_w(const void *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked, int num_sms,
+                                DevStatus *st, cudaStream_t s) {
+  if (n <= 16) return launch_gram_split_t<16, IN_DF>(W, ldw, m, n, Gpacked, num_sms, st, s);
+  if (n <= 32) return launch_gram_split_t<32, IN_DF>(W, ldw, m, n, Gpacked, num_sms, st, s);
+  return launch_gram_split_t<64, IN_DF>(W, ldw, m, n, Gpacked, num_sms, st, s);
+}
+}  // namespace
+
+cudaError_t launch_gram_split(const void *W, bool in_df, int64_t ldw, int64_t m, int64_t n, double *Gpacked,
+                              int num_sms, DevStatus *st, cudaStream_t s) {
+  if (!gram_split_supported(n)) return cudaErrorInvalidValue;
+  return in_df ? launch_gram_split_w<true>(W, ldw, m, n, Gpacked, num_sms, st, s)
+               : launch_gram_split_w<false>(W, ldw, m, n, Gpacked, num_sms, st, s);
 }
 
 }  // namespace rq

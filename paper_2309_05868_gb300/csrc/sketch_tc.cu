@@ -81,7 +81,7 @@ __device__ __forceinline__ void sk_issue_kstep(uint32_t tmem, uint64_t ad, uint6
 template <bool RAD>
 __global__ void __launch_bounds__(SK_THREADS, 1)
     k_sketch_oz(const double *__restrict__ A, int64_t lda, const double *__restrict__ B, int64_t ldb, int M,
-                int64_t K, int n, double *C, int64_t chunks_per_cta, int ctas_per_tile, uint64_t rad_seed,
+                int64_t K, int n, double *C, int64_t ldc, int64_t chunks_per_cta, int ctas_per_tile, uint64_t rad_seed,
                 double rad_scale, DevStatus *st) {
   // one decision for the whole CTA (its threads meet at block barriers below)
   if (__syncthreads_or(threadIdx.x == 0 && status_failed(st))) return;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
   } else if (reads) {
     const int row = row0 + 32 * q + lane;
     if (row < M) {
-      double *cp = C + (int64_t)row * n;
+      double *cp = C + (int64_t)row * ldc;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int j = 32 * ch + c;
@@ -266,13 +266,13 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
   if (warp == 0) tmem_free(tmem, SK_TMEM_COLS);
 }
 
-bool sketch_oz_supported(int64_t n) { return n >= 1 && n <= SK_NP; }
+bool sketch_oz_supported(int64_t n) { return n >= 1 && n <= 2 * SK_NP; }
 
 namespace {
 template <bool RAD>
 cudaError_t launch_sketch_oz_t(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
-                               int64_t n, double *C, uint64_t rad_seed, double rad_scale, int num_sms, DevStatus *st,
-                               cudaStream_t s) {
+                               int64_t n, double *C, int64_t ldc, uint64_t rad_seed, double rad_scale, int num_sms,
+                               DevStatus *st, cudaStream_t s) {
   if (M <= 0 || K <= 0) return cudaSuccess;
   const int64_t tiles = ceil_div(M, SK_ROWS);
   const int64_t nchunks = ceil_div(K, SK_K);
@@ -283,20 +283,32 @@ cudaError_t launch_sketch_oz_t(const double *A, int64_t lda, const double *B, in
   if (grid >= ((int64_t)1 << 31) || M >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_sketch_oz<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SK_SMEM);
   if (e != cudaSuccess) return e;
-  k_sketch_oz<RAD><<<(unsigned)grid, SK_THREADS, SK_SMEM, s>>>(A, lda, B, ldb, (int)M, K, (int)n, C, chunks_per_cta,
-                                                               (int)ctas_per_tile, rad_seed, rad_scale, st);
+  k_sketch_oz<RAD><<<(unsigned)grid, SK_THREADS, SK_SMEM, s>>>(A, lda, B, ldb, (int)M, K, (int)n, C, ldc,
+                                                               chunks_per_cta, (int)ctas_per_tile, rad_seed, rad_scale,
+                                                               st);
   return cudaGetLastError();
 }
 }  // namespace
 
+// n <= 128 as column blocks of at most 64 (the column scales are per column anyway)
 cudaError_t launch_sketch_oz(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t M, int64_t K,
                              int64_t n, double *C, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_sketch_oz_t<false>(A, lda, B, ldb, M, K, n, C, 0, 0.0, num_sms, st, s);
+  for (int64_t c0 = 0; c0 < n; c0 += SK_NP) {
+    cudaError_t e = launch_sketch_oz_t<false>(A, lda, B + c0, ldb, M, K, std::min<int64_t>(SK_NP, n - c0), C + c0, n, 0,
+                                              0.0, num_sms, st, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_sketch_oz_rademacher(uint64_t seed, const double *B, int64_t ldb, int64_t M, int64_t K, int64_t n,
                                         double *C, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_sketch_oz_t<true>(nullptr, 0, B, ldb, M, K, n, C, seed, 1.0 / sqrt((double)M), num_sms, st, s);
+  for (int64_t c0 = 0; c0 < n; c0 += SK_NP) {
+    cudaError_t e = launch_sketch_oz_t<true>(nullptr, 0, B + c0, ldb, M, K, std::min<int64_t>(SK_NP, n - c0), C + c0, n,
+                                             seed, 1.0 / sqrt((double)M), num_sms, st, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace rq

@@ -35,8 +35,9 @@
 //   warps 8-15 read tensor memory back (TMEM lanes 32 (w & 3) .., 16 columns of each half),
 //     recombine and store 64-byte row segments of Y,
 //   warp 16 loads 32-row sub-tiles of X into a four-slot ring (slot q holds sub-tile q) with
-//     per-row bulk copies (one lane per row; rows padded to 528 bytes in shared memory, so the
-//     slicers' reads of eight rows at one column fall into eight different bank groups),
+//     16-byte asynchronous copies (one row per instruction; rows padded to 528 bytes in shared
+//     memory, so the slicers' reads of eight rows at one column fall into eight different bank
+//     groups) and prefetches the next tile towards L2,
 //   warp 17 owns tensor memory and issues the MMAs,
 // handing tiles over through mbarriers.  B's digit slices are built once per CTA.  A's K-block
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
@@ -86,9 +87,9 @@ static_assert(OFF_A % 1024 == 0 && OFF_STAGE % 1024 == 0 && B_BYTES == 45056, "l
 static_assert(TQ_SMEM <= 232448, "shared memory budget");
 
 // LOAD_ASYNC: 16-byte asynchronous copies, one row per warp instruction (lane = 16-byte chunk);
-// LOAD_BULK: one bulk copy per row; both need 16-byte aligned rows and an even column count.
-// LOAD_PLAIN: element loads.  Every loader lane arrives on the slot's barrier once per fill.
-enum LoadMode { LOAD_ASYNC = 0, LOAD_BULK = 1, LOAD_PLAIN = 2 };
+// needs 16-byte aligned rows and an even column count.  LOAD_PLAIN: element loads.  Every loader
+// lane arrives on the slot's barrier once per fill.
+enum LoadMode { LOAD_ASYNC = 0, LOAD_PLAIN = 1 };
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
@@ -110,14 +111,17 @@ __device__ __forceinline__ void set_abort(volatile int *abort_flag, DevStatus *s
 __device__ __forceinline__ constexpr uint64_t a_off(int s, int c) { return ((uint64_t)s * A_SLICE + (uint64_t)c * 2 * A_LBO) >> 4; }
 __device__ __forceinline__ constexpr uint64_t b_off(int h, int c) { return (uint64_t)b_block(h, c) >> 4; }
 
-// One half's products for K-step C: A slice s times B slices 0 .. 7 - s (at most 6) of block
-// (H, C), into regions s .. of that half.  The first product of a half (C = 0, s = 0) runs with
-// N = 256 over the zero eighth slice and overwrites all eight regions; every other accumulates.
-template <int H, int C>
+// One half's products for K-step C: A slice s times B slices 0 .. NR - 1 - s (at most 6) of block
+// (H, C), into regions s .. NR - 1 of that half, NR = NDA + 1 regions for NDA digits of A (7: the
+// pairs s + t <= 7; 6: s + t <= 6, a 48-bit product).  The first product of a half (C = 0, s = 0)
+// covers every region (for NR = 8 with the zero eighth B slice) and overwrites them; every other
+// accumulates.
+template <int H, int C, int NDA>
 __device__ __forceinline__ void issue_half_kstep(uint32_t tmem, uint64_t ad, uint64_t bd) {
+  constexpr int NR = NDA + 1;
 #pragma unroll
-  for (int s = 0; s < NDIG8; ++s) {
-    const int nt = (C == 0 && s == 0) ? 8 : (s == 0 ? 7 : 8 - s);
+  for (int s = 0; s < NDA; ++s) {
+    const int nt = (C == 0 && s == 0) ? NR : (NR - s < 7 ? NR - s : 7);
     umma_bf16(tmem + (uint32_t)(256 * H + 32 * s), ad + a_off(s, C), bd + b_off(H, C), umma_idesc_f16(TQ_ROWS, 32 * nt),
               (C == 0 && s == 0) ? 0u : 1u);
   }
@@ -144,18 +148,21 @@ __device__ __forceinline__ double add_fixed(double ref, long long t, int u0) {
 
 enum Epilogue { EPI_STORE = 0, EPI_ADDREF = 1, EPI_RESID = 2 };
 
-// FULLN: nk == nn == 64 with 16-byte aligned rows of Y: no per-value column checks, and rows of a
+// NH: column halves of 32 (1 when nk, nn <= 32: only K-blocks 0, 1 and tensor-memory half 0 are
+// used).  NDA: digits of A (7, or 6 for the 48-bit products of RANDQR_F32X2).
+// FULLN: nk == nn == 32 NH with 16-byte aligned rows of Y: no per-value column checks, and rows of a
 // partly filled sub-tile are cut whatever their slot holds (their products are never stored).
 // REV: X's columns are read as X J and Y's written as Y J (J the reversal of nk, nn columns).
 // EPI_ADDREF: Y = Ref + X B (Ref may be Y itself, read in the same column order).
 // EPI_RESID: instead of storing Y, accumulate sums[0] += sum (Ref - Y)^2 and sums[1] += sum Ref^2
 // over the rows (the residual of a factorization V = Q R, with X = Q and B = R).
-template <bool FULLN, bool REV, int EPI>
+template <bool FULLN, bool REV, int EPI, int NH, int NDA>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
     k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int nk, int nn,
               const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode, bool vec_store,
               const double *Vref, int64_t ldvr, double *sums, DevStatus *st) {
   constexpr bool RESID = EPI == EPI_RESID;
+  constexpr int NKB = 2 * NH;  // K-blocks of 16 columns
   if (status_failed(st)) return;
   const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t tq_smem[];
@@ -263,11 +270,6 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
             for (int r = 0; r < cnt; ++r)
               cp_async16(smem_addr(dst + (size_t)r * STAGE_PITCH + 16u * lane), X + (r0 + r) * ldx + 2 * lane);
           cp_async_arrive(fb);
-        } else if (cnt > 0 && load_mode == LOAD_BULK) {
-          if (lane == 0) mbar_expect_tx(fb, (uint32_t)cnt * (uint32_t)nk * 8u);
-          __syncwarp();
-          if (lane < cnt) bulk_load(smem_addr(dst + (size_t)lane * STAGE_PITCH), X + (r0 + lane) * ldx, (uint32_t)nk * 8u, fb);
-          if (lane != 0) mbar_arrive(fb);
         } else {
           for (int e = lane; e < cnt * nk; e += 32) {
             const int r = e / nk, cc = e - r * nk;
@@ -302,9 +304,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         // opaque per tile: keeps the compiler from hoisting all descriptor sums into registers
         uint64_t ad = ad0, bd = bd0;
         asm volatile("" : "+l"(ad), "+l"(bd));
-        issue_half_kstep<0, 0>(tmem, ad, bd);
-        issue_half_kstep<0, 1>(tmem, ad, bd);
+        issue_half_kstep<0, 0, NDA>(tmem, ad, bd);
+        issue_half_kstep<0, 1, NDA>(tmem, ad, bd);
         umma_commit(bar(BAR_HDONE + 0));
+        if (NH == 1) {  // no second half: A's K-blocks 0 and 1 are free once these complete
+          umma_commit(bar(BAR_KFREE + 0));
+          umma_commit(bar(BAR_KFREE + 1));
+          continue;
+        }
         // half 1: all four K-steps; after K-step c no MMA of this tile reads A's K-block c
         if (!mbar_wait_or_abort(bar(BAR_TEMPTY + 1), ph ^ 1, abort_flag, lim) ||
             !mbar_wait_or_abort(bar(BAR_AFULL + 2), ph, abort_flag, lim) ||
@@ -313,13 +320,13 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
           break;
         }
         fence_after_sync();
-        issue_half_kstep<1, 0>(tmem, ad, bd);
+        issue_half_kstep<1, 0, NDA>(tmem, ad, bd);
         umma_commit(bar(BAR_KFREE + 0));
-        issue_half_kstep<1, 1>(tmem, ad, bd);
+        issue_half_kstep<1, 1, NDA>(tmem, ad, bd);
         umma_commit(bar(BAR_KFREE + 1));
-        issue_half_kstep<1, 2>(tmem, ad, bd);
+        issue_half_kstep<1, 2, NDA>(tmem, ad, bd);
         umma_commit(bar(BAR_KFREE + 2));
-        issue_half_kstep<1, 3>(tmem, ad, bd);
+        issue_half_kstep<1, 3, NDA>(tmem, ad, bd);
         umma_commit(bar(BAR_KFREE + 3));
         umma_commit(bar(BAR_HDONE + 1));
       }
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     uint8_t *const arow = As + (size_t)(row >> 3) * A_SBO + (size_t)(row & 7) * 16;
     bool ok = true;
     for (int i = 0; i < ntiles && ok; ++i) {
-      unsigned long long e[4][8];
+      unsigned long long e[NKB][8];
       for (int u = 0; u < 2; ++u)
         if (!mbar_wait_or_abort(bar(BAR_FULL + grp + 2 * u), (uint32_t)(i & 1), abort_flag, lim)) ok = false;
       if (!ok) break;
@@ -350,7 +357,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const uint8_t *src = stage + (size_t)q * STAGE_BYTES;
       uint32_t mxh = 0;  // largest high word without its sign: bits 20-30 are the exponent field
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < NKB; ++c) {
         const int kg = 2 * c + kk;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));  // the other half of the row
       const int E = scale_exp(mx);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < NKB; ++c) {
         if (i > 0 && !mbar_wait_or_abort(bar(BAR_KFREE + c), (uint32_t)((i - 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
           digits8_biased(fix54_biased(e[c][2 * u], E), fix54_biased(e[c][2 * u + 1], E), w[u]);
         uint8_t *dst = arow + (size_t)(2 * c + kk) * A_LBO;
 #pragma unroll
-        for (int p = 0; p < NDIG8; ++p)
+        for (int p = NDIG8 - NDA; p < NDIG8; ++p)  // slices s = NDIG8 - 1 - p < NDA
           *(uint4 *)(dst + (size_t)(NDIG8 - 1 - p) * A_SLICE) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
         fence_async_smem();
         __syncwarp();
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
       const int64_t row0 = r_begin + (int64_t)i * TQ_ROWS + 32 * quad;
       int er[2][2];
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < NH; ++h) {
         if (!mbar_wait_or_abort(bar(BAR_HDONE + h), (uint32_t)(i & 1), abort_flag, lim)) {
           ok = false;
           break;
@@ -432,7 +439,13 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-            for (int g = 0; g < 8; ++g) tmem_ld16x256(ta + (uint32_t)(32 * g + 8 * cc), v[cc][g]);
+            for (int g = 0; g < 8; ++g) {
+              if (g < NDA + 1) {
+                tmem_ld16x256(ta + (uint32_t)(32 * g + 8 * cc), v[cc][g]);
+              } else {  // 48-bit products: region 7 holds nothing
+                v[cc][g][0] = v[cc][g][1] = v[cc][g][2] = v[cc][g][3] = 0u;
+              }
+            }
           tmem_wait_ld();
           tmem_regs_ready(v[0]);
           tmem_regs_ready(v[1]);
@@ -524,10 +537,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 
-// the loader's copy mechanism for aligned rows (LOAD_ASYNC or LOAD_BULK)
-int g_trsm_load_mode = LOAD_ASYNC;
-
-template <bool REV, int EPI>
+template <bool REV, int EPI, int NDA>
 cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk, int64_t nn,
                              const double *Bpacked, const double *Vref, int64_t ldvr, double *sums, int num_sms,
                              DevStatus *st, cudaStream_t s) {
@@ -537,13 +547,20 @@ cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ld
   ctas = ceil_div(m, rows_per_cta);
   // bulk copies need 16-byte aligned rows of a multiple of 16 bytes
   const int load_mode =
-      (((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && (nk * 8) % 16 == 0) ? g_trsm_load_mode : LOAD_PLAIN;
+      (((uintptr_t)X & 15) == 0 && (ldx * 8) % 16 == 0 && (nk * 8) % 16 == 0) ? LOAD_ASYNC : LOAD_PLAIN;
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0 &&
                          (EPI != EPI_ADDREF || (((uintptr_t)Vref & 15) == 0 && (ldvr % 2) == 0));
   if (REV && (!vec_store || (nk % 2) != 0 || (nn % 2) != 0)) return cudaErrorInvalidValue;
+  // one column half when both widths fit in 32 (the upper-triangular B then needs K < 32 only)
+  const bool half = nk <= 32 && nn <= 32 && !REV && EPI == EPI_STORE;
   // the full-width form stores 16-byte pairs unconditionally: only with aligned rows of Y
-  const bool full = nk == TQ_NP && nn == TQ_NP && vec_store && EPI != EPI_RESID;
-  auto kern = full ? k_trsm_oz<true, REV, EPI> : k_trsm_oz<false, REV, EPI>;
+  const int64_t width = half ? 32 : TQ_NP;
+  const bool full = nk == width && nn == width && vec_store && EPI != EPI_RESID;
+  decltype(&k_trsm_oz<false, REV, EPI, 2, NDA>) kern;
+  if (half)
+    kern = full ? k_trsm_oz<true, false, EPI_STORE, 1, NDA> : k_trsm_oz<false, false, EPI_STORE, 1, NDA>;
+  else
+    kern = full ? k_trsm_oz<true, REV, EPI, 2, NDA> : k_trsm_oz<false, REV, EPI, 2, NDA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)nk, (int)nn, Bpacked, rows_per_cta,
@@ -552,8 +569,10 @@ cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ld
 }
 
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
-                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_trsm_oz_t<false, EPI_STORE>(X, ldx, Y, ldy, m, n, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+                           const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s, int digits) {
+  if (digits == 6)
+    return launch_trsm_oz_t<false, EPI_STORE, 6>(X, ldx, Y, ldy, m, n, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_STORE, 7>(X, ldx, Y, ldy, m, n, n, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
 }
 
 cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk,
@@ -561,16 +580,16 @@ cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_
                                  int num_sms, DevStatus *st, cudaStream_t s) {
   if (!Ref) {
     if (reverse) return cudaErrorInvalidValue;
-    return launch_trsm_oz_t<false, EPI_STORE>(X, ldx, Y, ldy, m, nk, nn, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+    return launch_trsm_oz_t<false, EPI_STORE, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
   }
   if (reverse)
-    return launch_trsm_oz_t<true, EPI_ADDREF>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
-  return launch_trsm_oz_t<false, EPI_ADDREF>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
+    return launch_trsm_oz_t<true, EPI_ADDREF, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_ADDREF, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
 }
 
 cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,
                                  const double *Rpacked, double *sums, int num_sms, DevStatus *st, cudaStream_t s) {
-  return launch_trsm_oz_t<false, EPI_RESID>(Q, ldq, nullptr, 0, m, n, n, Rpacked, V, ldv, sums, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_RESID, 7>(Q, ldq, nullptr, 0, m, n, n, Rpacked, V, ldv, sums, num_sms, st, s);
 }
 
 }  // namespace rq

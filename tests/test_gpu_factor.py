@@ -103,21 +103,43 @@ def test_randqr_alone_matches_oracle(rq):
     assert info.rs_min_diag > 0 and info.rs_max_diag >= info.rs_min_diag
 
 
-@pytest.mark.parametrize("kappa", [1.0, 1e5])
-def test_cholqr2_parity(rq, kappa):
-    m, n = 20000, 32
+@pytest.mark.parametrize("m,n,kappa,tc", [(30000, 64, 1e12, True), (20000, 100, 1e10, True),
+                                          (20000, 64, 1e10, False)])
+def test_randqr_alone_solve_paths(rq, m, n, kappa, tc):
+    """randQR alone through the split-product solve (n = 64: one product with R_s^{-1};
+    n = 100: blocked at n1 = 36) and through FP64 substitution (tensor cores off): Q0 against
+    the oracle's V R_s^{-1} to within the perturbation theory of a triangular solve with the
+    same R_s (u kappa(V) relative to |Q0|, with a margin), and R0 = R_s."""
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    V = synthetic.make_v(m, n, kappa, seed=n + 1)
+    S2 = oracle.gauss_sketch(7, s2, s1)
+    ctx = rq.Context(0)
+    ctx.set_tensor_cores(tc)
+    Q0, R0, _ = rq.randqr_randqr(torch.from_numpy(V).cuda(), s1, s2, seed=5,
+                                 S2=torch.from_numpy(S2).cuda(), ctx=ctx)
+    ctx.close()
+    Q0, R0 = Q0.cpu().numpy(), R0.cpu().numpy()
+    Q0o, R0o, _, _ = oracle.randqr(V, s1, s2, seed=5, S2=S2)
+    assert np.abs(R0 - R0o).max() / np.abs(R0o).max() < 1e-9
+    assert np.linalg.cond(Q0) < 10
+    assert np.abs(Q0 - Q0o).max() <= 100 * kappa * 2.0**-53 * np.abs(Q0o).max()
+
+
+@pytest.mark.parametrize("m,n,kappa", [(20000, 32, 1.0), (20000, 32, 1e5), (30001, 64, 1e7), (20000, 100, 1e6)])
+def test_cholqr2_parity(rq, m, n, kappa):
+    # both passes' solves are split products with the computed inverses (n = 100: blocked)
     V = synthetic.make_v(m, n, kappa, seed=8)
     Q, R, _ = rq.randqr_cholqr2(torch.from_numpy(V).cuda())
     Q, R = Q.cpu().numpy(), R.cpu().numpy()
     Qo, Ro = oracle.cholqr2(V)
     assert oracle.orth_err(Q)[0] <= 1e-13 and oracle.resid(V, Q, R) <= 1e-14
     assert np.abs(Q - Qo).max() <= max(1e-10, 1e-14 * kappa**2)
-    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-12
+    # R0 = chol(V^T V) moves by up to u kappa(V) (normwise) under the Gram's rounding
+    assert np.abs(R - Ro).max() / np.abs(Ro).max() <= max(1e-12, 1e-16 * kappa)
 
 
-@pytest.mark.parametrize("kappa", [1.0, 1e9])
-def test_shifted_cholqr3_parity(rq, kappa):
-    m, n = 20000, 32
+@pytest.mark.parametrize("m,n,kappa", [(20000, 32, 1.0), (20000, 32, 1e9), (30000, 64, 1e12), (20000, 128, 1e10)])
+def test_shifted_cholqr3_parity(rq, m, n, kappa):
     V = synthetic.make_v(m, n, kappa, seed=9)
     Q, R, _ = rq.randqr_shifted_cholqr3(torch.from_numpy(V).cuda())
     Q, R = Q.cpu().numpy(), R.cpu().numpy()
@@ -408,3 +430,26 @@ def test_tensor_core_gram_rows_of_changing_magnitude(rq):
         assert oracle.orth_err(Q)[0] <= 1e-12 and oracle.resid(V, Q, R) <= 1e-13
         assert np.abs(R - Ro).max() / np.abs(Ro).max() <= 1e-10
         ctx.close()
+
+
+@pytest.mark.parametrize("m,n", [(20001, 66), (33333, 100), (40000, 128), (5000, 128), (30001, 1), (20011, 7),
+                                 (25000, 16), (33333, 17), (40000, 32), (9999, 33), (40001, 64)])
+def test_gram_against_the_oracle(rq, m, n):
+    """The split-product Gram at every width: n <= 16, <= 32 and <= 64 by the 16-, 32- and
+    64-column instances of the Gram kernel, 64 < n <= 128 by the 64-column instance on the first
+    64 columns and the cross-block kernel for the rest against all n, read back through the shard
+    stage that returns it:
+    against the oracle's Gram of the same W (the split format's error is a few units of 2^-53
+    of the columns' scales; the bound allows for the oracle's own sequential sums), on rows whose magnitude jumps every 64 rows so that events
+    restart and groups are cut again with their own scales."""
+    V = synthetic.make_v(m, n, 1e3, seed=n)
+    V *= np.ldexp(1.0, 5 * ((np.arange(m) // 64) % 4))[:, None]
+    Vd = torch.from_numpy(V).cuda()
+    s1, s2 = synthetic.default_sketch_sizes(n)
+    Rs, _ = rq.randqr_sketch_r(rq.randqr_sketch(Vd, s1, s2, seed=1))
+    W, G = rq.randqr_shard_gram(Vd, Rs)
+    Wh, Gh = W.cpu().numpy(), G.cpu().numpy()
+    Go = oracle.gram(Wh)
+    scale = np.sqrt(np.outer(np.diag(Go), np.diag(Go)))
+    assert np.abs(Gh - Go).max() / scale.max() <= 1e-12
+    assert np.allclose(Gh, Gh.T, rtol=0, atol=0)  # both triangles from the packed upper one
