@@ -53,10 +53,11 @@ def roofline_model(kind, n):
 
 # DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
 # m = 2^20, n = 64 with --set full, divided by m), scaled to a launch by the rows it processes.
-# Valid for n = 64 and the kernels as captured; a kernel changed since its capture has no entry
-# (its traffic is reported as null until it is captured again).
-MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (537.01e6 + 484.83e6) / 1048576,
-                                   "gram_tc": (537.01e6 + 3.06e6) / 1048576}
+# Valid for n = 64 and the kernels as captured (the capture of commit b8f118d: k_trsm_oz's
+# full-width instance, the mean of its two launches, and k_gram_split<64>); a kernel changed
+# since its capture has no entry (its traffic is reported as null until it is captured again).
+MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (543.319e6 + 486.550e6) / 1048576,
+                                   "gram_tc": (537.186e6 + 3.241e6) / 1048576}
 
 
 def kernel_roofline(kind, avg_ms, m, n):
@@ -527,32 +528,39 @@ def large_config(rq, synthetic, torch, dev, m, n, kappa, prec, steps=3):
 
 
 def l2_resident_rowpass(rq, synthetic, torch, dev, m=1 << 17, n=64, steps=20):
-    """The row-pass kernels on a matrix that stays in L2 between steps (in-place factorization,
-    m x n FP64 = 64 MB at the defaults against 129 MB of L2): per-kernel time per million rows.
-    Set beside the same figure at the bench's HBM-resident size, it shows how much of a kernel's
-    time its HBM traffic accounts for (equal times: the kernel is bound by its own work)."""
+    """The row-pass kernels on one matrix small enough to stay in L2 between steps (in-place
+    factorization, m x n FP64 = 64 MB at the defaults against 129 MB of L2), timed twice: warm
+    (nothing else runs between the steps, so the kernels read V from L2) and cold (a 512 MB
+    buffer is written between the steps, so they read it from HBM).  Same launches, same sizes:
+    equal per-kernel times mean the kernel is bound by its own work, not by its HBM traffic."""
     V0 = synthetic.make_v_torch(m, n, 1e12, seed=3, device=dev)
     V = V0.clone()
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(1 << 26, dtype=torch.float64, device=dev)
     ctx = rq.Context(dev.index or 0)
     s1, s2 = 2 * (n * n + n), 4 * n
-    for _ in range(3):
-        V.copy_(V0)
-        rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
-    torch.cuda.synchronize()
-    ctx.kernel_times()
-    ctx.set_profiling(True)
-    for _ in range(steps):  # Q = V in place: the step's working set stays at m n 8 bytes
-        rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
-    torch.cuda.synchronize()
-    ctx.set_profiling(False)
-    kt = ctx.kernel_times()
+    out = {"m": m, "n": n, "bytes_resident": 8 * m * n}
+    for mode in ("warm", "cold"):
+        for _ in range(3):
+            V.copy_(V0)
+            rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
+        torch.cuda.synchronize()
+        ctx.kernel_times()
+        ctx.set_profiling(True)
+        for _ in range(steps):  # Q = V in place: the step's working set stays at m n 8 bytes
+            if mode == "cold":
+                flush.fill_(1.0)
+            rq.randqr_factor(V, s1, s2, seed=0, Q=V, R=R, ctx=ctx, sync=False)
+        torch.cuda.synchronize()
+        ctx.set_profiling(False)
+        kt = ctx.kernel_times()
+        out[mode + "_kernels_us"] = {k: 1e3 * v[0] / steps for k, v in kt.items()}
     st, _ = rq.get_status(ctx)
+    out["status"] = st
     ctx.close()
-    del V, V0
+    del V, V0, flush
     torch.cuda.empty_cache()
-    return {"m": m, "n": n, "bytes_resident": 8 * m * n, "status": st,
-            "kernels_ms_per_Mrow": {k: v[0] / steps / (m / 1e6) for k, v in kt.items()}}
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -852,8 +860,6 @@ def main():
         if world == 1:
             line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
             line["row_pass_l2_resident"] = l2_resident_rowpass(rq, synthetic, torch, dev)
-            line["row_pass_l2_resident"]["hbm_resident_kernels_ms_per_Mrow"] = {
-                k: v / (m / 1e6) for k, v in line["kernels_ms_per_step"].items()}
             line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
             for kap in (1e2, 1e6, 1e10, 1e12):
                 for pr in (rq.FP64, rq.F32X2):

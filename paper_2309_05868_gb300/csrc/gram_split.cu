@@ -1,7 +1,8 @@
 // gram_split.cu -- G = W^T W (Algorithm 2 step 1, the Gram of each Cholesky pass) for n <= 64
 // from exact split products on the tensor cores.
 //
-// Rows are taken in groups of 64.  Column j of a group gets a scale 2^E_j > max_r |w_rj| and
+// Rows are taken in groups (64 64 / NP rows for the instance of width NP, below).  Column j of a
+// group gets a scale 2^E_j > max_r |w_rj| and
 // w_rj = 2^(E_j - 54) X_rj up to truncation, with X_rj = trunc(w_rj 2^(54 - E_j)) written in
 // eight balanced 7-bit digits d_p (tc.cuh; slice s = 7 - p).  The kernel comes in three widths
 // NP = 64, 32, 16 (n padded to NP): a slice holds NP columns, and SPA = 128 / NP consecutive
@@ -9,13 +10,14 @@
 // L % NP).  Slices t of the same buffer are the B operand, up to 256 / NP of them stacked along
 // N per MMA.  A-tile a times slice t lands in region c = SPA a + t (NP tensor-memory columns),
 // so region c of lane L gathers the pairs (s, t) with s + t = c + L / NP: lanes with p = L / NP
-// hold D_g for g = c + p.  A-tile a needs the slices t <= 7 - SPA a; NP = 64 issues 24 MMAs per
-// 64-row group (N from 128 to 256), NP = 32 eight, NP = 16 four.
+// hold D_g for g = c + p.  A-tile a needs the slices t <= 7 - SPA a; per K-step of 16 rows
+// NP = 64 issues 6 MMAs (N from 128 to 256), NP = 32 two, NP = 16 one.  A group of 64 64 / NP
+// rows (64, 128, 256) keeps the work per group, 4096 values and 64 KB of slices, the same.
 //
 // Groups form events: the first group of an event takes its column maxima plus one bit of
 // headroom as scales, and the following groups keep those scales unless one of their columns
-// outgrew them, up to 16 groups.  An event's groups accumulate in the same regions (at most 1024
-// rows), so every D is a sum of at most 4 x 1024 digit products of at most 2^12, |D| <= 2^24,
+// outgrew them, up to 1024 rows.  An event's groups accumulate in the same regions, so every D
+// is a sum of at most 4 x 1024 digit products of at most 2^12, |D| <= 2^24,
 // exact in FP32 (NP = 32: two pairs per region, NP = 16: one).  With
 //   T_p(j, k) = sum_c 2^(7 (7 - c)) D_c(SPA-row p, j, k),
 // the event's contribution is 2^(E_j + E_k - 59 - 7p) T_p; pairs with g >= 9 (and half of g = 8)
@@ -25,14 +27,14 @@
 // the next event's products wait for a read-back to finish (tensor memory holds one event).
 //
 // One CTA per SM, persistent over its row range; warps specialise:
-//   warps 0-3 find each group's column scales (first pass over the staged rows) and cut the
-//     group into digit slices (second pass; two slice buffers, alternating groups); a warp owns
-//     NP / 4 columns, and the lanes of one column split the group's 64 rows,
-//   warps 4-11 read the regions back (warp w: TMEM lanes 32 (w & 3) .., columns k in the half
-//     (w - 4) / 4 of the NP) and keep the FP64 sums,
-//   warp 12 loads 32-row sub-tiles into a ring with bulk copies (64 / NP * 2 groups in flight,
-//     so a group's rows arrive while earlier ones are cut),
-//   warp 13 owns tensor memory and issues the MMAs, closing an event (commit to the
+//   warps 0 .. GS_NSW - 1 find each group's column scales (first pass over the staged rows) and
+//     cut the group into digit slices (second pass; two slice buffers, alternating groups); a
+//     warp owns NP / GS_NSW columns, and the lanes of one column split the group's rows,
+//   the next 8 warps read the regions back (warp w: TMEM lanes 32 (w & 3) .., one half of the
+//     NP columns k) and keep the FP64 sums,
+//   the next warp loads 32-row sub-tiles into a ring with bulk copies (two groups in flight, so
+//     a group's rows arrive while the previous one is cut),
+//   the last warp owns tensor memory and issues the MMAs, closing an event (commit to the
 //     recombination warps) when the next group starts a new one.
 #include "common.cuh"
 #include "tc.cuh"
@@ -42,27 +44,34 @@ namespace rq {
 namespace {
 using namespace tc;
 
-constexpr int GS_SUB = 32, GS_GROUP = 64;
-// Groups per tensor-memory accumulation: 1024 rows keep every region within 4 x 1024 digit
-// products of at most 2^12, |D| <= 2^24, exact in FP32.
-constexpr int GS_EV_GROUPS = 16;
-constexpr int GS_THREADS = 448;
-constexpr int GW_LOAD = 12, GW_MMA = 13;
+constexpr int GS_SUB = 32;
+// Rows per tensor-memory accumulation: 1024 keep every region within 4 x 1024 digit products of
+// at most 2^12, |D| <= 2^24, exact in FP32.
+constexpr int GS_EV_ROWS = 1024;
+constexpr int GS_NSW = 4;                       // slicer warps (0 .. GS_NSW - 1)
+constexpr int GW_READ0 = GS_NSW;                 // 8 recombination warps (a multiple of 4 first)
+constexpr int GW_LOAD = GS_NSW + 8, GW_MMA = GS_NSW + 9;
+constexpr int GS_THREADS = 32 * (GS_NSW + 10);
 constexpr int GS_NBARS_MAX = 2 * 16 + 9;  // full[NQ], empty[NQ], sl_full[2], sl_empty[2], t_full,
                                           // t_empty, drain, scale_bar, ev_bar
 
-// Shared-memory plan of the width-NP instance.
+// Shared-memory plan of the width-NP instance.  A group has 64 * 64 / NP rows, so that every
+// instance cuts 4096 values per group (32 rows per slicer lane) into 64 KB of slices.
 template <int NP>
 struct GsCfg {
+  static constexpr int GROUP = 64 * 64 / NP;           // rows per group (K of its products)
+  static constexpr int KSTEPS = GROUP / 16;            // MMA K-steps per group
+  static constexpr int EV_GROUPS = GS_EV_ROWS / GROUP; // groups per event at most
   static constexpr int SPA = 128 / NP;                 // slices per A-tile
   static constexpr int SPB = 256 / NP;                 // slices per MMA's B (N <= 256)
   static constexpr int NAT = 8 / SPA;                  // A-tiles
-  static constexpr int NGF = 128 / NP;                 // groups in flight in the stage ring
-  static constexpr int NQ = 2 * NGF;                   // stage slots (32-row sub-tiles)
-  static constexpr int CPW = NP / 4;                   // columns per slicer warp
+  static constexpr int NSUB = GROUP / GS_SUB;          // staged 32-row sub-tiles per group
+  static constexpr int NQ = 2 * NSUB;                  // stage slots: two groups in flight
+  static constexpr int CPW = NP / GS_NSW;              // columns per slicer warp
   static constexpr int RP = 32 / CPW;                  // lanes per column
-  static constexpr int RPT = GS_GROUP / RP;            // rows of a group per slicer lane
-  static constexpr uint32_t SLICE = NP * GS_GROUP * 2; // one slice of one group (f16 digits)
+  static constexpr int RPT = GROUP / RP;               // rows of a group per slicer lane
+  static constexpr uint32_t SBO = GROUP * 16;          // 8-column core-matrix groups
+  static constexpr uint32_t SLICE = NP * GROUP * 2;    // one slice of one group (f16 digits)
   static constexpr uint32_t BUF = NDIG * SLICE;
   static constexpr uint32_t PITCH = NP * 8;            // staged row
   static constexpr uint32_t STAGE = GS_SUB * PITCH;    // one 32-row sub-tile
@@ -76,7 +85,7 @@ struct GsCfg {
   static constexpr size_t OFF_MISC = OFF_BARS + NBARS * 8;
   static constexpr size_t SMEM = OFF_MISC + 16;
   static_assert(SMEM <= 232448, "shared memory budget");
-  static_assert(RPT % 8 == 0 && RPT <= GS_SUB, "a slicer lane cuts whole K-groups of one sub-tile");
+  static_assert(RPT % 8 == 0 && GS_SUB % RPT == 0, "a slicer lane cuts whole K-groups of one sub-tile");
   static_assert(NBARS <= GS_NBARS_MAX, "barrier count");
 };
 
@@ -98,14 +107,14 @@ __device__ __forceinline__ long long g_fix(unsigned long long bits, int E) {
   return fix54(__longlong_as_double((long long)bits), E);
 }
 
-// One 64-row group's MMAs (K = 64 in four steps of 16): A-tile a (slices SPA a ..) times the
-// slices t = 0 .. 7 - SPA a, SPB of them stacked per MMA, into regions SPA a + t.  The first
-// A-tile's products at K-step 0 of an event's first group open every region.
+// One group's MMAs (K = GROUP in steps of 16): A-tile a (slices SPA a ..) times the slices
+// t = 0 .. 7 - SPA a, SPB of them stacked per MMA, into regions SPA a + t.  The first A-tile's
+// products at K-step 0 of an event's first group open every region.
 template <int NP>
 __device__ __forceinline__ void gram_issue_tile(uint32_t tmem, uint64_t d0, bool first) {
   using C = GsCfg<NP>;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < C::KSTEPS; ++c) {
     const uint64_t kc = (uint64_t)(256 * c) >> 4;
 #pragma unroll
     for (int a = 0; a < C::NAT; ++a) {
@@ -155,16 +164,16 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
   if (tid == 0) {
     for (int q = 0; q < C::NQ; ++q) {
       mbar_init_count(full0 + 8 * q, 1);
-      mbar_init_count(empty0 + 8 * q, 4);
+      mbar_init_count(empty0 + 8 * q, GS_NSW);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init_count(slf0 + 8 * b, 4);
+      mbar_init_count(slf0 + 8 * b, GS_NSW);
       mbar_init_count(sle0 + 8 * b, 1);
     }
     mbar_init_count(t_full, 1);
     mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
-    mbar_init_count(scale_bar, 4);
+    mbar_init_count(scale_bar, GS_NSW);
     mbar_init_count(ev_bar, 1);
     *abort_flag = 0;
     for (int e = 0; e < 16; ++e) evt[e] = 0;
@@ -177,29 +186,29 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
 
   const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r_end = imin64(m, r_begin + rows_per_cta);
-  const int ngroups = r_end > r_begin ? (int)((r_end - r_begin + GS_GROUP - 1) / GS_GROUP) : 0;
+  const int ngroups = r_end > r_begin ? (int)((r_end - r_begin + C::GROUP - 1) / C::GROUP) : 0;
   auto sub_rows = [&](int g, int q) -> int {
-    const int64_t r0 = r_begin + (int64_t)g * GS_GROUP + GS_SUB * q;
+    const int64_t r0 = r_begin + (int64_t)g * C::GROUP + GS_SUB * q;
     return r0 < r_end ? (int)imin64(GS_SUB, r_end - r0) : 0;
   };
 
   if (warp == GW_LOAD) {
     // ------------------------------------------------------------------ loader
-    // group g uses slots 2 (g % NGF) and 2 (g % NGF) + 1, on their (g / NGF)-th use
+    // group g uses slots NSUB (g & 1) .. NSUB (g & 1) + NSUB - 1, on their (g >> 1)-th use
     int last_use[C::NQ];
 #pragma unroll
     for (int q = 0; q < C::NQ; ++q) last_use[q] = -1;
     for (int g = 0; g < ngroups && !*abort_flag; ++g) {
       bool ok = true;
-      const int use = g / C::NGF;
-      for (int qq = 0; qq < 2; ++qq) {
-        const int q = 2 * (g % C::NGF) + qq;
+      const int use = g >> 1;
+      for (int qq = 0; qq < C::NSUB; ++qq) {
+        const int q = C::NSUB * (g & 1) + qq;
         if (!mbar_wait_or_abort(empty0 + 8 * q, (uint32_t)((use & 1) ^ 1), abort_flag, lim)) {
           if (lane == 0) fail();
           ok = false;
           break;
         }
-        const int64_t r0 = r_begin + (int64_t)g * GS_GROUP + GS_SUB * qq;
+        const int64_t r0 = r_begin + (int64_t)g * C::GROUP + GS_SUB * qq;
         const int cnt = sub_rows(g, qq);
         uint8_t *dst = stage + (size_t)q * C::STAGE;
         const uint32_t fb = full0 + 8 * q;
@@ -233,9 +242,9 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
   } else if (warp == GW_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint64_t dA = umma_desc(smem_addr(slices), 128, 1024);
-      const uint64_t dB = umma_desc(smem_addr(slices + C::BUF), 128, 1024);
-      // Events: one tensor-memory accumulation = one group, or up to GS_EV_GROUPS consecutive
+      const uint64_t dA = umma_desc(smem_addr(slices), 128, C::SBO);
+      const uint64_t dB = umma_desc(smem_addr(slices + C::BUF), 128, C::SBO);
+      // Events: one tensor-memory accumulation = one group, or up to EV_GROUPS consecutive
       // groups with common scales.  evt[8 + (ev & 3)] names the event's last group (whose scale
       // slot the recombination reads).
       int ev = 0, pending_g = -1, last_g = -1;
@@ -280,20 +289,20 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       mbar_wait(drain, 0);
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < GS_NSW) {
     // ------------------------------------------------------------------ scales and slices
-    // Lane: column j = CPW warp + (lane % CPW); rows rp RPT .. rp RPT + RPT - 1 of the group
-    // (rp = lane / CPW), which lie in sub-tile hq of the group.
+    // Lane: column j = CPW warp + (lane % CPW); the RPT rows from rp RPT (rp = lane / CPW) of
+    // the group, inside sub-tile hq.
     const int j = C::CPW * warp + (lane % C::CPW), rp = lane / C::CPW;
     const int row0 = rp * C::RPT, hq = row0 / GS_SUB, rin = row0 % GS_SUB;
     const bool cj = j < n;
     int ev_len = 0, n_scale_syncs = 0;  // the same in every slicer thread
     for (int g = 0; g < ngroups; ++g) {
-      const int b = g & 1, use = g / C::NGF;
-      const int q = 2 * (g % C::NGF) + hq;  // this lane's staged sub-tile
+      const int b = g & 1, use = g >> 1;
+      const int q = C::NSUB * b + hq;  // this lane's staged sub-tile
       bool ok = true;
-      for (int qq = 0; qq < 2 && ok; ++qq)
-        ok = mbar_wait_or_abort(full0 + 8 * (2 * (g % C::NGF) + qq), (uint32_t)(use & 1), abort_flag, lim);
+      for (int qq = 0; qq < C::NSUB && ok; ++qq)
+        ok = mbar_wait_or_abort(full0 + 8 * (C::NSUB * b + qq), (uint32_t)(use & 1), abort_flag, lim);
       if (!ok) {
         if (lane == 0) fail();
         break;
@@ -301,10 +310,10 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       // Scales.  The first group of an event takes its column maxima (a first pass over the staged
       // rows) plus one bit of headroom; a later group is cut with the event's scales straight
       // away and keeps them unless one of its values reached 2^E, in which case it is cut
-      // again with its own maxima and starts a new event (up to GS_EV_GROUPS groups per event).
+      // again with its own maxima and starts a new event (up to EV_GROUPS groups per event).
       const int cnt = sub_rows(g, hq) - rin;  // rows of this lane's range that exist
       const uint8_t *src = stage + (size_t)q * C::STAGE + (size_t)rin * C::PITCH + 8 * j;
-      const bool spec = g > 0 && ev_len < GS_EV_GROUPS;
+      const bool spec = g > 0 && ev_len < C::EV_GROUPS;
       int E;
       if (spec) {
         E = colE[((g - 1) & 3) * NP + j];
@@ -322,7 +331,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
       if (!mbar_wait_or_abort(sle0 + 8 * b, (uint32_t)(((g >> 1) & 1) ^ 1), abort_flag, lim)) {
         ok = false;
       } else {
-        uint8_t *buf = slices + (size_t)b * C::BUF + (size_t)(j >> 3) * 1024 + (j & 7) * 16;
+        uint8_t *buf = slices + (size_t)b * C::BUF + (size_t)(j >> 3) * C::SBO + (j & 7) * 16;
         bool merge = false;
         for (int attempt = 0; attempt < 2; ++attempt) {
           // pass 2: this lane's rows into slice buffer b (and its largest exponent)
@@ -347,7 +356,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
               *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * C::SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
           }
           if (!spec || attempt == 1) break;
-          // did any value of the group reach the event's scale?  (the four slicer warps meet)
+          // did any value of the group reach the event's scale?  (the slicer warps meet)
           const bool over = __any_sync(0xffffffffu, cj && mxe >= E + 1023);
           if (lane == 0 && over) atomicMax((int *)&evt[3 + g % 3], g + 1);
           __syncwarp();
@@ -370,10 +379,8 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
           if (rp == 0) colE[(g & 3) * NP + j] = E;
           if (warp == 0 && lane == 0) evt[g % 3] = merge;  // g continues the event of g - 1
           __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(empty0 + 8 * (2 * (g % C::NGF)));
-            mbar_arrive(empty0 + 8 * (2 * (g % C::NGF) + 1));
-          }
+          if (lane == 0)
+            for (int qq = 0; qq < C::NSUB; ++qq) mbar_arrive(empty0 + 8 * (C::NSUB * b + qq));
           fence_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(slf0 + 8 * b);
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(GS_THREADS, 1)
     // Warp: TMEM lanes 32 quad .. 32 quad + 31 (lane L: slice row p = L / NP of the A-tiles,
     // column j = L % NP), columns k in [KH kh, KH kh + KH).
     constexpr int KH = NP / 2;
-    const int quad = warp & 3, kh = (warp - 4) >> 2;
+    const int quad = warp & 3, kh = (warp - GW_READ0) >> 2;
     const int L = 32 * quad + lane, par = L / NP, j = L % NP;
     const int jlo = (32 * quad) % NP;  // smallest j of this warp
     const uint32_t tq = tmem + ((uint32_t)(32 * quad) << 16);
@@ -454,8 +461,8 @@ template <int NP, bool IN_DF>
 cudaError_t launch_gram_split_t(const void *W, int64_t ldw, int64_t m, int64_t n, double *Gpacked, int num_sms,
                                 DevStatus *st, cudaStream_t s) {
   using C = GsCfg<NP>;
-  int64_t ctas = std::min<int64_t>(ceil_div(m, GS_GROUP), (int64_t)num_sms);
-  const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), GS_GROUP) * GS_GROUP;
+  int64_t ctas = std::min<int64_t>(ceil_div(m, C::GROUP), (int64_t)num_sms);
+  const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), C::GROUP) * C::GROUP;
   ctas = ceil_div(m, rows_per_cta);
   const bool aligned = ((uintptr_t)W & 15) == 0;
   const int load_mode = (aligned && n == NP && ldw == NP) ? GLOAD_BLOCK
