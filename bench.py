@@ -98,7 +98,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, baselines, CPU baseline (quick runs)")
     p.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
-    p.add_argument("--serve-requests", type=int, default=2000,
+    p.add_argument("--serve-requests", type=int, default=20000,
                    help="requests of the served stream (the configuration's full stream is 20000)")
     p.add_argument("--gen", default="qr", choices=["qr", "gauss"],
                    help="qr: V = U diag(sigma) W^T; gauss: plain N(0,1/m) entries (kappa ~ 1, "
@@ -276,10 +276,10 @@ def run_reference(a):
 # ---------------------------------------------------------------------------------------
 # Served stream: Poisson arrivals of requests through randqr_submit / randqr_poll
 # ---------------------------------------------------------------------------------------
-def serve_bench(rq, synthetic, torch, dev, n_req=2000, loads=(0.5, 0.8, 0.95), seed=7):
+def serve_bench(rq, synthetic, torch, dev, n_req=20000, loads=(0.5, 0.8, 0.95), seed=7):
     """The served stream: requests with m log-uniform in [1e4, 4e6], n uniform in
-    {4, 8, 16, 32, 64}, kappa log-uniform in [1, 1e12] (one pre-built matrix per (n, kappa
-    level); a request takes its first m rows).  The sequential plain-FP64 service time of every
+    {4, 8, 16, 32, 64}, kappa one of 1, 1e4, 1e8, 1e12 with equal odds (one pre-built matrix
+    per (n, kappa); a request takes its first m rows).  The sequential plain-FP64 service time of every
     request is measured first; arrivals are then Poisson at each offered load x that capacity,
     through randqr_submit / randqr_poll with 8 slots and a 64 GB budget, in FP64 and with
     max_orth_err = 1e-12 (the caller accepts 1e-12: rand_cholQR may take its reduced-precision
@@ -340,7 +340,7 @@ def serve_bench(rq, synthetic, torch, dev, n_req=2000, loads=(0.5, 0.8, 0.95), s
                 # every request in flight has buffers of its own (freed when it finishes)
                 Q = torch.empty((m, n), dtype=torch.float64, device=dev)
                 R = torch.empty((n, n), dtype=torch.float64, device=dev)
-                if nxt % 97 == 0:  # kept for the accuracy sample
+                if nxt % max(1, n_req // 200) == 0:  # about 200 kept for the accuracy sample
                     sample[nxt] = (Q, R)
                 t, _ = rq.randqr_submit(sctx, pools[(n, k)][:m], Q=Q, R=R, seed=0, max_orth_err=max_orth)
                 pending[t] = nxt

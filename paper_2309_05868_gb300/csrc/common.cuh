@@ -201,6 +201,11 @@ cudaError_t launch_sketch_oz_rademacher(uint64_t seed, const double *B, int64_t 
 // Householder R of the rows x n sketch; with scratch (hhqr_scratch_doubles) and n >= 32 it runs
 // on several co-resident CTAs, otherwise on one.
 size_t hhqr_scratch_doubles(int64_t rows, int64_t n);
+// The same on one cluster of 8 CTAs (hhqr_cluster.cu), for n >= 16 and sketches whose columns fit
+// in shared memory; launch_hhqr takes it first.
+bool hhqr_cluster_ok(int64_t rows, int64_t n);
+cudaError_t launch_hhqr_cluster(const double *A, int64_t rows, int64_t n, double *Rpacked, DevStatus *st,
+                                cudaStream_t s);
 cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, double *scratch, DevStatus *st,
                         cudaStream_t s);
 cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,

@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) k_cs_scatter(const double *__restrict__ V
 // hands the slot to the bulk-copy engine as an FP64 add into W1's bucket row
 // (cp.reduce.async.bulk .add.f64): one request of 8 n bytes per row instead of n scalar
 // reductions.  A slot is rewritten only after the engine has read it (bulk groups committed
-// per row, waited for with a lag of SC_RING - 1).  Needs 16-byte aligned rows of W1 (n even).
-constexpr int SC_WARPS = 8, SC_RING = 8;
+// per row, waited for with a lag of RING - 1).  Needs 16-byte aligned rows of W1 (n even).
+constexpr int SC_WARPS = 8;
 
 __device__ __forceinline__ void bulk_reduce_add_f64(double *dst, uint32_t src, uint32_t bytes) {
   asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;\n" ::"l"(dst), "r"(src),
@@ -139,14 +139,14 @@ __device__ __forceinline__ void bulk_reduce_add_f64(double *dst, uint32_t src, u
                : "memory");
 }
 
-template <int CPL>
+template <int CPL, int RING = (CPL <= 2 ? 8 : 4)>
 __global__ void __launch_bounds__(SC_WARPS * 32) k_cs_scatter_bulk(const double *__restrict__ V, int64_t m, int n,
                                                                    int64_t ldv, uint32_t s1, uint64_t seed,
                                                                    int64_t row0, double *__restrict__ W1,
                                                                    const DevStatus *st) {
   if (status_failed(st)) return;
   constexpr int RG = 4;
-  __shared__ __align__(16) double ring[SC_WARPS][SC_RING][32 * CPL];
+  __shared__ __align__(16) double ring[SC_WARPS][RING][32 * CPL];  // at most 32 KB
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(SC_WARPS * 32) k_cs_scatter_bulk(const double 
       for (int g = 0; g < RG; ++g) {
         const uint32_t x = __shfl_sync(0xffffffffu, bs, (r0 + g) & 31);
         if (r0 + g < rows) {
-          double *slot = ring[wl][k % SC_RING];
-          if (k >= SC_RING) {  // the engine has read this slot's previous row
-            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(SC_RING - 1) : "memory");
+          double *slot = ring[wl][k % RING];
+          if (k >= RING) {  // the engine has read this slot's previous row
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(RING - 1) : "memory");
             __syncwarp();
           }
 #pragma unroll
@@ -195,12 +195,14 @@ __global__ void __launch_bounds__(SC_WARPS * 32) k_cs_scatter_bulk(const double 
 cudaError_t launch_cs_scatter(const double *V, int64_t m, int64_t n, int64_t ldv, int64_t s1,
                               uint64_t seed, int64_t row0, double *W1, int num_sms, const DevStatus *st,
                               cudaStream_t s) {
-  if (n % 2 == 0 && n <= 64 && ((uintptr_t)W1 & 15) == 0) {
+  if (n % 2 == 0 && n <= 128 && ((uintptr_t)W1 & 15) == 0) {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 32 * SC_WARPS), (int64_t)num_sms * 8));
     if (n <= 32)
       k_cs_scatter_bulk<1><<<blocks, SC_WARPS * 32, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
-    else
+    else if (n <= 64)
       k_cs_scatter_bulk<2><<<blocks, SC_WARPS * 32, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
+    else
+      k_cs_scatter_bulk<4><<<blocks, SC_WARPS * 32, 0, s>>>(V, m, (int)n, ldv, (uint32_t)s1, seed, row0, W1, st);
     return cudaGetLastError();
   }
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 256), (int64_t)num_sms * 8));

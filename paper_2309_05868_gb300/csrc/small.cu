@@ -252,6 +252,12 @@ size_t hhqr_scratch_doubles(int64_t rows, int64_t n) { return (size_t)n * (size_
 
 cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, double *scratch, DevStatus *st,
                         cudaStream_t s) {
+  if (hhqr_cluster_ok(rows, n)) {
+    // one thread-block cluster; where the cluster cannot be placed, the cooperative kernel
+    const cudaError_t e = launch_hhqr_cluster(A, rows, n, Rpacked, st, s);
+    if (e == cudaSuccess) return e;
+    (void)cudaGetLastError();
+  }
   const int ncl = (int)ceil_div(n, HQ_CTAS);
   const size_t coop_smem = sizeof(double) * (size_t)(ncl + 1) * (size_t)rows;
   if (scratch && n >= 2 * HQ_CTAS && coop_smem <= 200 * 1024) {

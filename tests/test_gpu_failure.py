@@ -45,7 +45,7 @@ def test_timeouts_in_each_waiting_kernel_and_recovery(rq):
     ctx.set_wait_limit(0)
     # the split-product sketch GEMM (the first kernel of rand_cholQR that waits)
     _expect_timeout(rq, lambda: rq.randqr_factor(Vd, seed=1, ctx=ctx))
-    # the multi-CTA Householder QR of the sketch (flag waits across CTAs)
+    # the cluster Householder QR of the sketch (flag waits across the cluster's CTAs)
     Ws = rq.randqr_sketch(Vd, s1, s2, seed=1, ctx=good)
     _expect_timeout(rq, lambda: rq.randqr_sketch_r(Ws, ctx=ctx))
     # the split-product triangular solve (mbarrier pipeline) through the shard stage
@@ -66,8 +66,9 @@ def test_timeouts_in_each_waiting_kernel_and_recovery(rq):
     good.close()
 
 
-def test_timeout_in_the_older_gram_kernel(rq):
-    # 64 < n <= 128: the Gram runs the older split-product kernel, whose waits are bounded too
+def test_timeout_above_64_columns(rq):
+    # 64 < n <= 128: the Gram of the first 64 columns is the first kernel to wait and gives up;
+    # the cross-block Gram and the blocked solves after it return at once on the failed status
     m, n = 20000, 100
     Vd = torch.from_numpy(synthetic.make_v(m, n, 1e3, seed=4)).cuda()
     ctx = rq.Context(0)

@@ -44,7 +44,8 @@ def test_gauss_sketch_matches_oracle(rq, seed, s2, s1):
 
 
 @pytest.mark.parametrize("m,n,s1", [(1000, 1, 4), (3001, 7, 97), (20000, 16, 544),
-                                    (50_000, 33, 2244), (40_000, 64, 8320), (10_000, 128, 33024)])
+                                    (50_000, 33, 2244), (40_000, 64, 8320), (10_000, 128, 33024),
+                                    (30_001, 100, 3000), (40_000, 128, 4000), (5000, 97, 1000)])
 def test_countsketch_integer_bit_exact(rq, m, n, s1):
     # Integer entries: every partial sum is exact in FP64, so the atomics' order does not
     # matter and W1 must equal the oracle's bit for bit.  With S2 = I, Ws = W1 exactly.
