@@ -253,6 +253,16 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(X + p0 * ldx),
                      "r"((uint32_t)(prow * nk * 8)) : "memory");
       }
+      // the reference rows this tile's read-back adds to (EPI_ADDREF), towards L2 a tile ahead
+      // of their use: one prefetch per 128-byte line of each row's nn values
+      if (EPI == EPI_ADDREF) {
+        const int64_t t0 = r_begin + (int64_t)i * TQ_ROWS;
+        for (int r = lane; r < TQ_ROWS && t0 + r < r_end; r += 32) {
+          const double *row = Vref + (t0 + r) * ldvr;
+          for (int c = 0; c < nn + 16; c += 16)  // every line the row's nn values touch
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(row + min(c, nn - 1)) : "memory");
+        }
+      }
       for (int q = 0; q < TQ_NSTAGE; ++q) {
         if (!mbar_wait_or_abort(bar(BAR_EMPTY + q), (uint32_t)((i & 1) ^ 1), abort_flag, lim)) {
           if (lane == 0 && !*abort_flag) set_abort(abort_flag, st);
@@ -436,6 +446,21 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
         for (int rg = 0; rg < 2; ++rg) {  // 16-row group
           uint32_t v[2][8][4];
           const uint32_t ta = tmem + ((uint32_t)(32 * quad + 16 * rg) << 16) + (uint32_t)(256 * h + 16 * cq);
+          // EPI_ADDREF: this group's reference pairs are requested before the tensor-memory loads,
+          // so their latency overlaps the read-back (pairs that are not whole are read below)
+          double2 rvh[2][2];
+          if (EPI == EPI_ADDREF) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+              for (int hr = 0; hr < 2; ++hr) {
+                const int64_t grow = row0 + 16 * rg + 8 * hr + tr;
+                const int k0 = 32 * h + 16 * cq + 8 * cc + tc2;
+                const bool whole = grow < r_end && k0 + 1 < nn && (REV || FULLN || vec_store);
+                const int64_t col = REV ? (int64_t)nn - 2 - k0 : (int64_t)k0;
+                rvh[cc][hr] = whole ? *(const double2 *)(Vref + grow * ldvr + col) : make_double2(0.0, 0.0);
+              }
+          }
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
@@ -488,7 +513,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
                   if (k0 + 1 < nn) {
                     double a1 = y1, a0 = y0;
                     if (EPI == EPI_ADDREF) {
-                      const double2 rv = *(const double2 *)(Vref + grow * ldvr + cpos);
+                      const double2 rv = rvh[cc][hr];
                       a1 = add_fixed(rv.x, t1, er[rg][hr] + e1);
                       a0 = add_fixed(rv.y, t0, er[rg][hr] + e0);
                     }
@@ -499,7 +524,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
                   double a0 = y0, a1 = y1;
                   if (FULLN || (vec_store && k0 + 1 < nn)) {
                     if (EPI == EPI_ADDREF) {
-                      const double2 rv = *(const double2 *)(Vref + grow * ldvr + k0);
+                      const double2 rv = rvh[cc][hr];
                       a0 = add_fixed(rv.x, t0, er[rg][hr] + e0);
                       a1 = add_fixed(rv.y, t1, er[rg][hr] + e1);
                     }
