@@ -405,7 +405,7 @@ typedef struct {
                           ||V - QR||_F/||V||_F <= 1e-13 in this library's tests; 0 = FP64 */
   int32_t want_accuracy; /* nonzero: the request's randqr_info carries orth_err2 and
                             resid_relF measured on the device (randqr_info) */
-  int32_t reserved;
+  int32_t reserved;      /* must be 0 */
 } randqr_request;
 
 typedef struct {
@@ -419,6 +419,11 @@ typedef struct {
  * Only while nothing is queued or running.  Without this call the first submit creates a
  * server with 8 slots and the context's budget (64 GiB if that is 0). */
 randqr_status randqr_serve_config(randqr_ctx *ctx, int32_t slots, size_t hbm_budget_bytes);
+/* A descriptor is checked whole before anything is queued: an unknown algo or prec, sizes or
+ * leading dimensions out of range, NULL or overlapping V, Q, R (Q == V needs ldq == ldv),
+ * sketch sizes that do not fit, or a nonzero reserved field return RANDQR_ERR_ARG and queue
+ * nothing; requests already queued or running are not affected.  submit_batch checks every
+ * descriptor first and queues none if one is refused. */
 randqr_status randqr_submit(randqr_ctx *ctx, const randqr_request *req, uint64_t *ticket);
 randqr_status randqr_submit_batch(randqr_ctx *ctx, const randqr_request *reqs, int32_t count,
                                   uint64_t *tickets);

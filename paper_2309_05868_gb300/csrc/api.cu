@@ -187,7 +187,9 @@ bool bad_factor_args(const double *V, int64_t m, int64_t n, int64_t ldv, const d
       ranges_overlap(V, span_bytes(m, n, ldv), Q, span_bytes(m, n, ldq)))
     return true;
   if (Q == V && ldq != ldv) return true;
-  if (ranges_overlap(R, span_bytes(n, n, ldr), Q, span_bytes(m, n, ldq))) return true;
+  if (ranges_overlap(R, span_bytes(n, n, ldr), Q, span_bytes(m, n, ldq)) ||
+      ranges_overlap(R, span_bytes(n, n, ldr), V, span_bytes(m, n, ldv)))
+    return true;
   return false;
 }
 
@@ -215,6 +217,13 @@ randqr_status finish_call(randqr_ctx *ctx, cudaStream_t s, randqr_info *info) {
 }
 
 }  // namespace
+
+namespace rq {
+bool factor_args_bad(const double *V, int64_t m, int64_t n, int64_t ldv, const double *Q, int64_t ldq,
+                     const double *R, int64_t ldr) {
+  return bad_factor_args(V, m, n, ldv, Q, ldq, R, ldr);
+}
+}  // namespace rq
 
 // ---- Accuracy of a result (randqr_info.want_accuracy) -------------------------------------
 // Enqueued after a factorization on its stream: Q^T Q into w.acc (packed) with the library's
@@ -353,12 +362,28 @@ randqr_status sketch_and_hhqr(randqr_ctx *ctx, const double *V, int64_t m, int64
 
 // The split-product solves blocked for 64 < n <= 128 (n even, 16-byte aligned rows): columns split
 // at n1 = n - 64 into X = [X1 X2], B = [[B11, B12], [0, B22]] upper triangular; every block
-// product is one launch of the split-product kernel on at most 64 x 64 operands, and B12 = U + L
-// (its upper and strictly lower parts) runs as two upper-triangular products, L through the
-// column reversals (J L J is upper triangular).
+// product is one launch of the split-product kernel on at most 64 x 64 operands.  The dense block
+// B12 (n1 x 64) runs as one product that leaves out its rows 32 .. n1 - 1 in columns 0 .. 31
+// (the kernel's first column half takes K < 32), plus one half-width product that adds
+// X1[:, 32:n1] B12[32:n1, 0:32] (only when n1 > 32).
 bool blocked_tc_ok(const randqr_ctx *ctx, int64_t n, const void *X, int64_t ldx, const void *Y, int64_t ldy) {
   return ctx->use_tc && n > 64 && n <= 128 && n % 2 == 0 && ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0 &&
          ldx % 2 == 0 && ldy % 2 == 0;
+}
+
+// Y2 += X1 B12 for a dense n1 x 64 block B12 (row-major, ld 64): the full product without
+// B12[32:n1, 0:32], then that corner as a half-width product into Y2's first 32 columns.
+cudaError_t dense_block_add(randqr_ctx *ctx, const double *X1, int64_t ldx, double *Y2, int64_t ldy, int64_t m,
+                            int64_t n1, const double *B12, cudaStream_t s) {
+  cudaError_t e = timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X1, ldx, Y2, ldy, m, n1, 64, B12, false, Y2, ldy, ctx->num_sms, ctx->status_dev,
+                                    s, 64);
+  });
+  if (e != cudaSuccess || n1 <= 32) return e;
+  return timed(ctx, s, rq::K_TRSM_TC, [&] {
+    return rq::launch_trsm_oz_block(X1 + 32, ldx, Y2, ldy, m, n1 - 32, 32, B12 + 32 * 64, false, Y2, ldy, ctx->num_sms,
+                                    ctx->status_dev, s, 64);
+  });
 }
 
 // Y = X Binv with Binv = R^{-1}, R well conditioned, by the explicit inverse (packed in Binv): all
@@ -367,22 +392,14 @@ bool blocked_tc_ok(const randqr_ctx *ctx, int64_t n, const void *X, int64_t ldx,
 randqr_status blocked_product_tc(randqr_ctx *ctx, const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m,
                                  int64_t n, const double *Binv, const Workspace &w, cudaStream_t s) {
   const int64_t n1 = n - 64;
-  double *B22 = w.blk, *U12 = w.blk + 2080, *L12 = w.blk + 2 * 2080;
+  double *B22 = w.blk, *B12 = w.blk + 2080;  // B12 dense, n1 x 64 (ld 64)
   RQ_CUDA(rq::launch_block_prep(Binv, n, 0, 1.0, B22, ctx->status_dev, s));
-  RQ_CUDA(rq::launch_block_prep(Binv, n, 1, 1.0, U12, ctx->status_dev, s));
-  RQ_CUDA(rq::launch_block_prep(Binv, n, 2, 1.0, L12, ctx->status_dev, s));
+  RQ_CUDA(rq::launch_block_prep(Binv, n, 3, 1.0, B12, ctx->status_dev, s));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
     return rq::launch_trsm_oz_block(X + n1, ldx, Y + n1, ldy, m, 64, 64, B22, false, nullptr, 0, ctx->num_sms,
                                     ctx->status_dev, s);
   }));
-  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz_block(X, ldx, Y + n1, ldy, m, n1, 64, U12, false, Y + n1, ldy, ctx->num_sms,
-                                    ctx->status_dev, s);
-  }));
-  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz_block(X, ldx, Y + n1, ldy, m, n1, 64, L12, true, Y + n1, ldy, ctx->num_sms,
-                                    ctx->status_dev, s);
-  }));
+  RQ_CUDA(dense_block_add(ctx, X, ldx, Y + n1, ldy, m, n1, B12, s));
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
     return rq::launch_trsm_oz_block(X, ldx, Y, ldy, m, n1, n1, Binv, false, nullptr, 0, ctx->num_sms,
                                     ctx->status_dev, s);
@@ -398,24 +415,25 @@ randqr_status blocked_product_tc(randqr_ctx *ctx, const double *X, int64_t ldx, 
 randqr_status blocked_first_solve_tc(randqr_ctx *ctx, const double *V, int64_t ldv, double *Q, int64_t ldq, int64_t m,
                                      int64_t n, const double *Rs, const Workspace &w, cudaStream_t s) {
   const int64_t n1 = n - 64;
-  double *R22 = w.blk, *mU12 = w.blk + 2080, *mL12 = w.blk + 2 * 2080, *R11i = w.blk + 3 * 2080,
-         *R22i = w.blk + 4 * 2080;
+  double *R22 = w.blk, *mR12 = w.blk + 2080, *R11i = w.blk + 3 * 2080, *R22i = w.blk + 4 * 2080;
   RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(Rs, n1, R11i, ctx->status_dev, s); }));
   RQ_CUDA(rq::launch_block_prep(Rs, n, 0, 1.0, R22, ctx->status_dev, s));
   RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(R22, 64, R22i, ctx->status_dev, s); }));
-  RQ_CUDA(rq::launch_block_prep(Rs, n, 1, -1.0, mU12, ctx->status_dev, s));
-  RQ_CUDA(rq::launch_block_prep(Rs, n, 2, -1.0, mL12, ctx->status_dev, s));
+  RQ_CUDA(rq::launch_block_prep(Rs, n, 3, -1.0, mR12, ctx->status_dev, s));  // -R12, dense
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
     return rq::launch_trsm_oz_block(V, ldv, Q, ldq, m, n1, n1, R11i, false, nullptr, 0, ctx->num_sms, ctx->status_dev, s);
   }));
+  // T = V2 - W1 R12 into Q2
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz_block(Q, ldq, Q + n1, ldq, m, n1, 64, mU12, false, V + n1, ldv, ctx->num_sms,
-                                    ctx->status_dev, s);
+    return rq::launch_trsm_oz_block(Q, ldq, Q + n1, ldq, m, n1, 64, mR12, false, V + n1, ldv, ctx->num_sms,
+                                    ctx->status_dev, s, 64);
   }));
-  RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-    return rq::launch_trsm_oz_block(Q, ldq, Q + n1, ldq, m, n1, 64, mL12, true, Q + n1, ldq, ctx->num_sms,
-                                    ctx->status_dev, s);
-  }));
+  if (n1 > 32) {
+    RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+      return rq::launch_trsm_oz_block(Q + 32, ldq, Q + n1, ldq, m, n1 - 32, 32, mR12 + 32 * 64, false, Q + n1, ldq,
+                                      ctx->num_sms, ctx->status_dev, s, 64);
+    }));
+  }
   RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
     return rq::launch_trsm_oz_block(Q + n1, ldq, Q + n1, ldq, m, 64, 64, R22i, false, nullptr, 0, ctx->num_sms,
                                     ctx->status_dev, s);

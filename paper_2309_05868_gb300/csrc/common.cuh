@@ -201,6 +201,10 @@ cudaError_t launch_sketch_oz_rademacher(uint64_t seed, const double *B, int64_t 
 // Householder R of the rows x n sketch; with scratch (hhqr_scratch_doubles) and n >= 32 it runs
 // on several co-resident CTAs, otherwise on one.
 size_t hhqr_scratch_doubles(int64_t rows, int64_t n);
+// The argument checks of the factorization entry points (sizes, leading dimensions, and no
+// overlap of V, Q, R except Q == V with equal leading dimensions): true if they fail.
+bool factor_args_bad(const double *V, int64_t m, int64_t n, int64_t ldv, const double *Q, int64_t ldq,
+                     const double *R, int64_t ldr);
 // The same on one cluster of 8 CTAs (hhqr_cluster.cu), for n >= 16 and sketches whose columns fit
 // in shared memory; launch_hhqr takes it first.
 bool hhqr_cluster_ok(int64_t rows, int64_t n);
@@ -242,17 +246,19 @@ cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, co
 // (trsm_tc.cu), n <= 64; Y may equal X (same ld)
 bool trsm_oz_supported(int64_t n);
 // One block product of a blocked solve (64 < n <= 128): Y = X B, or Y = Ref + X B when Ref is
-// given (Ref may be Y), for X with nk <= 64 columns, Y with nn <= 64, B packed upper
-// (dimension nn, entries with row >= nk ignored); reverse: X read as X J and Y (and Ref) as Y J
-// (J the column reversal; needs Ref, even nk and nn, 16-byte aligned rows)
+// given (Ref may be Y), for X with nk <= 64 columns, Y with nn <= 64.  B packed upper (b_ld = 0:
+// dimension nn, entries with row >= nk ignored), or dense row-major with leading dimension b_ld
+// >= nn, of which the entries (j, k) with k < 32 <= j are left out when nn > 32 (the first column
+// half takes K < 32 only: a second product adds them); reverse (packed B only): X read as X J and
+// Y (and Ref) as Y J (J the column reversal; needs Ref, even nk and nn, 16-byte aligned rows)
 cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk,
                                  int64_t nn, const double *Bpacked, bool reverse, const double *Ref, int64_t ldref,
-                                 int num_sms, DevStatus *st, cudaStream_t s);
+                                 int num_sms, DevStatus *st, cudaStream_t s, int b_ld = 0);
 // The blocks of an upper-triangular R (packed, dimension n, 64 < n <= 128) split at n1 = n - 64:
 // mode 0: R22 (rows and columns n1 .. n-1); mode 1: sign * R12 restricted to its upper part
 // (entries (j, k) with j <= k, j < n1); mode 2: sign * J L12 J with L12 the strictly lower part of
 // R12 (entry (c, k) = sign * R(n1 - 1 - c, n1 + 63 - k) where that lies below R12's diagonal).
-// Output packed upper of dimension 64.
+// Output packed upper of dimension 64; mode 3: sign * R12 dense, n1 x 64 row-major (ld 64).
 cudaError_t launch_block_prep(const double *Rp, int64_t n, int mode, double sign, double *Bout, const DevStatus *st,
                               cudaStream_t s);
 // digits: 7 (products to 2^-56 of the row x column scales, the FP64 path) or 6 (2^-48: RANDQR_F32X2)

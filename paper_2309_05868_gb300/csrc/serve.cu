@@ -81,9 +81,8 @@ size_t footprint(const randqr_request &r) {
 bool bad_request(const randqr_request &r) {
   if (r.algo < RANDQR_ALGO_RAND_CHOLQR || r.algo > RANDQR_ALGO_SHIFTED_CHOLQR3) return true;
   if (r.prec != RANDQR_FP64 && r.prec != RANDQR_F32X2) return true;
-  if (!r.V || !r.Q || !r.R || r.n < 1 || r.n > 128 || r.m < r.n || r.ldv < r.n ||
-      r.ldq < r.n || r.ldr < r.n)
-    return true;
+  if (r.reserved != 0) return true;  // a descriptor written by a different build, or corrupted
+  if (rq::factor_args_bad(r.V, r.m, r.n, r.ldv, r.Q, r.ldq, r.R, r.ldr)) return true;
   if (r.algo == RANDQR_ALGO_RAND_CHOLQR) {
     int64_t s1, s2;
     sketch_sizes(r, &s1, &s2);

@@ -390,6 +390,10 @@ __global__ void k_block_prep(const double *Rp, int n, int mode, double sign, dou
   const int n1 = n - 64;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 64; e += gridDim.x * blockDim.x) {
     const int j = e >> 6, k = e & 63;  // row j, column k of the output (j <= k stored)
+    if (mode == 3) {  // dense R12: R(j, n1 + k), j < n1 <= n1 + k
+      if (j < n1) Bout[j * 64 + k] = sign * Rp[tri_idx(j, n1 + k)];
+      continue;
+    }
     if (j > k) continue;
     double v = 0.0;
     if (mode == 0) {

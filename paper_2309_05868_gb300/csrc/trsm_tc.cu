@@ -159,7 +159,7 @@ enum Epilogue { EPI_STORE = 0, EPI_ADDREF = 1, EPI_RESID = 2 };
 template <bool FULLN, bool REV, int EPI, int NH, int NDA>
 __global__ void __launch_bounds__(TQ_THREADS, 1)
     k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int nk, int nn,
-              const double *__restrict__ Bp, int64_t rows_per_cta, int load_mode, bool vec_store,
+              const double *__restrict__ Bp, int b_ld, int64_t rows_per_cta, int load_mode, bool vec_store,
               const double *Vref, int64_t ldvr, double *sums, DevStatus *st) {
   constexpr bool RESID = EPI == EPI_RESID;
   constexpr int NKB = 2 * NH;  // K-blocks of 16 columns
@@ -200,9 +200,14 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   __syncthreads();
 
   // ---- B's digit slices (all threads, once): column scales, then the blocks
+  // B entry (j, k): packed upper (b_ld == 0), or dense row-major with leading dimension b_ld; a
+  // dense B contributes the rows j < 32 of its columns k < 32 only (the K-steps the first column
+  // half takes), its other rows there being left to another product
+  auto b_used = [&](int j, int k) { return k < nn && j < nk && (b_ld ? (k >= 32 || j < 32) : j <= k); };
+  auto b_at = [&](int j, int k) { return b_ld ? Bp + (int64_t)j * b_ld + k : Bp + tri_idx(j, k); };
   for (int e = tid; e < TQ_NP * TQ_NP; e += TQ_THREADS) {
     const int k = e >> 6, j = e & 63;
-    if (k < nn && j <= k && j < nk) atomicMax(&colexp[k], expfield<false>(Bp + tri_idx(j, k)));
+    if (b_used(j, k)) atomicMax(&colexp[k], expfield<false>(b_at(j, k)));
   }
   for (int e = tid; e < (int)(B_TSLICE / 4); e += TQ_THREADS) {  // the zero eighth slices
     *(uint32_t *)(Bs + b_block(0, 0) + 7 * B_TSLICE + 4 * e) = 0u;
@@ -215,8 +220,8 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
     const int h = bb < 2 ? 0 : 1, c = bb < 2 ? bb : bb - 2;
     const int k = 32 * h + kp, j = 16 * c + 2 * jp;
     const int F = scale_exp(colexp[k]);
-    const long long za = (k < nn && j <= k && j < nk) ? fix54(Bp[tri_idx(j, k)], F) : 0;
-    const long long zb = (k < nn && j + 1 <= k && j + 1 < nk) ? fix54(Bp[tri_idx(j + 1, k)], F) : 0;
+    const long long za = b_used(j, k) ? fix54(*b_at(j, k), F) : 0;
+    const long long zb = b_used(j + 1, k) ? fix54(*b_at(j + 1, k), F) : 0;
     uint32_t w[NDIG8];
     digits8(za, zb, w);
     const uint32_t off = b_block(h, c) + (uint32_t)(kp >> 3) * B_SBO + (uint32_t)(jp >> 2) * B_LBO +
@@ -565,7 +570,7 @@ bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
 template <bool REV, int EPI, int NDA>
 cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk, int64_t nn,
                              const double *Bpacked, const double *Vref, int64_t ldvr, double *sums, int num_sms,
-                             DevStatus *st, cudaStream_t s) {
+                             DevStatus *st, cudaStream_t s, int b_ld = 0) {
   if (m <= 0) return cudaSuccess;
   int64_t ctas = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)num_sms);
   const int64_t rows_per_cta = ceil_div(ceil_div(m, ctas), TQ_ROWS) * TQ_ROWS;
@@ -576,19 +581,20 @@ cudaError_t launch_trsm_oz_t(const double *X, int64_t ldx, double *Y, int64_t ld
   const bool vec_store = ((uintptr_t)Y & 15) == 0 && (ldy % 2) == 0 &&
                          (EPI != EPI_ADDREF || (((uintptr_t)Vref & 15) == 0 && (ldvr % 2) == 0));
   if (REV && (!vec_store || (nk % 2) != 0 || (nn % 2) != 0)) return cudaErrorInvalidValue;
-  // one column half when both widths fit in 32 (the upper-triangular B then needs K < 32 only)
-  const bool half = nk <= 32 && nn <= 32 && !REV && EPI == EPI_STORE;
+  // one column half when both widths fit in 32 (B then needs K < 32 only)
+  const bool half = nk <= 32 && nn <= 32 && !REV && EPI != EPI_RESID;
   // the full-width form stores 16-byte pairs unconditionally: only with aligned rows of Y
   const int64_t width = half ? 32 : TQ_NP;
   const bool full = nk == width && nn == width && vec_store && EPI != EPI_RESID;
   decltype(&k_trsm_oz<false, REV, EPI, 2, NDA>) kern;
   if (half)
-    kern = full ? k_trsm_oz<true, false, EPI_STORE, 1, NDA> : k_trsm_oz<false, false, EPI_STORE, 1, NDA>;
+    kern = full ? k_trsm_oz<true, false, EPI == EPI_RESID ? EPI_STORE : EPI, 1, NDA>
+                : k_trsm_oz<false, false, EPI == EPI_RESID ? EPI_STORE : EPI, 1, NDA>;
   else
     kern = full ? k_trsm_oz<true, REV, EPI, 2, NDA> : k_trsm_oz<false, REV, EPI, 2, NDA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TQ_SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)nk, (int)nn, Bpacked, rows_per_cta,
+  kern<<<(unsigned)ctas, TQ_THREADS, TQ_SMEM, s>>>(X, ldx, Y, ldy, m, (int)nk, (int)nn, Bpacked, b_ld, rows_per_cta,
                                                    load_mode, vec_store, Vref, ldvr, sums, st);
   return cudaGetLastError();
 }
@@ -602,14 +608,17 @@ cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy,
 
 cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t nk,
                                  int64_t nn, const double *Bpacked, bool reverse, const double *Ref, int64_t ldref,
-                                 int num_sms, DevStatus *st, cudaStream_t s) {
+                                 int num_sms, DevStatus *st, cudaStream_t s, int b_ld) {
+  if (b_ld && (reverse || b_ld < nn)) return cudaErrorInvalidValue;
   if (!Ref) {
     if (reverse) return cudaErrorInvalidValue;
-    return launch_trsm_oz_t<false, EPI_STORE, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, nullptr, 0, nullptr, num_sms, st, s);
+    return launch_trsm_oz_t<false, EPI_STORE, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, nullptr, 0, nullptr, num_sms, st, s,
+                                                 b_ld);
   }
   if (reverse)
     return launch_trsm_oz_t<true, EPI_ADDREF, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
-  return launch_trsm_oz_t<false, EPI_ADDREF, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s);
+  return launch_trsm_oz_t<false, EPI_ADDREF, 7>(X, ldx, Y, ldy, m, nk, nn, Bpacked, Ref, ldref, nullptr, num_sms, st, s,
+                                                b_ld);
 }
 
 cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,

@@ -267,7 +267,8 @@ def test_full_size_elementwise_against_oracle(rq):
 
 @pytest.mark.parametrize("m,n,kappa,inplace", [(30000, 66, 1e12, False), (20000, 100, 1e14, False),
                                                  (40001, 128, 1e8, False), (20000, 128, 1e15, True),
-                                                 (9999, 97, 1e10, False)])
+                                                 (9999, 97, 1e10, False), (20000, 96, 1e12, False),
+                                                 (30001, 98, 1e10, True)])
 def test_blocked_solves_64_to_128(rq, m, n, kappa, inplace):
     """64 < n <= 128 (even n): both solves blocked into split products at n1 = n - 64 (the
     off-diagonal block by substitution order for the first solve, through the inverse for the

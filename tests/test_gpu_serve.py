@@ -165,3 +165,45 @@ def test_tensor_core_kernels_under_concurrent_load(rq):
             dr = ((R - alone[i][1]).abs().max() / alone[i][1].abs().max()).item()
             assert dq <= 1e-13 and dr <= 1e-13, (rep, i, dq, dr)
     ctx.close()
+
+
+def test_corrupted_descriptors_are_refused_while_others_run(rq):
+    """Failure detection for the request path: descriptors with a bad field (unknown algorithm
+    or precision, sizes or leading dimensions out of range, NULL or overlapping buffers, sketch
+    sizes that do not fit, a nonzero reserved word) are refused at submit with RANDQR_ERR_ARG
+    and queue nothing, a batch holding one of them queues none, and the requests already in
+    flight finish correctly."""
+    import ctypes
+    ctx = rq.Context(0)
+    good = [_V(200_000, 32, 1e6, seed=s) for s in range(4)]
+    tickets = [rq.randqr_submit(ctx, g, seed=i)[0] for i, g in enumerate(good)]
+    V = _V(20_000, 16, 1e3, seed=9)
+    base, keep = rq.make_request(V)
+    L = rq._serve_sigs(rq._load())
+
+    def corrupt(**kw):
+        r = rq.Request.from_buffer_copy(base)
+        for k, v in kw.items():
+            setattr(r, k, v)
+        return r
+
+    bad = [corrupt(algo=7), corrupt(algo=-1), corrupt(prec=5), corrupt(n=0), corrupt(n=129),
+           corrupt(m=8), corrupt(ldv=8), corrupt(ldq=8), corrupt(ldr=8), corrupt(V=None),
+           corrupt(Q=None), corrupt(R=None), corrupt(reserved=1),
+           corrupt(R=base.V + 8 * 1000),                # R inside V
+           corrupt(Q=base.V + 8 * 16, ldq=base.ldv),  # Q overlapping V without being V
+           corrupt(Q=base.V, ldq=base.ldv + 2),       # in place with another leading dimension
+           corrupt(s1=100, s2=200),                   # s1 < s2
+           corrupt(s1=600, s2=8)]                     # s2 < n
+    for r in bad:
+        t = ctypes.c_uint64(0)
+        assert L.randqr_submit(ctx.handle, ctypes.byref(r), ctypes.byref(t)) == -1
+    arr = (rq.Request * 3)(base, bad[0], base)
+    tk = (ctypes.c_uint64 * 3)()
+    assert L.randqr_submit_batch(ctx.handle, arr, 3, tk) == -1
+    assert rq.randqr_serve_stats_get(ctx)["submitted"] == len(tickets)
+    for t, g in zip(tickets, good):
+        st, _ = rq.randqr_wait(ctx, t)
+        assert st == 0
+    ctx.close()
+    del keep
