@@ -3,7 +3,7 @@
 // Together with the Gram of W's first 64 columns (gram_split.cu) that is the whole upper
 // triangle of G.
 //
-// Number format as in gram_split.cu: per 64-row group, column J of W gets a scale 2^E_J and
+// Number format as in gram_split.cu: per 32-row group, column J of W gets a scale 2^E_J and
 // eight balanced 7-bit digits (slice s = 0 the leading one).  Here an A operand is ONE slice of
 // all 128 (padded) columns -- M = 128, TMEM lane i <-> column J(i) -- and B is slices t of the
 // block of columns 64 .. 127 stacked along N, so region g = s + t (64 tensor-memory columns)
@@ -12,15 +12,15 @@
 // A region holds up to eight digit-pair sums of at most 2^12 each per row, so an event (groups
 // accumulated before one read-back) spans at most 512 rows: |D| <= 2^24, exact in FP32.
 //
-// Slice layout (K-major core matrices of 8 columns x 8 rows, no swizzle): slice s at 16 KB s,
-// and within it the 8-column group c of column block b at 1 KB (2 c + b).  So one slice's 16
-// row-groups are 1 KB apart (A: M = 128, lane i <-> column 64 ((i >> 3) & 1) + 8 (i >> 4) + (i & 7)),
-// and block 1's groups are 2 KB apart through consecutive slices (B: N = 64 per slice, stacked).
+// Slice layout (K-major core matrices of 8 columns x 8 rows, no swizzle): slice s at 8 KB s, and
+// within it the 8-column group c of column block b at 512 B (2 c + b).  So one slice's 16
+// row-groups are 512 B apart (A: M = 128, lane i <-> column 64 ((i >> 3) & 1) + 8 (i >> 4) + (i & 7)),
+// and block 1's groups are 1 KB apart through consecutive slices (B: N = 64 per slice, stacked).
 //
-// One CTA per SM, persistent over its rows; warps: 0-3 cut each 64-row group (two columns per
-// lane), 4-11 read the regions back and keep FP64 sums, 12 loads 32-row sub-tiles (two slots),
-// 13 owns tensor memory and issues the MMAs.  One slice buffer: a group is cut once the previous
-// group's MMAs are done.
+// One CTA per SM, persistent over its rows; warps: 0-3 cut each 32-row group (two columns and
+// 16 rows per lane), 4-11 read the regions back and keep FP64 sums, 12 loads the groups' rows
+// (two groups in flight), 13 owns tensor memory and issues the MMAs.  Two slice buffers of
+// 64 KB: a group is cut while the previous group's products run.
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -29,21 +29,23 @@ namespace rq {
 namespace {
 using namespace tc;
 
-constexpr int GC_SUB = 32, GC_COLS = 128, GC_GROUP = 64;
-constexpr int GC_EV_GROUPS = 8;  // 512 rows per event
+constexpr int GC_SUB = 32, GC_COLS = 128, GC_GROUP = 32;
+constexpr int GC_EV_GROUPS = 512 / GC_GROUP;  // 512 rows per event
 constexpr int GC_THREADS = 448;
 constexpr int GCW_LOAD = 12, GCW_MMA = 13;
 constexpr uint32_t GC_TMEM_COLS = 512;
-constexpr uint32_t GC_SLICE = 16384;             // 128 columns x 64 rows of f16 digits
-constexpr uint32_t GC_BUF = NDIG * GC_SLICE;     // 128 KB
+constexpr uint32_t GC_SBO = GC_GROUP * 16;       // 8-column core-matrix groups: 512 B
+constexpr uint32_t GC_SLICE = 16 * GC_SBO;       // 128 columns x 32 rows of f16 digits: 8 KB
+constexpr uint32_t GC_BUF = NDIG * GC_SLICE;     // 64 KB
 constexpr uint32_t GC_ROW = GC_COLS * 8;         // staged row: 1 KB
 constexpr uint32_t GC_STAGE = GC_SUB * GC_ROW;   // 32 KB sub-tile
 constexpr size_t COFF_SL = 0;
-constexpr size_t COFF_STAGE = COFF_SL + GC_BUF;
+constexpr size_t COFF_STAGE = COFF_SL + 2 * (size_t)GC_BUF;
 constexpr size_t COFF_COLE = COFF_STAGE + 2 * (size_t)GC_STAGE;
 constexpr size_t COFF_EVT = COFF_COLE + 4 * GC_COLS * sizeof(int);
 constexpr size_t COFF_BARS = COFF_EVT + 16 * sizeof(int);
-constexpr int GC_NBARS = 11;  // full[2], empty[2], sl_full, sl_empty, t_full, t_empty, drain, scale, ev
+// full[2], empty[2], sl_full[2], sl_empty[2], t_full, t_empty, drain, scale, ev
+constexpr int GC_NBARS = 13;
 constexpr size_t COFF_MISC = COFF_BARS + GC_NBARS * 8;
 constexpr size_t GC_SMEM = COFF_MISC + 16;
 static_assert(GC_SMEM <= 232448, "shared memory budget");
@@ -52,15 +54,15 @@ enum GcLoad { GC_LOAD_BLOCK = 0, GC_LOAD_ROWS = 1, GC_LOAD_PLAIN = 2 };
 
 // Byte offset, within a slice, of column J's core-matrix row (K-group 0).
 __device__ __forceinline__ uint32_t gc_col_off(int J) {
-  return (uint32_t)(2 * ((J & 63) >> 3) + (J >> 6)) * 1024u + (uint32_t)(J & 7) * 16u;
+  return (uint32_t)(2 * ((J & 63) >> 3) + (J >> 6)) * GC_SBO + (uint32_t)(J & 7) * 16u;
 }
 
-// One 64-row group's products (K = 64 in four steps): A slice s (all columns) times B slices t
+// One 32-row group's products (K = 32 in two steps): A slice s (all columns) times B slices t
 // of block 1 stacked along N (at most four per MMA), into regions s + t.  The two slice-0
 // products of an event's first group open all eight regions.
 __device__ __forceinline__ void gc_issue_group(uint32_t tmem, uint64_t dA, uint64_t dB, bool first) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < GC_GROUP / 16; ++c) {
     const uint64_t kc = (uint64_t)(256 * c) >> 4;
 #pragma unroll
     for (int s = 0; s < NDIG; ++s) {
@@ -92,9 +94,9 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
   volatile int *abort_flag = (volatile int *)(gc_smem + COFF_MISC + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]);
-  const uint32_t slf = smem_addr(&bars[4]), sle = smem_addr(&bars[5]);
-  const uint32_t t_full = smem_addr(&bars[6]), t_empty = smem_addr(&bars[7]), drain = smem_addr(&bars[8]);
-  const uint32_t scale_bar = smem_addr(&bars[9]), ev_bar = smem_addr(&bars[10]);
+  const uint32_t slf0 = smem_addr(&bars[4]), sle0 = smem_addr(&bars[6]);
+  const uint32_t t_full = smem_addr(&bars[8]), t_empty = smem_addr(&bars[9]), drain = smem_addr(&bars[10]);
+  const uint32_t scale_bar = smem_addr(&bars[11]), ev_bar = smem_addr(&bars[12]);
   auto fail = [&]() {
     if (!*abort_flag) {
       *abort_flag = 1;
@@ -106,9 +108,9 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
     for (int q = 0; q < 2; ++q) {
       mbar_init_count(full0 + 8 * q, 1);
       mbar_init_count(empty0 + 8 * q, 4);
+      mbar_init_count(slf0 + 8 * q, 4);
+      mbar_init_count(sle0 + 8 * q, 1);
     }
-    mbar_init_count(slf, 4);
-    mbar_init_count(sle, 1);
     mbar_init_count(t_full, 1);
     mbar_init_count(t_empty, 8);
     mbar_init_count(drain, 1);
@@ -133,17 +135,19 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
 
   if (warp == GCW_LOAD) {
     // ------------------------------------------------------------------ loader
+    // group g (one 32-row sub-tile) goes to slot g & 1, on the slot's (g >> 1)-th use
     int last_g[2] = {-1, -1};
     for (int g = 0; g < ngroups && !*abort_flag; ++g) {
       bool ok = true;
-      for (int q = 0; q < 2; ++q) {
-        if (!mbar_wait_or_abort(empty0 + 8 * q, (uint32_t)((g & 1) ^ 1), abort_flag, lim)) {
+      {
+        const int q = g & 1;
+        if (!mbar_wait_or_abort(empty0 + 8 * q, (uint32_t)(((g >> 1) & 1) ^ 1), abort_flag, lim)) {
           if (lane == 0) fail();
           ok = false;
           break;
         }
-        const int64_t r0 = r_begin + (int64_t)g * GC_GROUP + GC_SUB * q;
-        const int cnt = sub_rows(g, q);
+        const int64_t r0 = r_begin + (int64_t)g * GC_GROUP;
+        const int cnt = sub_rows(g, 0);
         uint8_t *dst = stage + (size_t)q * GC_STAGE;
         const uint32_t fb = full0 + 8 * q;
         if (cnt > 0 && load_mode == GC_LOAD_BLOCK) {
@@ -169,12 +173,14 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
     }
     if (lane == 0)
       for (int q = 0; q < 2; ++q)
-        if (last_g[q] >= 0) mbar_wait(full0 + 8 * q, (uint32_t)(last_g[q] & 1));
+        if (last_g[q] >= 0) mbar_wait(full0 + 8 * q, (uint32_t)((last_g[q] >> 1) & 1));
   } else if (warp == GCW_MMA) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint64_t dA = umma_desc(smem_addr(slices), 128, 1024);
-      const uint64_t dB = umma_desc(smem_addr(slices) + 1024, 128, 2048);
+      const uint64_t dA0 = umma_desc(smem_addr(slices), 128, GC_SBO);
+      const uint64_t dB0 = umma_desc(smem_addr(slices) + GC_SBO, 128, 2 * GC_SBO);
+      const uint64_t dA1 = umma_desc(smem_addr(slices + GC_BUF), 128, GC_SBO);
+      const uint64_t dB1 = umma_desc(smem_addr(slices + GC_BUF) + GC_SBO, 128, 2 * GC_SBO);
       int ev = 0, pending_g = -1, last_g = -1;
       bool ok = true;
       auto close_event = [&]() {
@@ -185,7 +191,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
         pending_g = -1;
       };
       for (int g = 0; g < ngroups && ok; ++g) {
-        if (!mbar_wait_or_abort(slf, (uint32_t)(g & 1), abort_flag, lim)) {
+        const int b = g & 1;  // slice buffer
+        if (!mbar_wait_or_abort(slf0 + 8 * b, (uint32_t)((g >> 1) & 1), abort_flag, lim)) {
           ok = false;
           break;
         }
@@ -199,11 +206,11 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
           pending_g = g;
         }
         fence_after_sync();
-        uint64_t a = dA, b = dB;
-        asm volatile("" : "+l"(a), "+l"(b));
-        gc_issue_group(tmem, a, b, !merge);
+        uint64_t da = b ? dA1 : dA0, db = b ? dB1 : dB0;
+        asm volatile("" : "+l"(da), "+l"(db));
+        gc_issue_group(tmem, da, db, !merge);
         last_g = g;
-        umma_commit(sle);
+        umma_commit(sle0 + 8 * b);
       }
       if (ok && pending_g >= 0) close_event();
       if (ok && mbar_wait_or_abort(t_empty, (uint32_t)((ev & 1) ^ 1), abort_flag, lim)) {
@@ -218,21 +225,23 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
     __syncwarp();
   } else if (warp < 4) {
     // ------------------------------------------------------------------ scales and slices
-    // Lane: columns J0 = 16 warp + (lane & 15) and J1 = J0 + 64, rows of sub-tile h = lane >> 4.
+    // Lane: columns J0 = 16 warp + (lane & 15) and J1 = J0 + 64, rows 16 h .. 16 h + 15 of the
+    // group (h = lane >> 4).
     const int h = lane >> 4;
+    constexpr int RPT = GC_GROUP / 2;
     int Jc[2], E[2], mxe[2];
     Jc[0] = 16 * warp + (lane & 15);
     Jc[1] = Jc[0] + 64;
     int ev_len = 0, n_scale_syncs = 0;
     for (int g = 0; g < ngroups; ++g) {
-      bool ok = true;
-      for (int q = 0; q < 2 && ok; ++q) ok = mbar_wait_or_abort(full0 + 8 * q, (uint32_t)(g & 1), abort_flag, lim);
+      const int b = g & 1;  // stage slot and slice buffer of the group
+      bool ok = mbar_wait_or_abort(full0 + 8 * b, (uint32_t)((g >> 1) & 1), abort_flag, lim);
       if (!ok) {
         if (lane == 0) fail();
         break;
       }
-      const int cnt = sub_rows(g, h);
-      const uint8_t *srow = stage + (size_t)h * GC_STAGE;
+      const int cnt = sub_rows(g, 0) - RPT * h;  // rows of this lane's range that exist
+      const uint8_t *srow = stage + (size_t)b * GC_STAGE + (size_t)(RPT * h) * GC_ROW;
       const bool spec = g > 0 && ev_len < GC_EV_GROUPS;
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
         } else {
           int mx = 0;
 #pragma unroll 8
-          for (int r = 0; r < GC_SUB; ++r) {
+          for (int r = 0; r < RPT; ++r) {
             const unsigned long long bits = (cj && r < cnt) ? *(const unsigned long long *)(srow + r * GC_ROW + 8 * J) : 0ULL;
             mx = max(mx, (int)((bits >> 52) & 0x7ff));
           }
@@ -251,8 +260,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
           E[cc] = scale_exp(mx) + 1;
         }
       }
-      // the previous group's products have read the slice buffer
-      if (!mbar_wait_or_abort(sle, (uint32_t)((g & 1) ^ 1), abort_flag, lim)) {
+      // the products of group g - 2 have read slice buffer b
+      if (!mbar_wait_or_abort(sle0 + 8 * b, (uint32_t)(((g >> 1) & 1) ^ 1), abort_flag, lim)) {
         if (lane == 0) fail();
         break;
       }
@@ -262,10 +271,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
         for (int cc = 0; cc < 2; ++cc) {
           const int J = Jc[cc];
           const bool cj = J < n;
-          uint8_t *buf = slices + gc_col_off(J);
+          uint8_t *buf = slices + (size_t)b * GC_BUF + gc_col_off(J);
           int mxl = 0;
 #pragma unroll 1
-          for (int r0 = 0; r0 < GC_SUB; r0 += 8) {
+          for (int r0 = 0; r0 < RPT; r0 += 8) {
             uint32_t w[4][NDIG];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
               mxl = max(mxl, max((int)((ba >> 52) & 0x7ff), (int)((bb >> 52) & 0x7ff)));
               digits2_biased(fix54_biased<DIG_BIAS>(ba, E[cc]), fix54_biased<DIG_BIAS>(bb, E[cc]), w[u]);
             }
-            const int kg = (GC_SUB * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the group
+            const int kg = (RPT * h + r0) >> 3;  // K-group of rows r0 .. r0 + 7 within the group
 #pragma unroll
             for (int p = 0; p < NDIG; ++p)
               *(uint4 *)(buf + (size_t)(NDIG - 1 - p) * GC_SLICE + kg * 128) = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
@@ -315,13 +324,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1)
       }
       if (warp == 0 && lane == 0) evt[g % 3] = merge;
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(empty0);
-        mbar_arrive(empty0 + 8);
-      }
+      if (lane == 0) mbar_arrive(empty0 + 8 * b);
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(slf);
+      if (lane == 0) mbar_arrive(slf0 + 8 * b);
     }
   } else {
     // ------------------------------------------------------------------ recombination and sums
