@@ -39,9 +39,12 @@ FP64_ALU_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # or (hi, lo) FP32 pair read per element, plus the write for the solves).
 
 def identity_gap2(G):
-    """||G - I||_2 of a small symmetric Gram, on the host (numpy's symmetric eigensolver)."""
+    """||G - I||_2 of a small symmetric Gram, on the host (numpy's symmetric eigensolver); inf
+    when G is not finite, so that a maximum over results cannot hide a bad one."""
     import numpy as np
     Gh = G.double().cpu().numpy()
+    if not np.isfinite(Gh).all():
+        return float("inf")
     return float(np.abs(np.linalg.eigvalsh(Gh - np.eye(Gh.shape[0]))).max())
 
 def roofline_model(kind, n):
@@ -356,12 +359,11 @@ def serve_bench(rq, synthetic, torch, dev, n_req=20000, loads=(0.5, 0.8, 0.95), 
             if arrivals is not None and not pending and nxt < n_req:
                 time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
         span = time.perf_counter() - t0
-        worst = 0.0
-        for i, (Q, R) in sample.items():
-            worst = max(worst, identity_gap2(Q.T @ Q))
+        gaps = [identity_gap2(Q.T @ Q) for Q, R in sample.values()]
         sctx.close()
         return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_req_s": n_req / span,
-                "eff_GBs": bytes_total / span / 1e9, "max_orth_err_2_sampled": worst}
+                "eff_GBs": bytes_total / span / 1e9, "max_orth_err_2_sampled": max(gaps, default=float("nan")),
+                "samples": len(gaps), "samples_not_finite": sum(1 for g in gaps if g == float("inf"))}
 
     bytes_total = sum(32.0 * m * n for (m, n, k) in reqs)
     res = {"requests": n_req, "slots": 8, "budget_bytes": 64 << 30,
