@@ -298,21 +298,24 @@ cudaError_t launch_hhqr(double *A, int64_t rows, int64_t n, double *Rpacked, dou
 // r_jj = sqrt(g_jj); r_jl = g_jl / r_jj; g_kl -= r_jk r_jl for j < k <= l.  A pivot that is
 // not > 0 (or NaN) stops the factorization with RANDQR_ERR_NOT_SPD(j+1).  If shift_coeff
 // is nonzero, shift_coeff * trace(G) is added to the diagonal first (sCholQR3's shift,
-// since trace(V^T V) = ||V||_F^2).
+// since trace(V^T V) = ||V||_F^2).  Step j's row of R is copied to a contiguous buffer, and the
+// trailing update gives each warp whole columns l (lanes down the rows k <= l of the packed
+// column), so no thread divides to find its entry.
 // Then, if Rprev is given, Rout = R Rprev (upper x upper, packed); if Rout_dense is given,
-// the final factor (Rout, or R itself) is written there row-major with zeros below.
+// the final factor (Rout, or R itself) is written there row-major with zeros below: a second
+// kernel over many CTAs (the product's n^3 / 6 FP64 multiply-adds would take one SM's FP64
+// pipe about 0.1 ms at n = 128).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, double shift_coeff,
-                                                         double *Rcp, const double *Rprev,
-                                                         double *Routp, double *Rdense,
-                                                         int64_t ldr, int stage, DevStatus *st) {
+__global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, double shift_coeff, double *Rcp,
+                                                         int stage, DevStatus *st) {
   if (status_failed(st)) return;
-  extern __shared__ double A[];  // packed upper, n(n+1)/2
+  extern __shared__ double A[];  // packed upper, n(n+1)/2, then row j of R (n)
   __shared__ double red[32];
   __shared__ int s_fail;
   __shared__ double s_inv;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   const int P = n * (n + 1) / 2;
+  double *rowj = A + P;
   for (int e = tid; e < P; e += nt) A[e] = Gp[e];
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -336,15 +339,18 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, doub
     }
     __syncthreads();
     if (s_fail) break;
-    // row j of R by the pivot's reciprocal (one multiply per entry; the single FP64 pipe of
-    // this SM is the limit here, not the latency), then the trailing update
+    // row j of R by the pivot's reciprocal (one multiply per entry), kept contiguous as well
     const double inv = s_inv;
-    for (int l = j + 1 + tid; l < n; l += nt) A[tri_idx(j, l)] *= inv;
+    for (int l = j + 1 + tid; l < n; l += nt) {
+      const double v = A[tri_idx(j, l)] * inv;
+      A[tri_idx(j, l)] = v;
+      rowj[l] = v;
+    }
     __syncthreads();
-    const int m = n - j - 1;  // trailing k, l in (j, n)
-    for (int e = tid; e < m * m; e += nt) {
-      const int k = j + 1 + e / m, l = j + 1 + e % m;
-      if (k <= l) A[tri_idx(k, l)] = fma(-A[tri_idx(j, k)], A[tri_idx(j, l)], A[tri_idx(k, l)]);
+    for (int l = j + 1 + warp; l < n; l += nwarps) {
+      const double rl = rowj[l];
+      double *col = A + l * (l + 1) / 2;  // column l: rows 0 .. l
+      for (int k = j + 1 + lane; k <= l; k += 32) col[k] = fma(-rowj[k], rl, col[k]);
     }
     __syncthreads();
   }
@@ -353,17 +359,31 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, doub
     return;
   }
   for (int e = tid; e < P; e += nt) Rcp[e] = A[e];
-  if (Rprev == nullptr && Rdense == nullptr) return;
-  // Rout(i, j) = sum_{k=i..j} R(i, k) Rprev(k, j)
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e % n;
+}
+
+// Rout(i, j) = sum_{k=i..j} R(i, k) Rprev(k, j) (packed, when Routp) and the dense row-major
+// Rdense (Rout, or R itself without Rprev), zeros below; both triangles staged in shared memory
+// by every CTA, one output per thread.
+__global__ void __launch_bounds__(256) k_tri_mul(const double *Rp, const double *Rprev, int n, double *Routp,
+                                                 double *Rdense, int64_t ldr, const DevStatus *st) {
+  if (status_failed(st)) return;
+  extern __shared__ double tm_sm[];
+  const int P = n * (n + 1) / 2;
+  double *Ra = tm_sm, *Rb = tm_sm + P;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    Ra[e] = Rp[e];
+    if (Rprev) Rb[e] = Rprev[e];
+  }
+  __syncthreads();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
     double v = 0.0;
     if (j >= i) {
       if (Rprev) {
-        for (int k = i; k <= j; ++k) v = fma(A[tri_idx(i, k)], Rprev[tri_idx(k, j)], v);
+        for (int k = i; k <= j; ++k) v = fma(Ra[tri_idx(i, k)], Rb[tri_idx(k, j)], v);
         if (Routp) Routp[tri_idx(i, j)] = v;
       } else {
-        v = A[tri_idx(i, j)];
+        v = Ra[tri_idx(i, j)];
       }
     }
     if (Rdense) Rdense[(int64_t)i * ldr + j] = v;
@@ -373,13 +393,21 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_potrf(double *Gp, int n, doub
 cudaError_t launch_potrf(double *G, int64_t n, double shift_coeff, double *Rc_packed,
                          const double *Rprev_packed, double *Rout_packed, double *Rout,
                          int64_t ldr, int32_t stage, DevStatus *st, cudaStream_t s) {
-  size_t dyn = sizeof(double) * (size_t)(n * (n + 1) / 2);
+  const size_t dyn = sizeof(double) * (size_t)(n * (n + 1) / 2 + n);
   if (dyn > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  k_potrf<<<1, SMALL_THREADS, dyn, s>>>(G, (int)n, shift_coeff, Rc_packed, Rprev_packed,
-                                        Rout_packed, Rout, ldr, stage, st);
+  k_potrf<<<1, SMALL_THREADS, dyn, s>>>(G, (int)n, shift_coeff, Rc_packed, stage, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || (Rprev_packed == nullptr && Rout == nullptr)) return e;
+  const size_t dyn2 = sizeof(double) * (size_t)(n * (n + 1));
+  if (dyn2 > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_tri_mul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn2);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (int)std::min<int64_t>(64, std::max<int64_t>(1, (n * n + 255) / 256));
+  k_tri_mul<<<blocks, 256, dyn2, s>>>(Rc_packed, Rprev_packed, (int)n, Rout_packed, Rout, ldr, st);
   return cudaGetLastError();
 }
 
