@@ -60,6 +60,20 @@ __device__ __forceinline__ uint32_t hc_rank() {
   return r;
 }
 
+// Sum of one value per thread over the CTA, returned to every thread (red: 32 doubles).  Ends
+// with a barrier, so shared-memory writes before it are seen by every thread after it.
+__device__ __forceinline__ double hc_block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // red is free (an earlier sum's readers are done)
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < HC_THREADS / 32; ++w) t += red[w];
+  return t;
+}
+
 // Reflector j from local column `col` (one warp): pub = [tau, beta, v_0 .. v_(rows-1)] with v
 // stored at its row index (rows j + 1 ..); col keeps beta at row j and v below.
 __device__ __forceinline__ void hc_reflect(double *col, int rows, int j, double *pub, int lane) {
@@ -104,7 +118,8 @@ __global__ void __launch_bounds__(HC_THREADS) k_hhqr_cluster(const double *Ag, i
   double *betas = pub + rows + 2;                       // n: every reflector's beta
   __shared__ int s_flag;                                // reflectors published by this CTA: last j + 1
   __shared__ int s_fail;
-  __shared__ double s_tau;
+  __shared__ double s_tau, s_rv0;
+  __shared__ double red[32];
   for (int e = tid; e < ncl * rows; e += HC_THREADS) {
     const int c = e / rows, i = e - c * rows;
     cols[e] = Ag[(size_t)i * n + b + HC_CTAS * c];
@@ -142,14 +157,14 @@ __global__ void __launch_bounds__(HC_THREADS) k_hhqr_cluster(const double *Ag, i
     }
     __syncthreads();
     const double tau = s_tau;
-    // local columns k > j; the owner of column j + 1 handles it first and publishes reflector j + 1
+    // The owner of column j + 1 updates that column and forms reflector j + 1 first (the step's
+    // critical path), then its other columns one warp each; the other CTAs go straight to their
+    // columns.  Tall sketches (rows >= 256) spread the critical column over all the owner's
+    // threads, so its FP64 work runs on every scheduler; shorter ones keep it on one warp.
     const int c_next = (j + 1 < n && (j + 1) % HC_CTAS == b) ? (j + 1) / HC_CTAS : -1;
-    for (int t = warp; t < ncl; t += HC_THREADS / 32) {
-      int c = t;
-      if (c_next >= 0) c = (t == 0) ? c_next : (t <= c_next ? t - 1 : t);
-      const int k = b + HC_CTAS * c;
-      if (k <= j) continue;
-      double *col = cols + (size_t)c * rows;
+    const bool coop = rows >= 256;
+    if (c_next >= 0 && !coop && warp == 0) {
+      double *col = cols + (size_t)c_next * rows;
       if (tau != 0.0) {
         double acc = 0.0;
         for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(vsh[i], col[i], acc);
@@ -160,10 +175,60 @@ __global__ void __launch_bounds__(HC_THREADS) k_hhqr_cluster(const double *Ag, i
         for (int i = j + 1 + lane; i < rows; i += 32) col[i] = fma(-vsh[i], w, col[i]);
         __syncwarp();
       }
-      if (c == c_next) {
-        hc_reflect(col, rows, j + 1, pub, lane);
-        __syncwarp();  // the warp's writes of the reflector, then the flag (release, cluster scope)
-        if (lane == 0) hc_st_release(flag_local, j + 2);
+      hc_reflect(col, rows, j + 1, pub, lane);
+      __syncwarp();  // the warp's writes of the reflector, then the flag (release, cluster scope)
+      if (lane == 0) hc_st_release(flag_local, j + 2);
+    }
+    if (c_next >= 0 && coop) {
+      double *col = cols + (size_t)c_next * rows;
+      if (tau != 0.0) {
+        double part = 0.0;
+        for (int i = j + 1 + tid; i < rows; i += HC_THREADS) part = fma(vsh[i], col[i], part);
+        const double w = tau * (col[j] + hc_block_sum(part, red));  // all threads read col[j] ...
+        for (int i = j + 1 + tid; i < rows; i += HC_THREADS) col[i] = fma(-vsh[i], w, col[i]);
+        __syncthreads();                                            // ... before it changes
+        if (tid == 0) col[j] -= w;
+      }
+      double part = 0.0;
+      for (int i = j + 2 + tid; i < rows; i += HC_THREADS) part = fma(col[i], col[i], part);
+      const double sigma = hc_block_sum(part, red);  // also orders the update before the reads below
+      if (tid == 0) {
+        const double x0 = col[j + 1];
+        double tau1 = 0.0, beta = x0, rv0 = 0.0;
+        if (sigma != 0.0) {
+          const double alpha = sqrt(x0 * x0 + sigma);
+          beta = (x0 >= 0.0) ? -alpha : alpha;
+          rv0 = 1.0 / (x0 - beta);
+          tau1 = (beta - x0) / beta;
+        }
+        s_rv0 = rv0;
+        col[j + 1] = beta;
+        pub[0] = tau1;
+        pub[1] = beta;
+      }
+      __syncthreads();
+      const double rv0 = s_rv0;
+      for (int i = j + 2 + tid; i < rows; i += HC_THREADS) {
+        const double v = col[i] * rv0;
+        col[i] = v;
+        pub[2 + i] = v;
+      }
+      __syncthreads();  // the whole reflector is written, then the flag (release, cluster scope)
+      if (tid == 0) hc_st_release(flag_local, j + 2);
+    }
+    if (tau != 0.0) {
+      for (int c = warp; c < ncl; c += HC_THREADS / 32) {
+        const int k = b + HC_CTAS * c;
+        if (k <= j || c == c_next) continue;
+        double *col = cols + (size_t)c * rows;
+        double acc = 0.0;
+        for (int i = j + 1 + lane; i < rows; i += 32) acc = fma(vsh[i], col[i], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double w = tau * (col[j] + acc);
+        __syncwarp();
+        if (lane == 0) col[j] -= w;
+        for (int i = j + 1 + lane; i < rows; i += 32) col[i] = fma(-vsh[i], w, col[i]);
+        __syncwarp();
       }
     }
     __syncthreads();
