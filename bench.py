@@ -189,6 +189,23 @@ def cpu_baseline(n, kappa, rows, s1, s2):
                       f"same s1/s2), single-threaded FP64 C oracle, {dt:.1f} s"}
 
 
+def cpu_baseline_small():
+    """The oracle on the small-matrix configuration (m = 20000, n = 16, kappa = 1e10,
+    s1 = 544, s2 = 64): microseconds per call, single thread, the mean of 5 calls."""
+    import oracle
+    import synthetic
+    m, n = 20000, 16
+    V = synthetic.make_v(m, n, 1e10, seed=0)
+    S2 = oracle.gauss_sketch(1, 64, 544)
+    oracle.rand_cholqr(V, 544, 64, seed=0, S2=S2)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        oracle.rand_cholqr(V, 544, 64, seed=0, S2=S2)
+    us = (time.perf_counter() - t0) / 5 * 1e6
+    return {"value": us, "unit": "us per call", "cores": 1, "kind": "oracle",
+            "sample": "rand_cholQR m=20000 n=16 kappa=1e10 s1=544 s2=64, single-threaded FP64 C oracle"}
+
+
 def cpu_baseline_parallel(n, kappa, rows, s1, s2):
     """The oracle's own routines, unchanged, on every host core: the row-block decomposition
     of Sec. 4.1 (per-block CountSketch with the global row index, trsm and Gram), one thread per
@@ -359,11 +376,18 @@ def serve_bench(rq, synthetic, torch, dev, n_req=20000, loads=(0.5, 0.8, 0.95), 
             if arrivals is not None and not pending and nxt < n_req:
                 time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
         span = time.perf_counter() - t0
-        gaps = [identity_gap2(Q.T @ Q) for Q, R in sample.values()]
+        gaps, first = [], []
+        for i, (Q, R) in sample.items():
+            G = Q.T @ Q
+            gaps.append(identity_gap2(G))
+            if len(first) < 3:  # what the first sampled results look like
+                first.append({"request": i, "m": Q.shape[0], "n": Q.shape[1], "gap": gaps[-1],
+                              "q_fro2": float((Q * Q).sum().item()), "r00": float(R[0, 0].item())})
         sctx.close()
         return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_req_s": n_req / span,
                 "eff_GBs": bytes_total / span / 1e9, "max_orth_err_2_sampled": max(gaps, default=float("nan")),
-                "samples": len(gaps), "samples_not_finite": sum(1 for g in gaps if g == float("inf"))}
+                "samples": len(gaps), "samples_not_finite": sum(1 for g in gaps if g == float("inf")),
+                "samples_exact": sum(1 for g in gaps if g == 0.0), "first_samples": first}
 
     bytes_total = sum(32.0 * m * n for (m, n, k) in reqs)
     res = {"requests": n_req, "slots": 8, "budget_bytes": 64 << 30,
@@ -863,6 +887,11 @@ def main():
             line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
             line["row_pass_l2_resident"] = l2_resident_rowpass(rq, synthetic, torch, dev)
             line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
+            # the headline shape across the conditioning range (accuracy; the timing does not
+            # depend on kappa)
+            for kap in (1.0, 1e4, 1e8, 1e15):
+                line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 64, kap,
+                                                          rq.FP64, steps=1))
             for kap in (1e2, 1e6, 1e10, 1e12):
                 for pr in (rq.FP64, rq.F32X2):
                     line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
@@ -876,6 +905,7 @@ def main():
         if rank == 0:
             line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18, s1, s2)
             line["cpu_baseline_parallel"] = cpu_baseline_parallel(n, a.kappa, 1 << 20, s1, s2)
+            line["cpu_baseline_small"] = cpu_baseline_small()
 
     if rank == 0:
         print(json.dumps(line), flush=True)
