@@ -51,7 +51,7 @@ def roofline_model(kind, n):
     return {"trsm": ("alu", n * n), "gram": ("alu", n * (n + 1)),
             "cs_scatter": ("hbm", 8 * n), "trsm_df": ("hbm", 16 * n),
             "gram_df": ("hbm", 8 * n), "gram_tc": ("hbm", 8 * n),
-            "trsm_tc": ("hbm", 16 * n)}.get(kind)
+            "trsm_tc": ("hbm", 16 * n), "solve_gram": ("hbm", 16 * n)}.get(kind)
 
 
 # DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
@@ -98,6 +98,8 @@ def parse():
     p.add_argument("--s1", type=int, default=0, help="CountSketch size (default 2 (n^2 + n))")
     p.add_argument("--s2", type=int, default=0, help="Gaussian sketch size (default 4 n)")
     p.add_argument("--prec", default="fp64", choices=["fp64", "f32x2"])
+    p.add_argument("--fused", action="store_true",
+                   help="n = 64: the first solve and the Gram in one fused launch instead of two")
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, baselines, CPU baseline (quick runs)")
     p.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
@@ -624,6 +626,8 @@ def main():
     Q = torch.empty_like(V)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
     ctx = rq.Context(local_rank)
+    if a.fused:
+        ctx.set_fused_first_pass(True)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -766,6 +770,13 @@ def main():
             line["modes"] = {other: {"value": algo_bytes / (oms / 1e3) / 1e9, "unit": "GB/s",
                                      "ms_per_step": oms, "accuracy": oacc,
                                      "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
+            # the first row pass as one fused launch or as two (solve, then the Gram of W)
+            ctx.set_fused_first_pass(not a.fused)
+            tms, tkt, _, tacc = measure(prec, a.steps)
+            ctx.set_fused_first_pass(a.fused)
+            line["modes"]["two_pass" if a.fused else "fused_first_pass"] = {
+                "value": algo_bytes / (tms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": tms,
+                "accuracy": tacc, "kernels_ms_per_step": {k: v[0] / a.steps for k, v in tkt.items()}}
 
         # end to end through the public API: pinned host V in, Q and R back to pinned host,
         # every step.  On one GPU that is the host-buffer call randqr_factor_host (its own

@@ -138,6 +138,18 @@ randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls);
  * selects the CUDA-core kernels of the chosen precision everywhere. */
 randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable);
 
+/* The first row pass of rand_cholQR in one launch (Algorithm 3 with the Gram of Algorithm 2
+ * step 1; default off): for n = 64 with the tensor cores on, contiguous rows (ldv = ldq = 64) and
+ * 16-byte aligned V and Q, W = V R_s^{-1} and G = W^T W come from one kernel on pairs of CTAs --
+ * one forms and stores W, the other takes the Gram of the rows just stored (from L2) -- so V is
+ * read once and W written once before the Cholesky factorization, instead of a solve pass
+ * followed by a Gram pass that reads W again: 16 m n fewer bytes of HBM traffic per
+ * factorization.  The arithmetic is that of the two separate kernels.  Both passes are bound by
+ * their instruction issue rather than by HBM on this path, and the fused launch runs each of
+ * them on half of the SMs, so it is not faster; enable = 1 selects it (randQR's shard stage,
+ * randqr_shard_gram, follows the same switch).  Returns RANDQR_ERR_ARG for a null ctx. */
+randqr_status randqr_set_fused_first_pass(randqr_ctx *ctx, int enable);
+
 /* ---- Per-kernel timing (tracing) ------------------------------------------------------
  * While profiling is on, every kernel the context launches is bracketed by two CUDA events
  * recorded on the call's stream.  randqr_get_kernel_times waits for those events, writes

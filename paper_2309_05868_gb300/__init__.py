@@ -162,6 +162,14 @@ class Context:
         L.randqr_set_tensor_cores.restype = _ct.c_int32
         self._check(L.randqr_set_tensor_cores(self._h, int(bool(enable))))
 
+    def set_fused_first_pass(self, enable=True):
+        """rand_cholQR at n = 64: the first solve and the Gram of W in one launch on paired CTAs,
+        or as two passes (the default); see randqr.h."""
+        L = _load()
+        L.randqr_set_fused_first_pass.argtypes = [_ct.c_void_p, _ct.c_int]
+        L.randqr_set_fused_first_pass.restype = _ct.c_int32
+        self._check(L.randqr_set_fused_first_pass(self._h, int(bool(enable))))
+
     def set_wait_limit(self, polls):
         """Poll bound of the kernels' bounded waits (< 0: the defaults); see randqr.h."""
         self._check(_load().randqr_set_wait_limit(self._h, int(polls)))

@@ -482,16 +482,18 @@ randqr_status cholqr_pass(randqr_ctx *ctx, const double *X, int64_t ldx, double 
                           int64_t m, int64_t n, double shift_coeff, const double *Rprev,
                           double *Rnext, double *Rdense, int64_t ldr, int stage,
                           randqr_precision prec, const Workspace &w, cudaStream_t s,
-                          bool inverse_ok = false, int digits = 7) {
-  RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
-  if (ctx->use_tc && rq::gram_oz_supported(n)) {
-    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
-      return launch_gram_tc(ctx, X, false, ldx, m, n, w.G, s);
-    }));
-  } else {
-    RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
-      return rq::launch_gram(X, ldx, m, n, w.G, prec, ctx->num_sms, ctx->status_dev, s);
-    }));
+                          bool inverse_ok = false, int digits = 7, bool gram_done = false) {
+  if (!gram_done) {  // (gram_done: G = X^T X is already in w.G, formed by the fused first pass)
+    RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+    if (ctx->use_tc && rq::gram_oz_supported(n)) {
+      RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] {
+        return launch_gram_tc(ctx, X, false, ldx, m, n, w.G, s);
+      }));
+    } else {
+      RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+        return rq::launch_gram(X, ldx, m, n, w.G, prec, ctx->num_sms, ctx->status_dev, s);
+      }));
+    }
   }
   RQ_CUDA(timed(ctx, s, rq::K_POTRF, [&] {
     return rq::launch_potrf(w.G, n, shift_coeff, w.Rc, Rprev, Rnext, Rdense, ldr, stage,
@@ -564,6 +566,13 @@ randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable) {
   return RANDQR_OK;
 }
 
+randqr_status randqr_set_fused_first_pass(randqr_ctx *ctx, int enable) {
+  if (!ctx) return RANDQR_ERR_ARG;
+  if (ctx->fuse_first_pass != (enable != 0) && ctx->batcher) rq_batcher_destroy(ctx);  // graphs hold the old kernels
+  ctx->fuse_first_pass = enable != 0;
+  return RANDQR_OK;
+}
+
 randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls) {
   if (!ctx) {
     rq_static_set_wait_limit(polls);
@@ -610,7 +619,7 @@ const char *randqr_kernel_name(int32_t kind) {
   static const char *names[rq::K_NUM_KINDS] = {"gauss_gen", "cs_scatter", "sketch_gemm", "hhqr",
                                                "trsm", "gram", "potrf", "unpack", "cs_hash",
                                                "pack_df", "trsm_df", "gram_df", "gram_tc",
-                                               "tri_inv", "trsm_tc"};
+                                               "tri_inv", "trsm_tc", "solve_gram"};
   return (kind >= 0 && kind < rq::K_NUM_KINDS) ? names[kind] : "unknown";
 }
 
@@ -770,11 +779,21 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
     // products, its stated precision) instead of seven.
     const int dg = prec == RANDQR_F32X2 ? 6 : 7;
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
-    RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
-      return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s, dg);
-    }));
+    // n = 64: the solve and the Gram of W in one launch (W stored once, its Gram taken on paired
+    // CTAs as the rows are stored); otherwise the solve, then the Gram inside the Cholesky pass
+    const bool fused = ctx->fuse_first_pass && rq::solve_gram_supported(n, V, ldv, Q, ldq, ctx->num_sms);
+    if (fused) {
+      RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+      RQ_CUDA(timed(ctx, s, rq::K_SOLVE_GRAM, [&] {
+        return rq::launch_solve_gram(V, ldv, Q, ldq, m, n, w.Rt2, w.G, ctx->num_sms, ctx->status_dev, s, dg);
+      }));
+    } else {
+      RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
+        return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s, dg);
+      }));
+    }
     if ((st = cholqr_pass(ctx, Q, ldq, Q, ldq, m, n, 0.0, w.Rs, nullptr, R, ldr, 1, RANDQR_FP64, w, s,
-                          /*inverse_ok=*/true, dg)) != RANDQR_OK)
+                          /*inverse_ok=*/true, dg, /*gram_done=*/fused)) != RANDQR_OK)
       return st;
     return finish_factor(ctx, s, info, V, ldv, Q, ldq, R, ldr, m, n);
   }
@@ -962,8 +981,17 @@ randqr_status randqr_shard_gram(randqr_ctx *ctx, const double *V, int64_t m, int
   Workspace w;
   if ((st = carve(ctx, n, 1, 1, &w)) != RANDQR_OK) return st;
   RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_pack_upper(Rs, ldrs, n, w.Rs, ctx->status_dev, s); }));
-  // W_k = V_k R_s^{-1} into Q (as in randqr_factor), then G_k = W_k^T W_k
-  if (use_tc_solve(ctx, n)) {
+  // W_k = V_k R_s^{-1} into Q (as in randqr_factor), then G_k = W_k^T W_k: one fused launch
+  // where randqr_factor takes it, else the solve and then the Gram
+  const bool fused = use_tc_solve(ctx, n) && ctx->fuse_first_pass &&
+                     rq::solve_gram_supported(n, V, ldv, Q, ldq, ctx->num_sms);
+  if (fused) {
+    RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
+    RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+    RQ_CUDA(timed(ctx, s, rq::K_SOLVE_GRAM, [&] {
+      return rq::launch_solve_gram(V, ldv, Q, ldq, m, n, w.Rt2, w.G, ctx->num_sms, ctx->status_dev, s, 7);
+    }));
+  } else if (use_tc_solve(ctx, n)) {
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));
     RQ_CUDA(timed(ctx, s, rq::K_TRSM_TC, [&] {
       return rq::launch_trsm_oz(V, ldv, Q, ldq, m, n, w.Rt2, ctx->num_sms, ctx->status_dev, s);
@@ -973,13 +1001,15 @@ randqr_status randqr_shard_gram(randqr_ctx *ctx, const double *V, int64_t m, int
       return rq::launch_trsm(V, ldv, Q, ldq, m, n, w.Rs, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
     }));
   }
-  RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
-  if (ctx->use_tc && rq::gram_oz_supported(n)) {
-    RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] { return launch_gram_tc(ctx, Q, false, ldq, m, n, w.G, s); }));
-  } else {
-    RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
-      return rq::launch_gram(Q, ldq, m, n, w.G, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
-    }));
+  if (!fused) {
+    RQ_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * packed(n), s));
+    if (ctx->use_tc && rq::gram_oz_supported(n)) {
+      RQ_CUDA(timed(ctx, s, rq::K_GRAM_TC, [&] { return launch_gram_tc(ctx, Q, false, ldq, m, n, w.G, s); }));
+    } else {
+      RQ_CUDA(timed(ctx, s, rq::K_GRAM, [&] {
+        return rq::launch_gram(Q, ldq, m, n, w.G, RANDQR_FP64, ctx->num_sms, ctx->status_dev, s);
+      }));
+    }
   }
   RQ_CUDA(timed(ctx, s, rq::K_UNPACK, [&] { return rq::launch_unpack_sym(w.G, n, G, ldg, ctx->status_dev, s); }));
   return RANDQR_OK;

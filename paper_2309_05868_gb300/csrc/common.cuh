@@ -124,6 +124,7 @@ struct randqr_ctx {
   char last_err[256] = {0};
   // Gram on the tensor cores (split products) when n <= 128
   bool use_tc = true;
+  bool fuse_first_pass = false;  // rand_cholQR n = 64: first solve and Gram in one launch
   // poll bound of the kernels' waits (randqr_set_wait_limit): < 0 = defaults
   int32_t wait_limit = -1;
   // accuracy measurement (randqr_info.want_accuracy): pinned host copy of Q^T Q (packed) and
@@ -160,7 +161,7 @@ namespace rq {
 // Kernel kinds for the per-kernel timing record.
 enum KernelKind {
   K_GAUSS_GEN = 0, K_CS_SCATTER, K_SKETCH_GEMM, K_HHQR, K_TRSM, K_GRAM, K_POTRF, K_UNPACK,
-  K_CS_HASH, K_PACK_DF, K_TRSM_DF, K_GRAM_DF, K_GRAM_TC, K_TRI_INV, K_TRSM_TC, K_NUM_KINDS
+  K_CS_HASH, K_PACK_DF, K_TRSM_DF, K_GRAM_DF, K_GRAM_TC, K_TRI_INV, K_TRSM_TC, K_SOLVE_GRAM, K_NUM_KINDS
 };
 }  // namespace rq
 
@@ -245,6 +246,13 @@ cudaError_t launch_tri_inv(const double *Rpacked, int64_t n, double *Xpacked, co
 // Y = X B (B upper triangular, packed) from exact split products on the tensor cores
 // (trsm_tc.cu), n <= 64; Y may equal X (same ld)
 bool trsm_oz_supported(int64_t n);
+// The first row pass of rand_cholQR in one launch (trsm_tc.cu): W = V B (B = R_s^{-1}, packed
+// upper, 64 x 64) stored into W and G += W^T W (packed upper, zeroed by the caller), on paired
+// CTAs.  Only n = 64 with contiguous 16-byte aligned rows (ldv = ldw = 64); W may be V.
+bool solve_gram_supported(int64_t n, const double *V, int64_t ldv, const double *W, int64_t ldw, int num_sms);
+cudaError_t launch_solve_gram(const double *V, int64_t ldv, double *W, int64_t ldw, int64_t m, int64_t n,
+                              const double *Bpacked, double *Gpacked, int num_sms, DevStatus *st, cudaStream_t s,
+                              int digits);
 // One block product of a blocked solve (64 < n <= 128): Y = X B, or Y = Ref + X B when Ref is
 // given (Ref may be Y), for X with nk <= 64 columns, Y with nn <= 64.  B packed upper (b_ld = 0:
 // dimension nn, entries with row >= nk ignored), or dense row-major with leading dimension b_ld

@@ -43,6 +43,7 @@
 // c (K-step c) is released to the next tile's slicers as soon as the last MMA that reads it has
 // completed.  In place (Y == X) is safe: a tile's rows are read before any are written.
 #include "common.cuh"
+#include "gram_split_body.cuh"
 #include "tc.cuh"
 
 namespace rq {
@@ -90,14 +91,6 @@ static_assert(TQ_SMEM <= 232448, "shared memory budget");
 // needs 16-byte aligned rows and an even column count.  LOAD_PLAIN: element loads.  Every loader
 // lane arrives on the slot's barrier once per fill.
 enum LoadMode { LOAD_ASYNC = 0, LOAD_PLAIN = 1 };
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-}
-// arrives on mbar once this thread's earlier cp.async copies have landed (no extra pending count)
-__device__ __forceinline__ void cp_async_arrive(uint32_t mbar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
-}
 
 // Byte offset of element (row r, column col) of a staged sub-tile.
 __device__ __forceinline__ uint32_t stage_off(int r, int col) { return (uint32_t)r * STAGE_PITCH + (uint32_t)col * 8u; }
@@ -156,14 +149,16 @@ enum Epilogue { EPI_STORE = 0, EPI_ADDREF = 1, EPI_RESID = 2 };
 // EPI_ADDREF: Y = Ref + X B (Ref may be Y itself, read in the same column order).
 // EPI_RESID: instead of storing Y, accumulate sums[0] += sum (Ref - Y)^2 and sums[1] += sum Ref^2
 // over the rows (the residual of a factorization V = Q R, with X = Q and B = R).
-template <bool FULLN, bool REV, int EPI, int NH, int NDA>
-__global__ void __launch_bounds__(TQ_THREADS, 1)
-    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int nk, int nn,
-              const double *__restrict__ Bp, int b_ld, int64_t rows_per_cta, int load_mode, bool vec_store,
-              const double *Vref, int64_t ldvr, double *sums, DevStatus *st) {
+// SIG: after storing its rows of tile i, read-back warp f publishes i + 1 in the 32-bit word
+// sig + 4 f of this CTA's shared memory (release at cluster scope), for a Gram CTA of the same
+// cluster that reads the stored rows (k_solve_gram); PRODUCER_DONE there once it gives up.
+template <bool FULLN, bool REV, int EPI, int NH, int NDA, bool SIG>
+__device__ __forceinline__ void trsm_oz_cta(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy,
+                                            int64_t m, int nk, int nn, const double *__restrict__ Bp, int b_ld,
+                                            int64_t rows_per_cta, int load_mode, bool vec_store, const double *Vref,
+                                            int64_t ldvr, double *sums, DevStatus *st, int cta, uint32_t sig) {
   constexpr bool RESID = EPI == EPI_RESID;
   constexpr int NKB = 2 * NH;  // K-blocks of 16 columns
-  if (status_failed(st)) return;
   const int lim = wait_bound(st, MAX_WAIT);
   extern __shared__ __align__(1024) uint8_t tq_smem[];
   uint8_t *Bs = tq_smem + OFF_B;
@@ -234,7 +229,7 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_begin = (int64_t)cta * rows_per_cta;
   const int64_t r_end = imin64(m, r_begin + rows_per_cta);
   const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + TQ_ROWS - 1) / TQ_ROWS) : 0;
   auto sub_rows = [&](int i, int q) -> int {
@@ -545,8 +540,13 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
           }
         }
       }
+      if (SIG && ok) {  // this warp's rows of tile i are stored
+        __syncwarp();
+        if (lane == 0) st_release_cluster_u32(sig + 4u * (uint32_t)f, (uint32_t)(i + 1));
+      }
     }
     if (!ok && lane == 0 && !*abort_flag) set_abort(abort_flag, st);
+    if (SIG && !ok && lane == 0) st_release_cluster_u32(sig + 4u * (uint32_t)f, PRODUCER_DONE);
     if (RESID) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -563,6 +563,16 @@ __global__ void __launch_bounds__(TQ_THREADS, 1)
   __syncthreads();
   fence_after_sync();
   if (warp == W_MMA) tmem_free(tmem, TQ_TMEM_COLS);
+}
+
+template <bool FULLN, bool REV, int EPI, int NH, int NDA>
+__global__ void __launch_bounds__(TQ_THREADS, 1)
+    k_trsm_oz(const double *__restrict__ X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int nk, int nn,
+              const double *__restrict__ Bp, int b_ld, int64_t rows_per_cta, int load_mode, bool vec_store,
+              const double *Vref, int64_t ldvr, double *sums, DevStatus *st) {
+  if (status_failed(st)) return;
+  trsm_oz_cta<FULLN, REV, EPI, NH, NDA, false>(X, ldx, Y, ldy, m, nk, nn, Bp, b_ld, rows_per_cta, load_mode, vec_store,
+                                               Vref, ldvr, sums, st, (int)blockIdx.x, 0u);
 }
 
 bool trsm_oz_supported(int64_t n) { return n >= 1 && n <= TQ_NP; }
@@ -624,6 +634,130 @@ cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_
 cudaError_t launch_trsm_oz_resid(const double *Q, int64_t ldq, const double *V, int64_t ldv, int64_t m, int64_t n,
                                  const double *Rpacked, double *sums, int num_sms, DevStatus *st, cudaStream_t s) {
   return launch_trsm_oz_t<false, EPI_RESID, 7>(Q, ldq, nullptr, 0, m, n, n, Rpacked, V, ldv, sums, num_sms, st, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// The first row pass of rand_cholQR in one launch (Algorithm 3: W = V R_s^{-1}, then the Gram
+// G = W^T W of the Cholesky pass, Algorithm 2 step 1), on pairs of CTAs of one cluster over one
+// row range each: the solver runs the solve above (full width, n = 64) and stores W; after each
+// 128-row tile its eight read-back warps publish their progress in the solver's shared memory,
+// and its partner runs the Gram of those rows (gram_split_body.cuh), each group once the tile
+// that holds it is stored, so W reaches the Gram from L2 a few tiles behind the solve instead
+// of from a second pass over HBM.  V is read once and W written once; G is accumulated as by
+// k_gram_split.  Each role is bound by its own instruction issue, not by HBM, and runs on half
+// the SMs, so the launch takes about as long as the two separate passes together or longer.
+namespace {
+constexpr size_t SG_BODY = TQ_SMEM > GsCfg<TQ_NP>::SMEM ? TQ_SMEM : GsCfg<TQ_NP>::SMEM;
+constexpr size_t SG_OFF_SIG = (SG_BODY + 15) / 16 * 16;
+constexpr size_t SG_SMEM = SG_OFF_SIG + 4 * PRODUCER_WARPS;
+static_assert(SG_SMEM <= 232448, "shared memory budget");
+static_assert(GS_THREADS <= TQ_THREADS && TQ_ROWS == TQ_PRODUCER_ROWS, "paired roles");
+// CTAs per cluster (SG_CL / 2 pairs) and the rank bit that tells the roles apart: rank r solves
+// when r & SG_ROLE is 0, and its Gram partner is rank r ^ SG_ROLE.  Clusters of four with the
+// solves on ranks 0, 1 and the Grams on ranks 2, 3: two SMs that share a TPC then run the same
+// role.  Measured at m = 2^23 (one launch): 4.93 ms so (36 clusters, 144 SMs); 7.65 ms with the
+// roles alternating (ranks 0, 2 solve), and 7.33 ms with clusters of two (76 clusters) -- an SM
+// slows down sharply when its TPC neighbour runs the other role's code.  Each role alone at the
+// same size: the solve 4.23 ms, the Gram 4.43 ms.
+constexpr int SG_CL = 4, SG_ROLE = 2;
+}  // namespace
+
+template <int NDA, int CL, int ROLE>
+__global__ void __launch_bounds__(TQ_THREADS, 1)
+    k_solve_gram(const double *__restrict__ V, int64_t ldv, double *W, int64_t m, const double *__restrict__ Bp,
+                 double *Gp, int64_t rows_per_pair, DevStatus *st) {
+  extern __shared__ __align__(1024) uint8_t sg_smem[];
+  const uint32_t rank = cluster_rank();
+  const bool solver = (rank & (uint32_t)ROLE) == 0;
+  // pair index: the cluster's pairs in order of the rank bits other than the role bit
+  const uint32_t in_cl = (rank & (uint32_t)(ROLE - 1)) | ((rank >> 1) & ~(uint32_t)(ROLE - 1));
+  const int pair = (int)((blockIdx.x / CL) * (CL / 2) + in_cl);
+  const bool skip = status_failed(st);
+  const uint32_t sig = smem_addr(sg_smem + SG_OFF_SIG);
+  if (solver && threadIdx.x < PRODUCER_WARPS)
+    ((volatile uint32_t *)(sg_smem + SG_OFF_SIG))[threadIdx.x] = skip ? PRODUCER_DONE : 0u;
+  __syncwarp();
+  cluster_sync_all();  // the progress words are set before the Gram CTAs read them
+  if (!skip) {
+    if (solver)
+      trsm_oz_cta<true, false, EPI_STORE, 2, NDA, true>(V, ldv, W, TQ_NP, m, TQ_NP, TQ_NP, Bp, 0, rows_per_pair,
+                                                       LOAD_ASYNC, true, nullptr, 0, nullptr, st, pair, sig);
+    else
+      gram_split_cta<TQ_NP, false, true>(W, TQ_NP, m, TQ_NP, Gp, rows_per_pair, GLOAD_ASYNC16, st, pair,
+                                         map_shared_rank(sig, rank ^ (uint32_t)ROLE));
+  }
+  __syncwarp();
+  cluster_sync_all();  // neither CTA leaves while the other may still read its shared memory
+}
+
+namespace {
+template <int NDA>
+cudaLaunchConfig_t solve_gram_config(cudaLaunchAttribute *attr, unsigned ctas, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(TQ_THREADS);
+  cfg.dynamicSmemBytes = SG_SMEM;
+  cfg.stream = s;
+  attr->id = cudaLaunchAttributeClusterDimension;
+  attr->val.clusterDim.x = SG_CL;
+  attr->val.clusterDim.y = 1;
+  attr->val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Solve/Gram pairs of the paired kernel that fit on the device at once (0 when none does), per
+// device: the clusters that fit times the pairs of a cluster.
+template <int NDA>
+int solve_gram_pairs(int num_sms, cudaStream_t s) {
+  constexpr int MAX_DEV = 64;
+  static int cached[MAX_DEV];  // 0: not asked yet; -1: none fits; else the count
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return 0;
+  if (cached[dev] == 0) {
+    int clusters = 0;
+    cudaLaunchAttribute attr;
+    const cudaLaunchConfig_t cfg = solve_gram_config<NDA>(&attr, (unsigned)(SG_CL * (num_sms / SG_CL)), s);
+    if (cudaFuncSetAttribute(k_solve_gram<NDA, SG_CL, SG_ROLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&clusters, k_solve_gram<NDA, SG_CL, SG_ROLE>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;  // not cached: asked again next time
+    }
+    cached[dev] = clusters > 0 ? clusters * (SG_CL / 2) : -1;
+  }
+  return cached[dev] > 0 ? cached[dev] : 0;
+}
+
+template <int NDA>
+cudaError_t launch_solve_gram_t(const double *V, int64_t ldv, double *W, int64_t m, const double *Bpacked,
+                                double *Gpacked, int num_sms, DevStatus *st, cudaStream_t s) {
+  const int max_pairs = solve_gram_pairs<NDA>(num_sms, s);
+  if (max_pairs <= 0) return cudaErrorInvalidConfiguration;
+  int64_t pairs = std::min<int64_t>(ceil_div(m, TQ_ROWS), (int64_t)max_pairs);
+  const int64_t rows_per_pair = ceil_div(ceil_div(m, pairs), TQ_ROWS) * TQ_ROWS;
+  pairs = ceil_div(ceil_div(m, rows_per_pair), SG_CL / 2) * (SG_CL / 2);  // whole clusters (a pair past m idles)
+  cudaError_t e = cudaFuncSetAttribute(k_solve_gram<NDA, SG_CL, SG_ROLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr;
+  const cudaLaunchConfig_t cfg = solve_gram_config<NDA>(&attr, (unsigned)(2 * pairs), s);
+  return cudaLaunchKernelEx(&cfg, k_solve_gram<NDA, SG_CL, SG_ROLE>, V, ldv, W, m, Bpacked, Gpacked, rows_per_pair, st);
+}
+}  // namespace
+
+bool solve_gram_supported(int64_t n, const double *V, int64_t ldv, const double *W, int64_t ldw, int num_sms) {
+  return n == TQ_NP && ldv == TQ_NP && ldw == TQ_NP && ((uintptr_t)V & 15) == 0 && ((uintptr_t)W & 15) == 0 &&
+         solve_gram_pairs<7>(num_sms, nullptr) > 0;
+}
+
+cudaError_t launch_solve_gram(const double *V, int64_t ldv, double *W, int64_t ldw, int64_t m, int64_t n,
+                              const double *Bpacked, double *Gpacked, int num_sms, DevStatus *st, cudaStream_t s,
+                              int digits) {
+  if (m <= 0) return cudaSuccess;
+  if (!solve_gram_supported(n, V, ldv, W, ldw, num_sms)) return cudaErrorInvalidValue;
+  return digits == 6 ? launch_solve_gram_t<6>(V, ldv, W, m, Bpacked, Gpacked, num_sms, st, s)
+                     : launch_solve_gram_t<7>(V, ldv, W, m, Bpacked, Gpacked, num_sms, st, s);
 }
 
 }  // namespace rq

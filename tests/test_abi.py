@@ -50,7 +50,7 @@ def test_binding_names_match_abi():
         if name in ("randqr_create", "randqr_destroy", "randqr_status_string",
                     "randqr_last_cuda_error", "randqr_get_status", "randqr_workspace_bytes",
                     "randqr_set_profiling", "randqr_get_kernel_times", "randqr_kernel_name",
-                        "randqr_set_tensor_cores", "randqr_set_sketch_kind"):
+                        "randqr_set_tensor_cores", "randqr_set_sketch_kind", "randqr_set_fused_first_pass"):
             continue  # wrapped by rq.Context / rq.get_status
         assert hasattr(rq, name), name
 
