@@ -132,9 +132,11 @@ randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls);
  * and even n <= 128 blocked at n - 64): both solves of rand_cholQR (Algorithm 3; R_s^{-1} is
  * applied to V so that its truncation error is a row-wise backward error in V, and kappa(R_c) =
  * O(1) by the sketch's embedding property; for n > 64 the first solve's off-diagonal block goes
- * by substitution order, T = V2 - W1 R12, W2 = T R22^{-1}) and the last pass of CholeskyQR2 and
- * of shifted CholeskyQR3.  Their earlier passes, whose R may be ill-conditioned, use
- * substitution.  The sketch GEMM Ws = S2 W1 is a split product too for n <= 128.  enable = 0
+ * by substitution order, T = V2 - W1 R12, W2 = T R22^{-1}) and every pass of CholeskyQR2 and
+ * of shifted CholeskyQR3 (their R is within the methods' own condition limit, kappa(R) below
+ * about u^{-1/2}, where the computed inverse's right perturbation, of order n u kappa(R), stays
+ * below the loss of orthogonality that pass has anyway, of order u kappa(R)^2, and the next pass
+ * removes both).  The sketch GEMM Ws = S2 W1 is a split product too for n <= 128.  enable = 0
  * selects the CUDA-core kernels of the chosen precision everywhere. */
 randqr_status randqr_set_tensor_cores(randqr_ctx *ctx, int enable);
 
