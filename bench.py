@@ -57,10 +57,12 @@ def roofline_model(kind, n):
 # DRAM bytes per row of V (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at
 # m = 2^20, n = 64 with --set full, divided by m), scaled to a launch by the rows it processes.
 # Valid for n = 64 and the kernels as captured (the capture of commit b7e56f9: k_trsm_oz's
-# full-width instance, the mean of its two launches, and k_gram_split<64>); a kernel changed
-# since its capture has no entry (its traffic is reported as null until it is captured again).
+# full-width instance, the mean of its two launches, and k_gram_split<64>; of commit adeb14f:
+# k_solve_gram, the mean of two launches); a kernel changed since its capture has no entry (its
+# traffic is reported as null until it is captured again).
 MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (543.559e6 + 486.409e6) / 1048576,
-                                   "gram_tc": (537.007e6 + 3.075e6) / 1048576}
+                                   "gram_tc": (537.007e6 + 3.075e6) / 1048576,
+                                   "solve_gram": (537.512e6 + 492.633e6) / 1048576}
 
 
 def kernel_roofline(kind, avg_ms, m, n):
