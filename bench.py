@@ -65,6 +65,13 @@ MEASURED_DRAM_BYTES_PER_ROW_N64 = {"trsm_tc": (543.559e6 + 486.409e6) / 1048576,
                                    "solve_gram": (537.512e6 + 492.633e6) / 1048576}
 
 
+# The unit a kernel kind's roofline is taken over, and how many of them one factorization runs:
+# a solve is one launch for n <= 64 and three or four block products above, the Gram one launch
+# or two (the first 64 columns, then the rest against all).
+UNIT_NAME = {"trsm_tc": "solve", "gram_tc": "Gram"}
+UNITS_PER_STEP = {"trsm_tc": 2, "gram_tc": 1, "solve_gram": 1, "cs_scatter": 1}
+
+
 def kernel_roofline(kind, avg_ms, m, n):
     model = roofline_model(kind, n)
     if model is None:
@@ -86,7 +93,7 @@ def kernel_roofline(kind, avg_ms, m, n):
             "traffic_source": ("ncu dram bytes per row at m=2^20, n=64, scaled by m" if traffic else
                                "not captured since the kernel last changed"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-            "algorithmic": f"{per_row} bytes per row x {m} rows per launch"}
+            "algorithmic": f"{per_row} bytes per row x {m} rows per {UNIT_NAME.get(kind, 'launch')}"}
 
 def parse():
     p = argparse.ArgumentParser()
@@ -699,7 +706,8 @@ def main():
 
     # dominant kernel and its roofline
     kind, (tot_ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
-    roof = kernel_roofline(kind, tot_ms / launches, m, n)
+    units = UNITS_PER_STEP.get(kind, launches / a.steps) * a.steps
+    roof = kernel_roofline(kind, tot_ms / units, m, n)
     roof["kernel_share"] = tot_ms / (ms * a.steps)
 
     line = {"metric": "rand_cholQR effective HBM GB/s (m x n FP64)", "value": value,

@@ -444,7 +444,6 @@ __device__ __forceinline__ void trsm_oz_cta(const double *__restrict__ X, int64_
             for (int hr = 0; hr < 2; ++hr) er[rg][hr] = rowexp[(i % 3) * TQ_ROWS + 32 * quad + 16 * rg + 8 * hr + tr];
 #pragma unroll 1
         for (int rg = 0; rg < 2; ++rg) {  // 16-row group
-          uint32_t v[2][8][4];
           const uint32_t ta = tmem + ((uint32_t)(32 * quad + 16 * rg) << 16) + (uint32_t)(256 * h + 16 * cq);
           // EPI_ADDREF: this group's reference pairs are requested before the tensor-memory loads,
           // so their latency overlaps the read-back (pairs that are not whole are read below)
@@ -461,36 +460,44 @@ __device__ __forceinline__ void trsm_oz_cta(const double *__restrict__ X, int64_
                 rvh[cc][hr] = whole ? *(const double2 *)(Vref + grow * ldvr + col) : make_double2(0.0, 0.0);
               }
           }
+          // NCC of the two 8-column chunks per tensor-memory wait: both (more loads in flight), or
+          // one at a time where the add-to-reference epilogue's live values would not fit the
+          // registers otherwise
+          constexpr int NCC = EPI == EPI_ADDREF ? 1 : 2;
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc)
+          for (int c2 = 0; c2 < 2 / NCC; ++c2) {
+          uint32_t v[NCC][8][4];
+#pragma unroll
+          for (int li = 0; li < NCC; ++li)
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
               if (g < NDA + 1) {
-                tmem_ld16x256(ta + (uint32_t)(32 * g + 8 * cc), v[cc][g]);
+                tmem_ld16x256(ta + (uint32_t)(32 * g + 8 * (c2 * NCC + li)), v[li][g]);
               } else {  // 48-bit products: region 7 holds nothing
-                v[cc][g][0] = v[cc][g][1] = v[cc][g][2] = v[cc][g][3] = 0u;
+                v[li][g][0] = v[li][g][1] = v[li][g][2] = v[li][g][3] = 0u;
               }
             }
           tmem_wait_ld();
-          tmem_regs_ready(v[0]);
-          tmem_regs_ready(v[1]);
-          if (rg == 1) {  // this half read: the next tile's MMAs of the half may start
+#pragma unroll
+          for (int li = 0; li < NCC; ++li) tmem_regs_ready(v[li]);
+          if (rg == 1 && c2 == 2 / NCC - 1) {  // this half read: the next tile's MMAs of the half may start
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(BAR_TEMPTY + h));
           }
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
+          for (int li = 0; li < NCC; ++li) {
+            const int cc = c2 * NCC + li;
             const int k0 = 32 * h + 16 * cq + 8 * cc + tc2;
             const int e0 = scale_exp(colexp[k0]) - 56, e1 = scale_exp(colexp[k0 + 1]) - 56;
 #pragma unroll
             for (int hr = 0; hr < 2; ++hr) {
               const int64_t grow = row0 + 16 * rg + 8 * hr + tr;
-              const long long t0 = recombine_b8(v[cc][0][2 * hr], v[cc][1][2 * hr], v[cc][2][2 * hr], v[cc][3][2 * hr],
-                                                v[cc][4][2 * hr], v[cc][5][2 * hr], v[cc][6][2 * hr], v[cc][7][2 * hr]);
-              const long long t1 = recombine_b8(v[cc][0][2 * hr + 1], v[cc][1][2 * hr + 1], v[cc][2][2 * hr + 1],
-                                                v[cc][3][2 * hr + 1], v[cc][4][2 * hr + 1], v[cc][5][2 * hr + 1],
-                                                v[cc][6][2 * hr + 1], v[cc][7][2 * hr + 1]);
+              const long long t0 = recombine_b8(v[li][0][2 * hr], v[li][1][2 * hr], v[li][2][2 * hr], v[li][3][2 * hr],
+                                                v[li][4][2 * hr], v[li][5][2 * hr], v[li][6][2 * hr], v[li][7][2 * hr]);
+              const long long t1 = recombine_b8(v[li][0][2 * hr + 1], v[li][1][2 * hr + 1], v[li][2][2 * hr + 1],
+                                                v[li][3][2 * hr + 1], v[li][4][2 * hr + 1], v[li][5][2 * hr + 1],
+                                                v[li][6][2 * hr + 1], v[li][7][2 * hr + 1]);
               // T / 2^12 (|.| < 2^63) times 2^(E_i + F_k - 56)
               const double y0 = int_times_pow2_cvt(t0, er[rg][hr] + e0);
               const double y1 = int_times_pow2_cvt(t1, er[rg][hr] + e1);
@@ -538,6 +545,7 @@ __device__ __forceinline__ void trsm_oz_cta(const double *__restrict__ X, int64_
               }
             }
           }
+          }  // c2
         }
       }
       if (SIG && ok) {  // this warp's rows of tile i are stored
