@@ -207,3 +207,50 @@ def test_corrupted_descriptors_are_refused_while_others_run(rq):
         assert st == 0
     ctx.close()
     del keep
+
+
+def test_slow_producer(rq):
+    """A producer that submits with gaps (the server drains to empty at one point and new work
+    arrives after it) and stalls for half a second mid-stream: every request completes once,
+    with the direct call's accuracy, and the server's counters come back to nothing queued,
+    running or in flight."""
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=4)
+    rng = np.random.default_rng(7)
+    shapes = [(int(rng.integers(5000, 60000)), int(rng.choice([4, 8, 16, 32, 64])), 10.0 ** rng.uniform(0, 12))
+              for _ in range(24)]
+    pending, finished, keep = set(), {}, {}
+
+    def poll_all():
+        for t in list(pending):
+            st, _ = rq.randqr_poll(ctx, t)
+            if st != rq.PENDING:
+                finished[t] = st
+                pending.discard(t)
+
+    for i, (m, n, kappa) in enumerate(shapes):
+        t, k = rq.randqr_submit(ctx, _V(m, n, kappa, seed=100 + i))
+        pending.add(t)
+        keep[t] = k
+        if i == 6:  # let the server run dry before the next arrival
+            t0 = time.time()
+            while pending:
+                poll_all()
+                assert time.time() - t0 < 60.0
+            s = rq.randqr_serve_stats_get(ctx)
+            assert s["queued"] == 0 and s["running"] == 0 and s["bytes_in_flight"] == 0, s
+        time.sleep(0.5 if i == 12 else float(rng.uniform(0.0, 0.02)))
+        poll_all()
+    t0 = time.time()
+    while pending:
+        poll_all()
+        assert time.time() - t0 < 120.0, "requests did not finish"
+    assert len(finished) == len(shapes) and all(st == 0 for st in finished.values()), finished
+    s = rq.randqr_serve_stats_get(ctx)
+    assert s["submitted"] == s["completed"] == len(shapes), s
+    assert s["queued"] == 0 and s["running"] == 0 and s["bytes_in_flight"] == 0, s
+    for t, (V, Q, R) in keep.items():
+        Vh, Qh, Rh = V.cpu().numpy(), Q.cpu().numpy(), R.cpu().numpy()
+        assert oracle.orth_err(Qh)[0] <= 1e-12
+        assert oracle.resid(Vh, Qh, Rh) <= 1e-13
+    ctx.close()
