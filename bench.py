@@ -200,6 +200,25 @@ def cpu_baseline(n, kappa, rows, s1, s2):
                       f"same s1/s2), single-threaded FP64 C oracle, {dt:.1f} s"}
 
 
+def fp64_dgemm_tflops(torch, dev, size=8192, reps=3):
+    """Context for the FP64 roof: cuBLAS DGEMM (torch.matmul on FP64, size^3), TFLOP/s by CUDA
+    events over `reps` products after one warm-up."""
+    a = torch.randn((size, size), dtype=torch.float64, device=dev)
+    b = torch.randn((size, size), dtype=torch.float64, device=dev)
+    c = a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        c = a @ b
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * size ** 3 / (ms / 1e3) / 1e12
+
+
 def cpu_baseline_small():
     """The oracle on the small-matrix configuration (m = 20000, n = 16, kappa = 1e10,
     s1 = 544, s2 = 64): microseconds per call, single thread, the mean of 5 calls."""
@@ -917,6 +936,8 @@ def main():
                 for pr in (rq.FP64, rq.F32X2):
                     line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
                                                               steps=1))
+        if world == 1:
+            line["fp64_dgemm_tflops"] = fp64_dgemm_tflops(torch, dev)
         if not a.no_serve:
             del Q
             torch.cuda.empty_cache()
