@@ -120,8 +120,12 @@ size_t randqr_workspace_bytes(const randqr_ctx *ctx);
  * Householder flags: seconds) is far above any legitimate wait.  polls >= 0 replaces it for
  * this context's later launches (0: a wait gives up without polling, so any launch that has
  * to wait at all fails with RANDQR_ERR_TIMEOUT -- a way to exercise the failure path on a
- * healthy GPU); polls < 0 restores the default.  With ctx == NULL the bound applies to
- * randqr_sketch_static instead (process-wide; set it while no such call is in flight). */
+ * healthy GPU); polls < 0 restores the default.  The bound, like the tensor-core and
+ * fused-pass switches, also holds for the context's served requests (from their next launch)
+ * and batched calls (a change drops the captured batch plans).  With ctx == NULL the bound
+ * applies to randqr_sketch_static instead (process-wide; set it while no such call is in
+ * flight).  Also: the Gram CTAs of the fused first pass (randqr_set_fused_first_pass) wait on
+ * their solver's progress words under the same bound. */
 randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls);
 
 /* Gram products on the tensor cores (default on): for n <= 128 the Gram G = W^T W of the

@@ -578,7 +578,9 @@ randqr_status randqr_set_wait_limit(randqr_ctx *ctx, int32_t polls) {
     rq_static_set_wait_limit(polls);
     return RANDQR_OK;
   }
-  ctx->wait_limit = polls < 0 ? -1 : std::min<int32_t>(polls, (1 << 30) - 1);
+  const int32_t limit = polls < 0 ? -1 : std::min<int32_t>(polls, (1 << 30) - 1);
+  if (limit != ctx->wait_limit && ctx->batcher) rq_batcher_destroy(ctx);  // graphs hold the old bound
+  ctx->wait_limit = limit;
   return RANDQR_OK;
 }
 

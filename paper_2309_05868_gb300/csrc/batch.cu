@@ -150,7 +150,7 @@ randqr_status build_plan(randqr_ctx *ctx, randqr_batcher *b, const randqr_batch_
       destroy_plan(p);
       return RANDQR_ERR_CUDA;
     }
-    c->use_tc = ctx->use_tc;
+    rq_inherit_settings(c, ctx);
     p->streams.push_back(s);
     p->subs.push_back(c);
   }

@@ -144,6 +144,13 @@ struct randqr_ctx {
   struct randqr_batcher *batcher = nullptr;
 };
 
+// The settings a context passes on to the contexts it runs work on (server slots, batch lanes).
+inline void rq_inherit_settings(randqr_ctx *sub, const randqr_ctx *ctx) {
+  sub->use_tc = ctx->use_tc;
+  sub->fuse_first_pass = ctx->fuse_first_pass;
+  sub->wait_limit = ctx->wait_limit;
+}
+
 // Tear down a context's request server (waits for its streams).
 void rq_server_destroy(randqr_ctx *ctx);
 // Wait bound of randqr_sketch_static's kernels (randqr_set_wait_limit with no context).

@@ -156,14 +156,14 @@ randqr_status start(randqr_ctx *ctx, randqr_server *sv, uint64_t t, int i) {
     int prec = r.prec;
     if (prec == RANDQR_FP64 && r.max_orth_err >= 1e-12) prec = RANDQR_F32X2;
     q.used_prec = prec;
-    sl.sub->use_tc = ctx->use_tc;
+    rq_inherit_settings(sl.sub, ctx);
     st = randqr_factor(sl.sub, r.V, r.m, r.n, r.ldv, s1, s2, r.seed, S2, (randqr_precision)prec,
                        r.Q, r.ldq, r.R, r.ldr, nullptr, sl.stream);
   } else if (r.algo == RANDQR_ALGO_CHOLQR2) {
-    sl.sub->use_tc = ctx->use_tc;
+    rq_inherit_settings(sl.sub, ctx);
     st = randqr_cholqr2(sl.sub, r.V, r.m, r.n, r.ldv, r.Q, r.ldq, r.R, r.ldr, nullptr, sl.stream);
   } else {
-    sl.sub->use_tc = ctx->use_tc;
+    rq_inherit_settings(sl.sub, ctx);
     st = randqr_shifted_cholqr3(sl.sub, r.V, r.m, r.n, r.ldv, r.Q, r.ldq, r.R, r.ldr, nullptr,
                                 sl.stream);
   }
