@@ -254,3 +254,23 @@ def test_slow_producer(rq):
         assert oracle.orth_err(Qh)[0] <= 1e-12
         assert oracle.resid(Vh, Qh, Rh) <= 1e-13
     ctx.close()
+
+
+def test_served_requests_take_the_wait_bound(rq):
+    """The server's slot contexts run under the serving context's wait bound: with 0 polls a
+    served request gives up at its first wait and retires with RANDQR_ERR_TIMEOUT; with the
+    default restored the next request on the same server completes."""
+    ctx = rq.Context(0)
+    rq.randqr_serve_config(ctx, slots=2)
+    V = _V(30000, 64, 1e6, seed=5)
+    ctx.set_wait_limit(0)
+    t, _ = rq.randqr_submit(ctx, V)
+    st, _ = rq.randqr_wait(ctx, t)
+    assert st == -7, st
+    ctx.set_wait_limit(-1)
+    t, (Vk, Q, R) = rq.randqr_submit(ctx, V)
+    st, _ = rq.randqr_wait(ctx, t)
+    assert st == 0, st
+    Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+    assert oracle.orth_err(Qh)[0] <= 1e-12 and oracle.resid(V.cpu().numpy(), Qh, Rh) <= 1e-13
+    ctx.close()
