@@ -662,11 +662,11 @@ static_assert(SG_SMEM <= 232448, "shared memory budget");
 static_assert(GS_THREADS <= TQ_THREADS && TQ_ROWS == TQ_PRODUCER_ROWS, "paired roles");
 // CTAs per cluster (SG_CL / 2 pairs) and the rank bit that tells the roles apart: rank r solves
 // when r & SG_ROLE is 0, and its Gram partner is rank r ^ SG_ROLE.  Clusters of four with the
-// solves on ranks 0, 1 and the Grams on ranks 2, 3: two SMs that share a TPC then run the same
-// role.  Measured at m = 2^23 (one launch): 4.93 ms so (36 clusters, 144 SMs); 7.65 ms with the
-// roles alternating (ranks 0, 2 solve), and 7.33 ms with clusters of two (76 clusters) -- an SM
-// slows down sharply when its TPC neighbour runs the other role's code.  Each role alone at the
-// same size: the solve 4.23 ms, the Gram 4.43 ms.
+// solves on ranks 0, 1 and the Grams on ranks 2, 3, so that two SMs sharing a TPC run the same
+// role.  One launch at m = 2^23, n = 64: 4.93 ms this way (36 clusters, 144 SMs); 7.65 ms with
+// the roles alternating (ranks 0, 2 solve) and 7.33 ms with clusters of two (76 clusters) --
+// an SM slows down sharply when its TPC neighbour runs the other role's code.  Each role alone
+// at the same size (its partner idle): the solve 4.23 ms, the Gram 4.43 ms.
 constexpr int SG_CL = 4, SG_ROLE = 2;
 }  // namespace
 
