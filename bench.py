@@ -937,7 +937,11 @@ def main():
                     line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
                                                               steps=1))
         if world == 1:
-            line["fp64_dgemm_tflops"] = fp64_dgemm_tflops(torch, dev)
+            try:  # context only: a failure here must not cost the line
+                line["fp64_dgemm_tflops"] = fp64_dgemm_tflops(torch, dev)
+            except Exception as e:  # noqa: BLE001
+                line["fp64_dgemm_tflops"] = None
+                line["fp64_dgemm_error"] = str(e)[:200]
         if not a.no_serve:
             del Q
             torch.cuda.empty_cache()
