@@ -290,3 +290,52 @@ def test_sketch_split_gemm_at_the_digit_extremes():
     C = split_gemm(A, B)
     exact = 64 * Fraction(x0) * Fraction(x0)
     assert abs(Fraction(float(C[0, 0])) - exact) <= Fraction(2) ** -52 * exact
+
+
+# ---- the add-to-reference epilogue of the blocked solves (T = V2 - W1 R12 formed as one sum) --
+def add_to_reference(ref, t, u0):
+    """ref + t 2^u0 as the blocked solves form it: one integer sum at the unit 2^u1, u1 = u0 or
+    coarser so that ref (truncated to that unit) needs at most 61 bits, then one rounding to
+    FP64 (nearest, as an int64 -> FP64 conversion rounds).  Returns (value, u1, integer sum)."""
+    import struct
+    b = struct.unpack("<Q", struct.pack("<d", ref))[0]
+    ef = (b >> 52) & 0x7FF
+    u1 = max(u0, ef - 1023 - 60)
+    ts = t >> min(u1 - u0, 63)  # floor, as an arithmetic shift
+    sh = ef - 1075 - u1
+    mant = (b & ((1 << 52) - 1)) | (1 << 52)
+    rf = 0 if ef == 0 else (mant << sh if sh >= 0 else (mant >> -sh if -sh < 63 else 0))
+    rf = -rf if b >> 63 else rf
+    total = ts + rf
+    return float(np.ldexp(float(total), u1)), u1, total
+
+
+def test_add_to_reference_is_one_rounding_of_the_exact_sum():
+    """Against the exact rational ref + t 2^u0, over references from 2^-300 to 2^300 (and zeros,
+    subnormals, both signs) and products of up to 62 bits at units that make either term
+    dominate: the integer sum fits 63 bits, and the result is within two units 2^u1 (the two
+    truncations) plus half an ulp (the one rounding) of the exact sum, a subnormal reference
+    counting as zero -- for a dominant reference 2^u1 is 2^-60 of its binade, so the reference
+    moves by at most 2^-58 of its magnitude."""
+    rng = np.random.default_rng(3)
+    for _ in range(4000):
+        kind = rng.integers(0, 6)
+        if kind == 0:
+            ref = 0.0
+        elif kind == 1:
+            ref = float(rng.choice([-1.0, 1.0]) * np.ldexp(float(rng.uniform(1, 2)), -1040))  # subnormal
+        else:
+            ref = float(rng.choice([-1.0, 1.0]) * np.ldexp(float(rng.uniform(1, 2)), int(rng.integers(-300, 300))))
+        bits = int(rng.integers(0, 63))
+        t = int(rng.integers(-(1 << bits), 1 << bits)) if bits else 0
+        e_ref = int(np.frexp(ref)[1]) if ref else 0
+        u0 = e_ref - int(rng.integers(0, 130))  # the product from far below to far above ref
+        val, u1, total = add_to_reference(ref, t, u0)
+        assert abs(total) < (1 << 63)
+        exact = Fraction(ref) + Fraction(t) * Fraction(2) ** u0
+        err = abs(Fraction(val) - exact)
+        ulp = Fraction(2) ** (int(np.frexp(val)[1]) - 53) if val else Fraction(0)
+        # a subnormal reference counts as zero: at most 2^-1022 more
+        assert err <= 2 * Fraction(2) ** u1 + ulp / 2 + Fraction(2) ** -1022, (ref, t, u0)
+        if abs(ref) >= 2.0 ** -1022 and u1 > u0:  # a dominant (normal) reference, relative to itself
+            assert 2 * Fraction(2) ** u1 <= Fraction(abs(ref)) * Fraction(2) ** -58
