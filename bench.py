@@ -72,6 +72,17 @@ UNIT_NAME = {"trsm_tc": "solve", "gram_tc": "Gram"}
 UNITS_PER_STEP = {"trsm_tc": 2, "gram_tc": 1, "solve_gram": 1, "cs_scatter": 1}
 
 
+def dominant_roofline(kt, ms_per_step, steps, m, n):
+    """The roofline object of the kernel kind with the most device time over `steps` steps
+    (kt: {kind: (total ms, launches)}), taken per unit of UNITS_PER_STEP (a solve, a Gram) or
+    per launch, with its share of the step."""
+    kind, (tot_ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
+    units = UNITS_PER_STEP.get(kind, launches / steps) * steps
+    roof = kernel_roofline(kind, tot_ms / units, m, n)
+    roof["kernel_share"] = tot_ms / (ms_per_step * steps)
+    return roof
+
+
 def kernel_roofline(kind, avg_ms, m, n):
     model = roofline_model(kind, n)
     if model is None:
@@ -723,11 +734,7 @@ def main():
     algo_bytes = 32.0 * m * n
     value = algo_bytes * world / (ms / 1e3) / 1e9
 
-    # dominant kernel and its roofline
-    kind, (tot_ms, launches) = max(kt.items(), key=lambda kv: kv[1][0])
-    units = UNITS_PER_STEP.get(kind, launches / a.steps) * a.steps
-    roof = kernel_roofline(kind, tot_ms / units, m, n)
-    roof["kernel_share"] = tot_ms / (ms * a.steps)
+    roof = dominant_roofline(kt, ms, a.steps, m, n)
 
     line = {"metric": "rand_cholQR effective HBM GB/s (m x n FP64)", "value": value,
             "unit": "GB/s", "n_gpus": world, "steps": a.steps, "warmup": max(a.warmup, 3),

@@ -62,3 +62,21 @@ def test_workload_names_carry_the_sketch_sizes():
     assert bench.workload_name(a) == "rand_cholQR m=8388608 n=64 kappa=1e+12 s1=8320 s2=256"
     a.s1, a.s2 = 34279, 776
     assert bench.workload_name(a).endswith("s1=34279 s2=776")
+
+
+def test_dominant_roofline_is_taken_per_solve():
+    # n = 128: a solve is four block launches, so the solve's roofline divides its bytes by the
+    # time of a whole solve, not of one launch (per launch it would read above the copy peak)
+    import bench
+    if not os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        pytest.skip("no measured peaks on this machine")
+    m, n, steps = 1 << 23, 128, 5
+    kt = {"trsm_tc": (20.0 * steps, 8 * steps), "gram_tc": (6.5 * steps, 2 * steps),
+          "cs_scatter": (2.0 * steps, steps)}
+    r = bench.dominant_roofline(kt, 30.0, steps, m, n)
+    assert r["kernel"] == "trsm_tc"
+    assert abs(r["achieved"] - 16 * n * m / 10.0e-3 / 1e9) < 1e-6  # two solves of 10 ms each
+    assert abs(r["kernel_share"] - 20.0 / 30.0) < 1e-12
+    # a kind without a unit is taken per launch
+    r = bench.dominant_roofline({"hhqr": (3.0 * steps, steps)}, 30.0, steps, m, n)
+    assert r["kernel"] == "hhqr" and r["achieved"] is None
