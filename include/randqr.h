@@ -58,14 +58,15 @@ typedef enum {
 
 /* Arithmetic of rand_cholQR's two triangular solves (and, with the tensor cores off, of its Gram).
  * With the tensor cores on (the default) and n <= 64 the solves are split products: RANDQR_FP64
- * keeps seven byte digits of every row (products to 2^-56 of the row and column scales, FP64's
- * accuracy), RANDQR_F32X2 six (2^-48, fewer products and digits: the faster mixed-precision form);
+ * keeps seven byte digits of every row (each term within 2^-54 of the product of its row and
+ * column scales, FP64's accuracy), RANDQR_F32X2 six (2^-46 per term, about an FP32 pair's
+ * accuracy, with fewer products and digits: the faster mixed-precision form);
  * for 64 < n <= 128 (even n) both take the seven-digit blocked products.  With the tensor cores
  * off, RANDQR_F32X2 selects the pair-arithmetic kernels.  Householder QR, Cholesky and
  * R = R_c R_s are FP64 in every case, and the Gram keeps its full split format. */
 typedef enum {
   RANDQR_FP64 = 0,   /* FP64 accuracy throughout */
-  RANDQR_F32X2 = 1   /* ~48-bit row passes: six-digit split products on the tensor cores, or
+  RANDQR_F32X2 = 1   /* ~46-bit row passes: six-digit split products on the tensor cores, or
                         double-float (pairs of FP32) on the FP32 pipes with the tensor cores off */
 } randqr_precision;
 

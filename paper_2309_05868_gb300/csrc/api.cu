@@ -777,7 +777,7 @@ static randqr_status factor_impl(randqr_ctx *ctx, const double *V, int64_t m, in
   }
   if (second_pass && use_tc_solve(ctx, n)) {
     // Both solves as tensor-core products with explicit inverses: W = V (R_s^{-1}) into Q, then
-    // the Cholesky pass on W in place.  RANDQR_F32X2 keeps six digits of the rows (48-bit
+    // the Cholesky pass on W in place.  RANDQR_F32X2 keeps six digits of the rows (46-bit
     // products, its stated precision) instead of seven.
     const int dg = prec == RANDQR_F32X2 ? 6 : 7;
     RQ_CUDA(timed(ctx, s, rq::K_TRI_INV, [&] { return rq::launch_tri_inv(w.Rs, n, w.Rt2, ctx->status_dev, s); }));

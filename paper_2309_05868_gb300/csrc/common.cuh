@@ -276,7 +276,7 @@ cudaError_t launch_trsm_oz_block(const double *X, int64_t ldx, double *Y, int64_
 // Output packed upper of dimension 64; mode 3: sign * R12 dense, n1 x 64 row-major (ld 64).
 cudaError_t launch_block_prep(const double *Rp, int64_t n, int mode, double sign, double *Bout, const DevStatus *st,
                               cudaStream_t s);
-// digits: 7 (products to 2^-56 of the row x column scales, the FP64 path) or 6 (2^-48: RANDQR_F32X2)
+// digits: 7 (each term within 2^-54 of its row x column scales, the FP64 path) or 6 (2^-46: RANDQR_F32X2)
 cudaError_t launch_trsm_oz(const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t m, int64_t n,
                            const double *Bpacked, int num_sms, DevStatus *st, cudaStream_t s, int digits = 7);
 // Gram from exact split products on the tensor cores, n <= 64 (gram_split.cu)

@@ -106,7 +106,7 @@ __device__ __forceinline__ constexpr uint64_t b_off(int h, int c) { return (uint
 
 // One half's products for K-step C: A slice s times B slices 0 .. NR - 1 - s (at most 6) of block
 // (H, C), into regions s .. NR - 1 of that half, NR = NDA + 1 regions for NDA digits of A (7: the
-// pairs s + t <= 7; 6: s + t <= 6, a 48-bit product).  The first product of a half (C = 0, s = 0)
+// pairs s + t <= 7; 6: s + t <= 6, a 46-bit product).  The first product of a half (C = 0, s = 0)
 // covers every region (for NR = 8 with the zero eighth B slice) and overwrites them; every other
 // accumulates.
 template <int H, int C, int NDA>
@@ -142,7 +142,7 @@ __device__ __forceinline__ double add_fixed(double ref, long long t, int u0) {
 enum Epilogue { EPI_STORE = 0, EPI_ADDREF = 1, EPI_RESID = 2 };
 
 // NH: column halves of 32 (1 when nk, nn <= 32: only K-blocks 0, 1 and tensor-memory half 0 are
-// used).  NDA: digits of A (7, or 6 for the 48-bit products of RANDQR_F32X2).
+// used).  NDA: digits of A (7, or 6 for the 46-bit products of RANDQR_F32X2).
 // FULLN: nk == nn == 32 NH with 16-byte aligned rows of Y: no per-value column checks, and rows of a
 // partly filled sub-tile are cut whatever their slot holds (their products are never stored).
 // REV: X's columns are read as X J and Y's written as Y J (J the reversal of nk, nn columns).
@@ -473,7 +473,7 @@ __device__ __forceinline__ void trsm_oz_cta(const double *__restrict__ X, int64_
             for (int g = 0; g < 8; ++g) {
               if (g < NDA + 1) {
                 tmem_ld16x256(ta + (uint32_t)(32 * g + 8 * (c2 * NCC + li)), v[li][g]);
-              } else {  // 48-bit products: region 7 holds nothing
+              } else {  // six-digit products: region 7 holds nothing
                 v[li][g][0] = v[li][g][1] = v[li][g][2] = v[li][g][3] = 0u;
               }
             }

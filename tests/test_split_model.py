@@ -85,10 +85,12 @@ def recombine(D):
     return out
 
 
-def split_product(X, B):
+def split_product(X, B, nda=7):
     """Y = X B the way the solve kernel forms it: row scales of X, column scales of B, byte
     digits, slice pairs s + t <= 7 in eight regions per column half; half h (columns
-    32h .. 32h + 31) takes the K range j < 32 (h + 1) that an upper-triangular B reaches."""
+    32h .. 32h + 31) takes the K range j < 32 (h + 1) that an upper-triangular B reaches.
+    nda = 6 keeps only X's six leading digits and the pairs s + t <= 6 (seven regions, the
+    48-bit products of RANDQR_F32X2)."""
     m, n = X.shape
     assert B.shape == (n, n) and n <= 64
     Xp = np.zeros((m, 64)); Xp[:, :n] = X
@@ -102,9 +104,9 @@ def split_product(X, B):
         D = []
         for g in range(8):
             acc = np.zeros((m, 32), dtype=np.int64)
-            for s in range(7):
+            for s in range(nda):
                 t = g - s
-                if 0 <= t < 7:
+                if 0 <= t < 7 and g <= nda:  # the pairs s + t <= nda (nda + 1 regions)
                     acc += dx[s][:, jj] @ db[t][jj, kk]
             assert np.abs(acc).max() <= (2 ** 22 if g <= 4 else 2 ** 23 - 1)
             D.append(acc)
@@ -339,3 +341,26 @@ def test_add_to_reference_is_one_rounding_of_the_exact_sum():
         assert err <= 2 * Fraction(2) ** u1 + ulp / 2 + Fraction(2) ** -1022, (ref, t, u0)
         if abs(ref) >= 2.0 ** -1022 and u1 > u0:  # a dominant (normal) reference, relative to itself
             assert 2 * Fraction(2) ** u1 <= Fraction(abs(ref)) * Fraction(2) ** -58
+
+
+def test_six_digit_products_meet_the_pair_arithmetic_bound():
+    """RANDQR_F32X2's solves keep six of X's seven digits: each term then loses less than one
+    unit of the dropped digit, 2^(E - 46) of the row scale, so the product's error stays below
+    2^-42 of the scale product over 64 terms -- the accuracy of FP32-pair arithmetic -- while
+    seven digits stay below 2^-50."""
+    rng = synthetic.rng(5)
+    m, n = 24, 64
+    X = rng.standard_normal((m, n)) * np.exp(rng.uniform(-10, 10, (m, 1)))
+    B = np.triu(rng.standard_normal((n, n)) * np.exp(rng.uniform(-10, 10, (1, n))))
+    E, F = scale_exp(X, 1), scale_exp(B, 0)
+    worst = {}
+    for nda in (6, 7):
+        Y = split_product(X, B, nda=nda)
+        w = 0.0
+        for i in range(m):
+            for k in range(0, n, 5):
+                exact = sum(Fraction(float(X[i, j])) * Fraction(float(B[j, k])) for j in range(n))
+                w = max(w, float(abs(Fraction(float(Y[i, k])) - exact) / Fraction(2) ** int(E[i, 0] + F[0, k])))
+        worst[nda] = w
+    assert worst[7] <= 2.0 ** -50, worst
+    assert 2.0 ** -52 < worst[6] <= 2.0 ** -42, worst  # coarser than seven digits, within the bound
