@@ -90,7 +90,7 @@ def split_product(X, B, nda=7):
     digits, slice pairs s + t <= 7 in eight regions per column half; half h (columns
     32h .. 32h + 31) takes the K range j < 32 (h + 1) that an upper-triangular B reaches.
     nda = 6 keeps only X's six leading digits and the pairs s + t <= 6 (seven regions, the
-    48-bit products of RANDQR_F32X2)."""
+    46-bit products of RANDQR_F32X2)."""
     m, n = X.shape
     assert B.shape == (n, n) and n <= 64
     Xp = np.zeros((m, 64)); Xp[:, :n] = X
