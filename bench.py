@@ -751,214 +751,221 @@ def main():
             "kernels_ms_per_step": {k: v[0] / a.steps for k, v in kt.items()},
             "accuracy": acc}
 
-    if not a.no_extras and world == 1:
-        # the row-sharded decomposition as logical shards on this GPU (sums in shard order)
-        P = 4
-        cuts = sharded.even_cuts(m, P)
-        Qs = Q
+    # everything past the timed step is context: on one GPU a failure there must not cost
+    # the line (with several ranks it ends the run, since the ranks meet in collectives)
+    try:
+        if not a.no_extras and world == 1:
+            # the row-sharded decomposition as logical shards on this GPU (sums in shard order)
+            P = 4
+            cuts = sharded.even_cuts(m, P)
+            Qs = Q
 
-        def logical_step():
-            sharded.factor_logical_shards(V, cuts, s1, s2, seed=0, Q=Qs, stages=stages)
+            def logical_step():
+                sharded.factor_logical_shards(V, cuts, s1, s2, seed=0, Q=Qs, stages=stages)
 
-        for _ in range(3):
-            logical_step()
-        torch.cuda.synchronize()
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        for _ in range(3):
-            logical_step()
-        h1.record(stream)
-        torch.cuda.synchronize()
-        sh_ms = h0.elapsed_time(h1) / 3
-        st, info = rq.get_status(ctx)
-        line["sharded_logical"] = {"shards": P, "ms_per_step": sh_ms,
-                                   "value": algo_bytes / (sh_ms / 1e3) / 1e9, "unit": "GB/s",
-                                   "over_unsharded": sh_ms / ms, "status": st}
-
-    if not a.no_extras and world == 1:
-        # the paper's multisketch sizes (Sec. 6.2) on the same matrix: a larger sketch GEMM
-        p1, p2 = synthetic.paper_multisketch_sizes(n)
-        for _ in range(2):
-            rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
-        torch.cuda.synchronize()
-        ctx.kernel_times()
-        ctx.set_profiling(True)
-        p0, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(3):
-            rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
-        pe.record(stream)
-        torch.cuda.synchronize()
-        ctx.set_profiling(False)
-        pkt = ctx.kernel_times()
-        pms = p0.elapsed_time(pe) / 3
-        st, _ = rq.get_status(ctx)
-        line["paper_sketch_sizes"] = {"s1": p1, "s2": p2, "ms_per_step": pms, "status": st,
-                                      "value": algo_bytes / (pms / 1e3) / 1e9, "unit": "GB/s",
-                                      "kernels_ms_per_step": {k: v[0] / 3 for k, v in pkt.items()}}
-
-    if not a.no_extras:
-        if world == 1:
-            # the other precision of the row passes, on the same matrix
-            other = "f32x2" if a.prec == "fp64" else "fp64"
-            oprec = rq.F32X2 if other == "f32x2" else rq.FP64
-            oms, okt, _, oacc = measure(oprec, a.steps)
-            line["modes"] = {other: {"value": algo_bytes / (oms / 1e3) / 1e9, "unit": "GB/s",
-                                     "ms_per_step": oms, "accuracy": oacc,
-                                     "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
-            # the first row pass as one fused launch or as two (solve, then the Gram of W)
-            ctx.set_fused_first_pass(not a.fused)
-            tms, tkt, _, tacc = measure(prec, a.steps)
-            ctx.set_fused_first_pass(a.fused)
-            line["modes"]["two_pass" if a.fused else "fused_first_pass"] = {
-                "value": algo_bytes / (tms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": tms,
-                "accuracy": tacc, "kernels_ms_per_step": {k: v[0] / a.steps for k, v in tkt.items()}}
-
-        # end to end through the public API: pinned host V in, Q and R back to pinned host,
-        # every step.  On one GPU that is the host-buffer call randqr_factor_host (its own
-        # upload, factorization in the context's staging area, download); consecutive steps
-        # alternate between two contexts on two streams, so step i + 1's upload overlaps step
-        # i's factorization and download (the pipeline a caller streaming matrices through the
-        # GPU would use).  Row shards (N > 1) copy around the sharded device call the same way.
-        Vh = V.cpu().pin_memory()
-        ke = max(2, min(a.steps, 6))
-        if world == 1:
-            Qh = [torch.empty_like(Vh).pin_memory() for _ in range(2)]
-            Rh = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
-            hctx = [ctx, rq.Context(local_rank)]
-            hst = [torch.cuda.Stream(device=dev) for _ in range(2)]
-            done = [torch.cuda.Event() for _ in range(2)]
-
-            def e2e_step(i):
-                b = i % 2
-                rq.randqr_factor_host(Vh, s1, s2, seed=0, prec=prec, Q=Qh[b], R=Rh[b], ctx=hctx[b],
-                                      stream=hst[b], sync=False)
-                done[b].record(hst[b])
-
-            for i in range(2):  # staging areas, workspaces and sketches in place
-                e2e_step(i)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for b in range(2):
-                hst[b].wait_event(f0)
-            for i in range(ke):
-                e2e_step(i)
-            for b in range(2):
-                stream.wait_event(done[b])
-            f1.record(stream)
-            torch.cuda.synchronize()
-            for b in range(2):
-                st_b, _ = rq.get_status(hctx[b], hst[b])
-                if st_b != 0:
-                    raise SystemExit(f"randqr_factor_host failed with status {st_b}")
-            e2e_ms = f0.elapsed_time(f1) / ke
-            del Qh, hctx
-            pipeline = ("randqr_factor_host on pinned host buffers; consecutive steps on two "
-                        "contexts and streams, so uploads, factorizations and downloads overlap")
-        else:
-            Qh = torch.empty_like(Vh).pin_memory()
-            Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-            Vd = [torch.empty_like(V) for _ in range(2)]
-            Qd = [torch.empty_like(V) for _ in range(2)]
-            Rd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
-            s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-            ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
-
-            def e2e_step(i):
-                b = i % 2
-                with torch.cuda.stream(s_in):
-                    if i >= 2:
-                        s_in.wait_event(ev["comp"][b])  # step i - 2 has read Vd[b]
-                    Vd[b].copy_(Vh, non_blocking=True)
-                    ev["in"][b].record(s_in)
-                stream.wait_event(ev["in"][b])
-                if i >= 2:
-                    stream.wait_event(ev["out"][b])  # step i - 2's download has read Qd[b], Rd[b]
-                _, Rk = sharded.factor_row_sharded(Vd[b], rank * m, allreduce, s1, s2, seed=0, Q=Qd[b],
-                                                   stages=stages)
-                Rd[b].copy_(Rk)
-                ev["comp"][b].record(stream)
-                with torch.cuda.stream(s_out):
-                    s_out.wait_event(ev["comp"][b])
-                    Qh.copy_(Qd[b], non_blocking=True)
-                    Rh.copy_(Rd[b], non_blocking=True)
-                    ev["out"][b].record(s_out)
-
-            for i in range(2):
-                e2e_step(i)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            s_in.wait_event(f0)
-            for i in range(ke):
-                e2e_step(i)
-            stream.wait_event(ev["out"][(ke - 1) % 2])
-            stream.wait_event(ev["out"][(ke - 2) % 2])
-            f1.record(stream)
-            torch.cuda.synchronize()
-            e2e_ms = f0.elapsed_time(f1) / ke
-            del Qh, Vd, Qd
-            pipeline = "upload, sharded factorization and download of consecutive steps overlap (3 streams)"
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = t.item()
-        line["e2e"] = {"value": algo_bytes * world / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-                       "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n,
-                       "ms_per_step": e2e_ms, "pipeline": pipeline}
-        del Vh
-
-        # GPU baselines on a matrix all three can factor (kappa = 1e4), same size
-        Vb = synthetic.make_v_torch(m, n, 1e4, seed=rank + 100, device=dev)
-        times = {}
-        for name, fn in [("rand_cholqr", lambda: rq.randqr_factor(Vb, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)),
-                         ("cholqr2", lambda: rq.randqr_cholqr2(Vb, Q=Q, R=R, ctx=ctx, sync=False)),
-                         ("shifted_cholqr3", lambda: rq.randqr_shifted_cholqr3(Vb, Q=Q, R=R, ctx=ctx, sync=False))]:
-            fn()
-            torch.cuda.synchronize()
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
             for _ in range(3):
-                fn()
-            g1.record(stream)
+                logical_step()
             torch.cuda.synchronize()
-            times[name] = g0.elapsed_time(g1) / 3
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            for _ in range(3):
+                logical_step()
+            h1.record(stream)
+            torch.cuda.synchronize()
+            sh_ms = h0.elapsed_time(h1) / 3
+            st, info = rq.get_status(ctx)
+            line["sharded_logical"] = {"shards": P, "ms_per_step": sh_ms,
+                                       "value": algo_bytes / (sh_ms / 1e3) / 1e9, "unit": "GB/s",
+                                       "over_unsharded": sh_ms / ms, "status": st}
+
+        if not a.no_extras and world == 1:
+            # the paper's multisketch sizes (Sec. 6.2) on the same matrix: a larger sketch GEMM
+            p1, p2 = synthetic.paper_multisketch_sizes(n)
+            for _ in range(2):
+                rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+            torch.cuda.synchronize()
+            ctx.kernel_times()
+            ctx.set_profiling(True)
+            p0, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(3):
+                rq.randqr_factor(V, p1, p2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)
+            pe.record(stream)
+            torch.cuda.synchronize()
+            ctx.set_profiling(False)
+            pkt = ctx.kernel_times()
+            pms = p0.elapsed_time(pe) / 3
             st, _ = rq.get_status(ctx)
-            times[name + "_status"] = st
-        line["baselines_ms"] = {"kappa": 1e4, **times,
-                                "rand_cholqr_over_cholqr2": times["rand_cholqr"] / times["cholqr2"],
-                                "rand_cholqr_over_shifted_cholqr3": times["rand_cholqr"] / times["shifted_cholqr3"]}
-        del Vb
-        if world == 1:
-            line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
-            line["row_pass_l2_resident"] = l2_resident_rowpass(rq, synthetic, torch, dev)
-            line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
-            # the headline shape across the conditioning range (accuracy; the timing does not
-            # depend on kappa)
-            for kap in (1.0, 1e4, 1e8, 1e15):
-                line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 64, kap,
-                                                          rq.FP64, steps=1))
-            for kap in (1e2, 1e6, 1e10, 1e12):
-                for pr in (rq.FP64, rq.F32X2):
-                    line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
-                                                              steps=1))
-        if world == 1:
-            try:  # context only: a failure here must not cost the line
-                line["fp64_dgemm_tflops"] = fp64_dgemm_tflops(torch, dev)
-            except Exception as e:  # noqa: BLE001
-                line["fp64_dgemm_tflops"] = None
-                line["fp64_dgemm_error"] = str(e)[:200]
-        if not a.no_serve:
-            del Q
-            torch.cuda.empty_cache()
-            line["serving"] = serve_bench(rq, synthetic, torch, dev, n_req=a.serve_requests)
-            torch.cuda.empty_cache()
-            line["batched"] = batch_bench(rq, synthetic, torch, dev)
-        if rank == 0:
-            line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18, s1, s2)
-            line["cpu_baseline_parallel"] = cpu_baseline_parallel(n, a.kappa, 1 << 20, s1, s2)
-            line["cpu_baseline_small"] = cpu_baseline_small()
+            line["paper_sketch_sizes"] = {"s1": p1, "s2": p2, "ms_per_step": pms, "status": st,
+                                          "value": algo_bytes / (pms / 1e3) / 1e9, "unit": "GB/s",
+                                          "kernels_ms_per_step": {k: v[0] / 3 for k, v in pkt.items()}}
+
+        if not a.no_extras:
+            if world == 1:
+                # the other precision of the row passes, on the same matrix
+                other = "f32x2" if a.prec == "fp64" else "fp64"
+                oprec = rq.F32X2 if other == "f32x2" else rq.FP64
+                oms, okt, _, oacc = measure(oprec, a.steps)
+                line["modes"] = {other: {"value": algo_bytes / (oms / 1e3) / 1e9, "unit": "GB/s",
+                                         "ms_per_step": oms, "accuracy": oacc,
+                                         "kernels_ms_per_step": {k: v[0] / a.steps for k, v in okt.items()}}}
+                # the first row pass as one fused launch or as two (solve, then the Gram of W)
+                ctx.set_fused_first_pass(not a.fused)
+                tms, tkt, _, tacc = measure(prec, a.steps)
+                ctx.set_fused_first_pass(a.fused)
+                line["modes"]["two_pass" if a.fused else "fused_first_pass"] = {
+                    "value": algo_bytes / (tms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": tms,
+                    "accuracy": tacc, "kernels_ms_per_step": {k: v[0] / a.steps for k, v in tkt.items()}}
+
+            # end to end through the public API: pinned host V in, Q and R back to pinned host,
+            # every step.  On one GPU that is the host-buffer call randqr_factor_host (its own
+            # upload, factorization in the context's staging area, download); consecutive steps
+            # alternate between two contexts on two streams, so step i + 1's upload overlaps step
+            # i's factorization and download (the pipeline a caller streaming matrices through the
+            # GPU would use).  Row shards (N > 1) copy around the sharded device call the same way.
+            Vh = V.cpu().pin_memory()
+            ke = max(2, min(a.steps, 6))
+            if world == 1:
+                Qh = [torch.empty_like(Vh).pin_memory() for _ in range(2)]
+                Rh = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+                hctx = [ctx, rq.Context(local_rank)]
+                hst = [torch.cuda.Stream(device=dev) for _ in range(2)]
+                done = [torch.cuda.Event() for _ in range(2)]
+
+                def e2e_step(i):
+                    b = i % 2
+                    rq.randqr_factor_host(Vh, s1, s2, seed=0, prec=prec, Q=Qh[b], R=Rh[b], ctx=hctx[b],
+                                          stream=hst[b], sync=False)
+                    done[b].record(hst[b])
+
+                for i in range(2):  # staging areas, workspaces and sketches in place
+                    e2e_step(i)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                for b in range(2):
+                    hst[b].wait_event(f0)
+                for i in range(ke):
+                    e2e_step(i)
+                for b in range(2):
+                    stream.wait_event(done[b])
+                f1.record(stream)
+                torch.cuda.synchronize()
+                for b in range(2):
+                    st_b, _ = rq.get_status(hctx[b], hst[b])
+                    if st_b != 0:
+                        raise SystemExit(f"randqr_factor_host failed with status {st_b}")
+                e2e_ms = f0.elapsed_time(f1) / ke
+                del Qh, hctx
+                pipeline = ("randqr_factor_host on pinned host buffers; consecutive steps on two "
+                            "contexts and streams, so uploads, factorizations and downloads overlap")
+            else:
+                Qh = torch.empty_like(Vh).pin_memory()
+                Rh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+                Vd = [torch.empty_like(V) for _ in range(2)]
+                Qd = [torch.empty_like(V) for _ in range(2)]
+                Rd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
+                s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+                ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
+
+                def e2e_step(i):
+                    b = i % 2
+                    with torch.cuda.stream(s_in):
+                        if i >= 2:
+                            s_in.wait_event(ev["comp"][b])  # step i - 2 has read Vd[b]
+                        Vd[b].copy_(Vh, non_blocking=True)
+                        ev["in"][b].record(s_in)
+                    stream.wait_event(ev["in"][b])
+                    if i >= 2:
+                        stream.wait_event(ev["out"][b])  # step i - 2's download has read Qd[b], Rd[b]
+                    _, Rk = sharded.factor_row_sharded(Vd[b], rank * m, allreduce, s1, s2, seed=0, Q=Qd[b],
+                                                       stages=stages)
+                    Rd[b].copy_(Rk)
+                    ev["comp"][b].record(stream)
+                    with torch.cuda.stream(s_out):
+                        s_out.wait_event(ev["comp"][b])
+                        Qh.copy_(Qd[b], non_blocking=True)
+                        Rh.copy_(Rd[b], non_blocking=True)
+                        ev["out"][b].record(s_out)
+
+                for i in range(2):
+                    e2e_step(i)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                s_in.wait_event(f0)
+                for i in range(ke):
+                    e2e_step(i)
+                stream.wait_event(ev["out"][(ke - 1) % 2])
+                stream.wait_event(ev["out"][(ke - 2) % 2])
+                f1.record(stream)
+                torch.cuda.synchronize()
+                e2e_ms = f0.elapsed_time(f1) / ke
+                del Qh, Vd, Qd
+                pipeline = "upload, sharded factorization and download of consecutive steps overlap (3 streams)"
+            if world > 1:
+                t = torch.tensor([e2e_ms], device=dev)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                e2e_ms = t.item()
+            line["e2e"] = {"value": algo_bytes * world / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+                           "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * n * n,
+                           "ms_per_step": e2e_ms, "pipeline": pipeline}
+            del Vh
+
+            # GPU baselines on a matrix all three can factor (kappa = 1e4), same size
+            Vb = synthetic.make_v_torch(m, n, 1e4, seed=rank + 100, device=dev)
+            times = {}
+            for name, fn in [("rand_cholqr", lambda: rq.randqr_factor(Vb, s1, s2, seed=0, prec=prec, Q=Q, R=R, ctx=ctx, sync=False)),
+                             ("cholqr2", lambda: rq.randqr_cholqr2(Vb, Q=Q, R=R, ctx=ctx, sync=False)),
+                             ("shifted_cholqr3", lambda: rq.randqr_shifted_cholqr3(Vb, Q=Q, R=R, ctx=ctx, sync=False))]:
+                fn()
+                torch.cuda.synchronize()
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for _ in range(3):
+                    fn()
+                g1.record(stream)
+                torch.cuda.synchronize()
+                times[name] = g0.elapsed_time(g1) / 3
+                st, _ = rq.get_status(ctx)
+                times[name + "_status"] = st
+            line["baselines_ms"] = {"kappa": 1e4, **times,
+                                    "rand_cholqr_over_cholqr2": times["rand_cholqr"] / times["cholqr2"],
+                                    "rand_cholqr_over_shifted_cholqr3": times["rand_cholqr"] / times["shifted_cholqr3"]}
+            del Vb
+            if world == 1:
+                line["small_matrix"] = small_latency(rq, synthetic, torch, dev)
+                line["row_pass_l2_resident"] = l2_resident_rowpass(rq, synthetic, torch, dev)
+                line["other_configs"] = [large_config(rq, synthetic, torch, dev, 1 << 23, 32, 1e12, rq.FP64)]
+                # the headline shape across the conditioning range (accuracy; the timing does not
+                # depend on kappa)
+                for kap in (1.0, 1e4, 1e8, 1e15):
+                    line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 64, kap,
+                                                              rq.FP64, steps=1))
+                for kap in (1e2, 1e6, 1e10, 1e12):
+                    for pr in (rq.FP64, rq.F32X2):
+                        line["other_configs"].append(large_config(rq, synthetic, torch, dev, 1 << 23, 128, kap, pr,
+                                                                  steps=1))
+            if world == 1:
+                try:  # context only: a failure here must not cost the line
+                    line["fp64_dgemm_tflops"] = fp64_dgemm_tflops(torch, dev)
+                except Exception as e:  # noqa: BLE001
+                    line["fp64_dgemm_tflops"] = None
+                    line["fp64_dgemm_error"] = str(e)[:200]
+            if not a.no_serve:
+                del Q
+                torch.cuda.empty_cache()
+                line["serving"] = serve_bench(rq, synthetic, torch, dev, n_req=a.serve_requests)
+                torch.cuda.empty_cache()
+                line["batched"] = batch_bench(rq, synthetic, torch, dev)
+            if rank == 0:
+                line["cpu_baseline"] = cpu_baseline(n, a.kappa, 1 << 18, s1, s2)
+                line["cpu_baseline_parallel"] = cpu_baseline_parallel(n, a.kappa, 1 << 20, s1, s2)
+                line["cpu_baseline_small"] = cpu_baseline_small()
+    except Exception as e:  # noqa: BLE001
+        if world > 1:
+            raise
+        line["extras_error"] = f"{type(e).__name__}: {str(e)[:300]}"
 
     if rank == 0:
         print(json.dumps(line), flush=True)
