@@ -126,7 +126,7 @@ randqr_status enqueue_item(Plan *p, int l, int i, const randqr_batch_item &it, c
 }
 
 // Build a plan with L lanes; items dealt largest-first round-robin.
-randqr_status build_plan(randqr_ctx *ctx, randqr_batcher *b, const randqr_batch_item *items,
+randqr_status build_plan(randqr_ctx *ctx, const randqr_batch_item *items,
                          int count, randqr_precision prec, const std::vector<const double *> &s2p,
                          int L, cudaStream_t timing_stream, Plan **out) {
   Plan *p = new (std::nothrow) Plan();
@@ -265,7 +265,7 @@ extern "C" randqr_status randqr_factor_batched(randqr_ctx *ctx, const randqr_bat
     for (int L : cand) {
       if (L > count && L != cand[0]) break;
       Plan *p = nullptr;
-      randqr_status st = build_plan(ctx, b, items, count, prec, s2p, std::min<int>(L, count), s, &p);
+      randqr_status st = build_plan(ctx, items, count, prec, s2p, std::min<int>(L, count), s, &p);
       if (st != RANDQR_OK) {
         destroy_plan(plan);
         return st;
